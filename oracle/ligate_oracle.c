@@ -1,0 +1,530 @@
+/*
+ * FP64 CPU oracle for the ligand dock+score hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the timed
+ * CPU baseline of the benchmark may load this file's library.  It shares no
+ * code, header, table or constant generator with the CUDA path, and it never
+ * touches a GPU.
+ *
+ * What it computes (paper Sec. 2: each ligand is docked in the binding site
+ * by a search with multiple restarts, scored with a geometry-only function,
+ * and the ligand's score is the score of its best pose; Sec. 3.3 batches
+ * many ligand-pocket pairs).  The paper names the method but gives no
+ * formula; the concrete readings taken here are:
+ *
+ *   pose(s, tors) : start s = o*A + a (orientation o, anchor a).  From the
+ *       input (reference) coordinates, each rotatable bond b, in ascending
+ *       DFS pre-order of its child atom v (root = atom 0, children visited
+ *       in ascending atom index), rotates the subtree of v (the side not
+ *       holding the root) about the axis u->v through the CURRENT positions
+ *       of u and v by theta = 2*pi*tors[b]/S (right-hand rule, Rodrigues).
+ *       Then x' = R_o (x - c) + anchor_a with c the centroid of the input
+ *       conformation and R_o the rotation of unit quaternion q_o.
+ *   score(x')    : E = sum_i G_{type(i)}(x'_i)
+ *                      + w * sum_{(i,j) in P} max(0, 1 - d_ij^2/d_c^2)^2
+ *       with P the atom pairs at least 4 bonds apart in the tree.
+ *   G_t(x)       : trilinear interpolation of map t at u = (x - origin)/h.
+ *       If any component of u lies outside [0, n-1] the atom scores the
+ *       out-of-grid penalty instead.  Cell index min(floor(u), n-2), so
+ *       every node, the upper faces included, returns its node value.
+ *       Written as successive linear interpolations along x, then y, then z.
+ *   greedy(s)    : tors = 0; for each bond b in order, try k = 0..S-1
+ *       (other torsions fixed), score each pose in full from the reference
+ *       coordinates, keep the smallest score (ties -> smaller k).
+ *   top-K        : the K starts with the smallest (E, s) pairs; the ligand
+ *       score is the first entry's E.
+ *   descriptor   : per ligand, counts of each atom type, 8-bin histograms
+ *       (edges 1.5, 3, ..., 10.5 A, last bin open) of intramolecular
+ *       distances for each unordered pair of DISTINCT types, and the
+ *       rotatable-bond count; every count goes through log1p; 233 used
+ *       entries zero-padded to 256.  The bin decision is taken in FP32
+ *       (d^2 = (dx*dx + dy*dy) + dz*dz with FP32 rounding at each step,
+ *       compared with the exactly representable squared edges), the
+ *       precision of the GPU kernel, so both sides pick the same bin.
+ *
+ * Parity pins for every function live in tests/test_oracle_*.py.
+ * Compile with -ffp-contract=off.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OR_EXPORT __attribute__((visibility("default")))
+#define OR_MAXA 256
+
+/* ------------------------------------------------------------------------ */
+/* Ligand topology, computed from the plain tree definition.                 */
+typedef struct {
+  int n;                  /* atoms */
+  double ref[OR_MAXA][3]; /* input coordinates */
+  int type[OR_MAXA];
+  int nadj[OR_MAXA];
+  int adj[OR_MAXA][8];
+  int parent[OR_MAXA];    /* rooted at atom 0 */
+  int preorder[OR_MAXA];  /* DFS pre-order position of each atom */
+  int nrot;
+  int rot_u[64], rot_v[64]; /* rotatable bonds, sorted by preorder[v] */
+  unsigned char *moved;     /* nrot x n flags: atom in subtree(v) */
+  int *topo;                /* n x n bond distances */
+  double centroid[3];
+} or_lig;
+
+static void dfs(or_lig *L, int a, int *counter) {
+  L->preorder[a] = (*counter)++;
+  /* children in ascending atom index */
+  int kids[8], nk = 0;
+  for (int q = 0; q < L->nadj[a]; ++q) {
+    int b = L->adj[a][q];
+    if (b != L->parent[a]) kids[nk++] = b;
+  }
+  for (int i = 1; i < nk; ++i)
+    for (int j = i; j > 0 && kids[j - 1] > kids[j]; --j) {
+      int t = kids[j]; kids[j] = kids[j - 1]; kids[j - 1] = t;
+    }
+  for (int i = 0; i < nk; ++i) {
+    L->parent[kids[i]] = a;
+    dfs(L, kids[i], counter);
+  }
+}
+
+static int in_subtree(const or_lig *L, int root, int a) {
+  while (a >= 0) {
+    if (a == root) return 1;
+    a = L->parent[a];
+  }
+  return 0;
+}
+
+/* Build the topology; returns 0 or -1 if the bonds do not form a tree. */
+static int lig_init(or_lig *L, int n, const float *xyz, const uint8_t *type, int nb,
+                    const int *bonds, const uint8_t *rot) {
+  L->moved = NULL;
+  L->topo = NULL;
+  if (n < 1 || n > OR_MAXA || nb != n - 1) return -1;
+  memset(L->nadj, 0, sizeof(L->nadj));
+  L->n = n;
+  for (int i = 0; i < n; ++i) {
+    for (int d = 0; d < 3; ++d) L->ref[i][d] = (double)xyz[3 * i + d];
+    L->type[i] = type[i];
+    L->parent[i] = -2;
+  }
+  for (int b = 0; b < nb; ++b) {
+    int x = bonds[2 * b], y = bonds[2 * b + 1];
+    if (x < 0 || y < 0 || x >= n || y >= n || x == y) return -1;
+    if (L->nadj[x] >= 8 || L->nadj[y] >= 8) return -1;
+    L->adj[x][L->nadj[x]++] = y;
+    L->adj[y][L->nadj[y]++] = x;
+  }
+  L->parent[0] = -1;
+  int visited = 0;
+  dfs(L, 0, &visited);
+  if (visited != n) return -1;
+  /* rotatable bonds: child = endpoint whose parent is the other */
+  L->nrot = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (!rot[b]) continue;
+    int x = bonds[2 * b], y = bonds[2 * b + 1];
+    int u = (L->parent[y] == x) ? x : y;
+    int v = (u == x) ? y : x;
+    if (L->nrot >= 64) return -1;
+    L->rot_u[L->nrot] = u; L->rot_v[L->nrot] = v; L->nrot++;
+  }
+  for (int i = 1; i < L->nrot; ++i) /* sort by preorder of child */
+    for (int j = i; j > 0 && L->preorder[L->rot_v[j - 1]] > L->preorder[L->rot_v[j]]; --j) {
+      int t = L->rot_u[j]; L->rot_u[j] = L->rot_u[j - 1]; L->rot_u[j - 1] = t;
+      t = L->rot_v[j]; L->rot_v[j] = L->rot_v[j - 1]; L->rot_v[j - 1] = t;
+    }
+  L->moved = (unsigned char *)malloc((size_t)(L->nrot > 0 ? L->nrot : 1) * n);
+  L->topo = (int *)malloc(sizeof(int) * (size_t)n * n);
+  if (!L->moved || !L->topo) return -1;
+  for (int b = 0; b < L->nrot; ++b)
+    for (int a = 0; a < n; ++a) L->moved[b * n + a] = (unsigned char)in_subtree(L, L->rot_v[b], a);
+  /* all-pairs bond distance by BFS from each atom */
+  int *queue = (int *)malloc(sizeof(int) * (size_t)n);
+  for (int s = 0; s < n; ++s) {
+    int *d = L->topo + (size_t)s * n;
+    for (int a = 0; a < n; ++a) d[a] = -1;
+    int h = 0, t = 0;
+    queue[t++] = s; d[s] = 0;
+    while (h < t) {
+      int a = queue[h++];
+      for (int q = 0; q < L->nadj[a]; ++q) {
+        int b = L->adj[a][q];
+        if (d[b] < 0) { d[b] = d[a] + 1; queue[t++] = b; }
+      }
+    }
+  }
+  free(queue);
+  for (int d = 0; d < 3; ++d) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += L->ref[i][d];
+    L->centroid[d] = s / n;
+  }
+  return 0;
+}
+static void lig_free(or_lig *L) { free(L->moved); free(L->topo); L->moved = NULL; L->topo = NULL; }
+
+/* ------------------------------------------------------------------------ */
+/* Geometry                                                                  */
+
+/* Rotation matrix of the unit quaternion q = (w, x, y, z) (normalised here):
+ * R v equals the vector part of q v q*. */
+OR_EXPORT void or_quat_to_matrix(const double q_in[4], double R[9]) {
+  double n = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+  double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Rodrigues rotation of point p about the axis through a with unit
+ * direction n, by angle theta (right-hand rule). */
+static void rodrigues(const double a[3], const double n[3], double c, double s, double p[3]) {
+  double v[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  double kv[3] = {n[1] * v[2] - n[2] * v[1], n[2] * v[0] - n[0] * v[2], n[0] * v[1] - n[1] * v[0]};
+  double kd = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+  for (int d = 0; d < 3; ++d) p[d] = a[d] + v[d] * c + kv[d] * s + n[d] * kd * (1.0 - c);
+}
+
+/* Rotate the subtree of bond b of L in coords x by angle theta about the
+ * current axis u->v. */
+static void apply_torsion(const or_lig *L, int b, double theta, double (*x)[3]) {
+  int u = L->rot_u[b], v = L->rot_v[b];
+  double n[3] = {x[v][0] - x[u][0], x[v][1] - x[u][1], x[v][2] - x[u][2]};
+  double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int d = 0; d < 3; ++d) n[d] /= len;
+  double c = cos(theta), s = sin(theta);
+  double axis_pt[3] = {x[v][0], x[v][1], x[v][2]};
+  for (int a = 0; a < L->n; ++a)
+    if (L->moved[b * L->n + a]) rodrigues(axis_pt, n, c, s, x[a]);
+}
+
+static const double OR_TWO_PI = 6.283185307179586476925286766559;
+
+/* Pose coordinates for rigid part (R, anchor) and torsion indices tors[nrot]
+ * with S steps per turn. */
+static void build_pose(const or_lig *L, const double R[9], const double anchor[3],
+                       const int *tors, int S, double (*out)[3]) {
+  for (int a = 0; a < L->n; ++a)
+    for (int d = 0; d < 3; ++d) out[a][d] = L->ref[a][d];
+  for (int b = 0; b < L->nrot; ++b)
+    if (tors[b] % S != 0) apply_torsion(L, b, OR_TWO_PI * (double)tors[b] / (double)S, out);
+  for (int a = 0; a < L->n; ++a) {
+    double v[3] = {out[a][0] - L->centroid[0], out[a][1] - L->centroid[1], out[a][2] - L->centroid[2]};
+    for (int d = 0; d < 3; ++d)
+      out[a][d] = R[3 * d] * v[0] + R[3 * d + 1] * v[1] + R[3 * d + 2] * v[2] + anchor[d];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pocket and score                                                          */
+typedef struct {
+  const float *maps; /* [T][nz][ny][nx] */
+  int n_types, nx, ny, nz;
+  double origin[3], h;
+  double penalty;   /* out-of-grid per-atom score */
+} or_pocket;
+
+static double lerp(double a, double b, double f) { return a + f * (b - a); }
+
+static double trilinear(const or_pocket *P, int t, const double x[3]) {
+  int dims[3] = {P->nx, P->ny, P->nz};
+  double u[3];
+  int c[3];
+  for (int d = 0; d < 3; ++d) {
+    u[d] = (x[d] - P->origin[d]) / P->h;
+    if (!(u[d] >= 0.0 && u[d] <= (double)(dims[d] - 1))) return P->penalty;
+    int f = (int)floor(u[d]);
+    c[d] = f < dims[d] - 2 ? f : dims[d] - 2;
+  }
+  double fx = u[0] - c[0], fy = u[1] - c[1], fz = u[2] - c[2];
+  const float *m = P->maps + (size_t)t * P->nx * P->ny * P->nz;
+#define V(i, j, k) ((double)m[((size_t)(c[2] + (k)) * P->ny + (c[1] + (j))) * P->nx + (c[0] + (i))])
+  double y0z0 = lerp(V(0, 0, 0), V(1, 0, 0), fx);
+  double y1z0 = lerp(V(0, 1, 0), V(1, 1, 0), fx);
+  double y0z1 = lerp(V(0, 0, 1), V(1, 0, 1), fx);
+  double y1z1 = lerp(V(0, 1, 1), V(1, 1, 1), fx);
+#undef V
+  double z0 = lerp(y0z0, y1z0, fy);
+  double z1 = lerp(y0z1, y1z1, fy);
+  return lerp(z0, z1, fz);
+}
+
+typedef struct {
+  double w;      /* clash weight */
+  double dc;     /* clash distance (A) */
+  int min_sep;   /* pairs at least this many bonds apart */
+} or_clash;
+
+static double score_coords(const or_lig *L, const or_pocket *P, const or_clash *C,
+                           double (*x)[3]) {
+  double e = 0.0;
+  for (int a = 0; a < L->n; ++a) e += trilinear(P, L->type[a], x[a]);
+  double cl = 0.0, inv = 1.0 / (C->dc * C->dc);
+  for (int i = 0; i < L->n; ++i)
+    for (int j = i + 1; j < L->n; ++j) {
+      if (L->topo[(size_t)i * L->n + j] < C->min_sep) continue;
+      double dx = x[i][0] - x[j][0], dy = x[i][1] - x[j][1], dz = x[i][2] - x[j][2];
+      double t = 1.0 - (dx * dx + dy * dy + dz * dz) * inv;
+      if (t > 0.0) cl += t * t;
+    }
+  return e + C->w * cl;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported API                                                              */
+
+/* Ligand input (one ligand). */
+typedef struct {
+  int n_atoms;
+  const float *xyz;      /* [n][3] */
+  const uint8_t *type;   /* [n] */
+  int n_bonds;           /* n-1 */
+  const int *bonds;      /* [n-1][2] */
+  const uint8_t *rot;    /* [n-1] */
+} or_ligand_in;
+
+typedef struct {
+  int n_orient, n_anchor, S;
+  const double *quat;     /* [n_orient][4] */
+  const float *anchors;   /* [n_anchor][3] */
+  double clash_w, clash_dc;
+  int clash_min_sep;
+  double penalty;
+} or_sampling;
+
+typedef struct {
+  const float *maps;
+  int n_types, nx, ny, nz;
+  double origin[3];
+  double h;
+} or_pocket_in;
+
+static void make_pocket(const or_pocket_in *pi, double penalty, or_pocket *P) {
+  P->maps = pi->maps; P->n_types = pi->n_types;
+  P->nx = pi->nx; P->ny = pi->ny; P->nz = pi->nz;
+  for (int d = 0; d < 3; ++d) P->origin[d] = pi->origin[d];
+  P->h = pi->h; P->penalty = penalty;
+}
+
+static void start_frame(const or_sampling *sp, int s, double R[9], double anc[3]) {
+  int o = s / sp->n_anchor, a = s % sp->n_anchor;
+  or_quat_to_matrix(sp->quat + 4 * o, R);
+  for (int d = 0; d < 3; ++d) anc[d] = (double)sp->anchors[3 * a + d];
+}
+
+/* Realised rotatable-bond count of a ligand in the oracle's order, with the
+ * (u, v) atoms of each bond; returns nrot or -1. */
+OR_EXPORT int or_ligand_bonds(const or_ligand_in *li, int *u_out, int *v_out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  for (int b = 0; b < L.nrot; ++b) { if (u_out) u_out[b] = L.rot_u[b]; if (v_out) v_out[b] = L.rot_v[b]; }
+  int r = L.nrot;
+  lig_free(&L);
+  return r;
+}
+
+/* Topological (bond-count) distance matrix n x n. */
+OR_EXPORT int or_topo_distance(const or_ligand_in *li, int *out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  memcpy(out, L.topo, sizeof(int) * (size_t)L.n * L.n);
+  lig_free(&L);
+  return 0;
+}
+
+/* Coordinates of n_poses poses: start ids s[i], torsions tors[i][nrot]
+ * (stride tors_stride); out [n_poses][n][3]. */
+OR_EXPORT int or_pose_coords(const or_ligand_in *li, const or_sampling *sp, int n_poses,
+                             const int *starts, const int *tors, int tors_stride, double *out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  for (int p = 0; p < n_poses; ++p) {
+    double R[9], anc[3];
+    start_frame(sp, starts[p], R, anc);
+    build_pose(&L, R, anc, tors + (size_t)p * tors_stride, sp->S, (double(*)[3])(out + (size_t)p * L.n * 3));
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* Apply torsions to the input coordinates in a caller-given bond order,
+ * each about the current axis, without the rigid part (pins torsion-order
+ * independence). angles[nrot] in radians; order[nrot] permutes bonds. */
+OR_EXPORT int or_torsions_in_order(const or_ligand_in *li, const double *angles, const int *order,
+                                   double *out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  double (*x)[3] = (double(*)[3])out;
+  for (int a = 0; a < L.n; ++a)
+    for (int d = 0; d < 3; ++d) x[a][d] = L.ref[a][d];
+  for (int q = 0; q < L.nrot; ++q) apply_torsion(&L, order[q], angles[order[q]], x);
+  lig_free(&L);
+  return 0;
+}
+
+/* Trilinear value of map t at n points (pins interpolation). */
+OR_EXPORT void or_trilinear(const or_pocket_in *pi, double penalty, int t, int n,
+                            const double *pts, double *out) {
+  or_pocket P;
+  make_pocket(pi, penalty, &P);
+  for (int i = 0; i < n; ++i) out[i] = trilinear(&P, t, pts + 3 * i);
+}
+
+/* Score of arbitrary coordinates [n][3] for the ligand's types/topology. */
+OR_EXPORT int or_score_coords(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                              const double *coords, double *out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_pocket P;
+  make_pocket(pi, sp->penalty, &P);
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+  double (*x)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+  memcpy(x, coords, sizeof(double) * 3 * (size_t)L.n);
+  *out = score_coords(&L, &P, &C, x);
+  free(x);
+  lig_free(&L);
+  return 0;
+}
+
+/* Scores of n_poses (start, tors) poses, parallel over poses. */
+OR_EXPORT int or_score_poses(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                             int n_poses, const int *starts, const int *tors, int tors_stride,
+                             double *out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_pocket P;
+  make_pocket(pi, sp->penalty, &P);
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+#pragma omp parallel
+  {
+    double (*x)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+#pragma omp for schedule(dynamic, 8)
+    for (int p = 0; p < n_poses; ++p) {
+      double R[9], anc[3];
+      start_frame(sp, starts[p], R, anc);
+      build_pose(&L, R, anc, tors + (size_t)p * tors_stride, sp->S, x);
+      out[p] = score_coords(&L, &P, &C, x);
+    }
+    free(x);
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* Greedy torsion sweep for the listed starts (parallel over starts).
+ * e_out[i] = final score, tors_out[i][nrot] (stride tors_stride) = chosen
+ * step per bond in bond order; trial_out (optional, [i][nrot][S]) = every
+ * trial score. */
+OR_EXPORT int or_greedy(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                        int n_starts, const int *starts, double *e_out, int *tors_out,
+                        int tors_stride, double *trial_out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_pocket P;
+  make_pocket(pi, sp->penalty, &P);
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+  const int S = sp->S;
+#pragma omp parallel
+  {
+    double (*x)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+    int tors[64];
+#pragma omp for schedule(dynamic, 4)
+    for (int i = 0; i < n_starts; ++i) {
+      double R[9], anc[3];
+      start_frame(sp, starts[i], R, anc);
+      for (int b = 0; b < L.nrot; ++b) tors[b] = 0;
+      double best = 0.0;
+      if (L.nrot == 0) {
+        build_pose(&L, R, anc, tors, S, x);
+        best = score_coords(&L, &P, &C, x);
+      }
+      for (int b = 0; b < L.nrot; ++b) {
+        int bk = 0;
+        for (int k = 0; k < S; ++k) {
+          tors[b] = k;
+          build_pose(&L, R, anc, tors, S, x);
+          double e = score_coords(&L, &P, &C, x);
+          if (trial_out) trial_out[((size_t)i * L.nrot + b) * S + k] = e;
+          if (k == 0 || e < best) { best = e; bk = k; }
+        }
+        tors[b] = bk;
+      }
+      e_out[i] = best;
+      for (int b = 0; b < L.nrot; ++b) tors_out[(size_t)i * tors_stride + b] = tors[b];
+    }
+    free(x);
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* Exhaustive enumeration of all S^nrot torsion combinations for each listed
+ * start; e_out[i][c] with c the odometer index (bond 0 fastest). */
+OR_EXPORT int or_exhaustive(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                            int n_starts, const int *starts, double *e_out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_pocket P;
+  make_pocket(pi, sp->penalty, &P);
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+  const int S = sp->S;
+  long long combos = 1;
+  for (int b = 0; b < L.nrot; ++b) combos *= S;
+#pragma omp parallel
+  {
+    double (*x)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+    int tors[64];
+#pragma omp for schedule(dynamic, 1) collapse(2)
+    for (int i = 0; i < n_starts; ++i)
+      for (long long c = 0; c < combos; ++c) {
+        double R[9], anc[3];
+        start_frame(sp, starts[i], R, anc);
+        long long r = c;
+        for (int b = 0; b < L.nrot; ++b) { tors[b] = (int)(r % S); r /= S; }
+        build_pose(&L, R, anc, tors, S, x);
+        e_out[(size_t)i * combos + c] = score_coords(&L, &P, &C, x);
+      }
+    free(x);
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Descriptor (256 entries, 233 used).                                       */
+OR_EXPORT int or_descriptor(const or_ligand_in *li, int n_types, double *out) {
+  if (n_types != 8) return -1;
+  for (int k = 0; k < 256; ++k) out[k] = 0.0;
+  int n = li->n_atoms;
+  double counts[8] = {0};
+  double hist[28][8];
+  memset(hist, 0, sizeof(hist));
+  for (int i = 0; i < n; ++i) counts[li->type[i]] += 1.0;
+  static const float edge2[7] = {2.25f, 9.0f, 20.25f, 36.0f, 56.25f, 81.0f, 110.25f};
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      int a = li->type[i], b = li->type[j];
+      if (a == b) continue;
+      if (a > b) { int t = a; a = b; b = t; }
+      /* pair index of (a, b), a < b, in lexicographic order */
+      int p = a * 8 - a * (a + 1) / 2 + (b - a - 1);
+      volatile float dx = li->xyz[3 * i] - li->xyz[3 * j];
+      volatile float dy = li->xyz[3 * i + 1] - li->xyz[3 * j + 1];
+      volatile float dz = li->xyz[3 * i + 2] - li->xyz[3 * j + 2];
+      volatile float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+      volatile float s1 = xx + yy;
+      volatile float d2 = s1 + zz;
+      int bin = 0;
+      for (int k = 0; k < 7; ++k) if (d2 >= edge2[k]) bin = k + 1;
+      hist[p][bin] += 1.0;
+    }
+  int nrot = 0;
+  for (int b = 0; b < li->n_bonds; ++b) nrot += li->rot[b] ? 1 : 0;
+  for (int t = 0; t < 8; ++t) out[t] = log1p(counts[t]);
+  for (int p = 0; p < 28; ++p)
+    for (int k = 0; k < 8; ++k) out[8 + 8 * p + k] = log1p(hist[p][k]);
+  out[232] = log1p((double)nrot);
+  return 0;
+}
