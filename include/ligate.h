@@ -1,0 +1,304 @@
+/*
+ * ligate.h - C ABI of the GB300 ligand dock+score library (libligate.so).
+ *
+ * What the library computes (paper Sec. 2, "LIGATE CADD workflow"): every
+ * ligand of a chemical library is docked into a prepared target binding
+ * site by a search with multiple restarts, each pose is scored by a
+ * geometry-only function, and the ligand's score is the score of its best
+ * pose; poses may then be re-scored.  Sec. 3.3 processes a BATCH of
+ * ligand-pocket pairs per device, with ligands grouped by size (atom count,
+ * rotatable-bond count) and batch shapes tuned per size.  Sec. 3.5 proposes
+ * an affinity-prediction model on ligand features to speed the screening.
+ *
+ * The paper gives no formula for any of these steps; the concrete method
+ * implemented here is:
+ *   start s = o * n_anchor + a   : orientation o (unit quaternion) x pocket
+ *                                  anchor a; x' = R_o (x - c) + anchor_a,
+ *                                  c = centroid of the input conformation.
+ *   torsion sweep (greedy)       : rotatable bonds in ascending DFS pre-order
+ *                                  of their child atom (root = atom 0,
+ *                                  children by ascending input index); for
+ *                                  each bond try theta_k = 2 pi k / S,
+ *                                  k = 0..S-1, rotating the child's subtree
+ *                                  about the current u->v axis (right-hand
+ *                                  rule), keep the best k (ties: smaller k).
+ *   score E                      : sum_i G_type(i)(x'_i)  (trilinear
+ *                                  interpolation of the type's grid map,
+ *                                  out-of-grid atoms score `penalty`)
+ *                                  + w sum_{pairs >= 4 bonds apart}
+ *                                        max(0, 1 - d^2 / d_c^2)^2.
+ *   top-K                        : the K starts with smallest (E, s).
+ * Lower scores are better.
+ *
+ * Conventions (every entry point):
+ *  - Returns LIGATE_OK or a negative ligate_status; no call aborts or exits.
+ *    The text of the last error of the calling thread is available from
+ *    ligate_last_error().
+ *  - Input arrays are borrowed for the duration of the call; the library
+ *    copies what it keeps.  Handles are owned by the caller and released
+ *    with the matching *_destroy (NULL is accepted and ignored).
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are memory
+ *    of the current CUDA device.  Calls are made on the current device.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that return results to host memory synchronise the
+ *    stream before returning; calls that write device memory only enqueue.
+ */
+#ifndef LIGATE_H
+#define LIGATE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+#if defined(__GNUC__)
+#pragma GCC visibility push(default) /* the library builds with hidden default visibility */
+#endif
+
+typedef enum {
+  LIGATE_OK = 0,
+  LIGATE_ERR_INVALID = -1,     /* bad argument or malformed input */
+  LIGATE_ERR_OOM = -2,         /* device or host allocation failed */
+  LIGATE_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  LIGATE_ERR_TIMEOUT = -4,     /* a bounded wait ran out */
+  LIGATE_ERR_UNSUPPORTED = -5  /* input beyond the documented limits */
+} ligate_status;
+
+/* Storage precision of the grid maps read by the docking kernel.  Every
+ * precision interpolates and accumulates in FP32. */
+typedef enum { LIGATE_FP32 = 0, LIGATE_BF16 = 1, LIGATE_FP16 = 2 } ligate_precision;
+
+/* Map layouts.  PLAIN: [type][z][y][x] node values.  CORNER: for each cell
+ * the 8 corner values stored contiguously (x fastest, then y, then z), so
+ * one interpolation reads one 32 B (FP32) or 16 B (BF16/FP16) vector. */
+typedef enum { LIGATE_LAYOUT_PLAIN = 0, LIGATE_LAYOUT_CORNER = 1 } ligate_layout;
+
+/* Limits: atoms per ligand, rotatable bonds per ligand, torsion steps,
+ * top-K, atom types. Larger inputs return LIGATE_ERR_UNSUPPORTED. */
+#define LIGATE_MAX_ATOMS 128
+#define LIGATE_MAX_ROT 16
+#define LIGATE_MAX_STEPS 32
+#define LIGATE_MAX_TOPK 32
+#define LIGATE_MAX_TYPES 16
+
+/* Pocket precision-mask bits for ligate_pocket_create. */
+#define LIGATE_POCKET_FP32_CORNER (1u << 0)
+#define LIGATE_POCKET_BF16_CORNER (1u << 1)
+#define LIGATE_POCKET_FP16_CORNER (1u << 2)
+
+const char *ligate_last_error(void); /* thread-local text, never NULL */
+const char *ligate_version(void);
+
+/* ------------------------------------------------------------------------
+ * Prepared target pocket (paper Sec. 2: the target structure every docking
+ * step needs).  maps: host FP32 [n_types][nz][ny][nx], node (ix,iy,iz) at
+ * origin + spacing*(ix,iy,iz) Angstrom.  anchors: host FP32 [n_anchors][3]
+ * Angstrom, the rigid-start translation points.  The FP32 plain layout is
+ * always uploaded; `precision_mask` (LIGATE_POCKET_* bits) adds the
+ * corner-packed copies, converted on the device (BF16/FP16 round to
+ * nearest even).  Errors: INVALID (NULL, dims < 2, n_types outside
+ * 1..LIGATE_MAX_TYPES, spacing <= 0, non-finite map value), OOM, CUDA. */
+typedef struct ligate_pocket ligate_pocket;
+ligate_status ligate_pocket_create(const float *maps, int n_types, int nx, int ny, int nz,
+                                   const double origin[3], double spacing, const float *anchors,
+                                   int n_anchors, unsigned precision_mask, ligate_pocket **out);
+void ligate_pocket_destroy(ligate_pocket *pocket);
+
+/* ------------------------------------------------------------------------
+ * Ligand library (paper Sec. 2: ligands after 3D preparation; Sec. 3.3:
+ * processed as a batch).  All host arrays, concatenated over ligands:
+ *   atom_offset[n_ligands+1], xyz[atoms][3] (Angstrom, the input
+ *   conformation), type[atoms] (< pocket n_types), bond_offset[n_ligands+1]
+ *   with exactly n_atoms-1 bonds per ligand, bonds[bonds][2] (atom indices
+ *   local to the ligand; the bonds must form a tree), rotatable[bonds] (0/1).
+ * ligate_batch_create validates, renumbers every ligand in DFS pre-order,
+ * builds its bond table and clash-pair masks on the host, and uploads the
+ * packed batch to the device, where it stays until destroyed.
+ * Errors: INVALID (not a tree, bad index or type, non-finite coordinate),
+ * UNSUPPORTED (more than LIGATE_MAX_ATOMS atoms or LIGATE_MAX_ROT rotatable
+ * bonds in a ligand), OOM, CUDA.  n_ligands == 0 is valid. */
+typedef struct {
+  int n_ligands;
+  const int32_t *atom_offset;
+  const float *xyz;
+  const uint8_t *type;
+  const int32_t *bond_offset;
+  const int32_t *bonds;
+  const uint8_t *rotatable;
+} ligate_ligands;
+
+typedef struct ligate_batch ligate_batch;
+ligate_status ligate_batch_create(const ligate_ligands *ligands, ligate_batch **out);
+void ligate_batch_destroy(ligate_batch *batch);
+
+typedef struct {
+  int n_ligands;
+  int max_atoms;
+  int max_rot;
+  int64_t total_atoms;
+} ligate_batch_info;
+ligate_status ligate_batch_get_info(const ligate_batch *batch, ligate_batch_info *out);
+/* Realised rotatable-bond count per ligand (host int32[n_ligands]). */
+ligate_status ligate_batch_rot_counts(const ligate_batch *batch, int32_t *out);
+
+/* ------------------------------------------------------------------------
+ * Search parameters.  orientations: host FP64 [n_orient][4] quaternions
+ * (w, x, y, z), normalised and re-orthonormalised in FP32 on the device.
+ * The first n_anchor pocket anchors are used.  clash_weight w, clash
+ * distance d_c (Angstrom), penalty = score of an out-of-grid atom.
+ * rescore_fp32: re-score the top_k poses from the FP32 maps and re-sort
+ * (the precision pattern for BF16/FP16 maps). */
+typedef struct {
+  int n_orient;
+  int n_anchor;
+  int torsion_steps;      /* S, 1..LIGATE_MAX_STEPS */
+  int top_k;              /* K, 1..LIGATE_MAX_TOPK */
+  const double *orientations;
+  float clash_weight;
+  float clash_cutoff;
+  float penalty;
+  ligate_precision precision;
+  ligate_layout layout;   /* CORNER is required for BF16/FP16 */
+  int rescore_fp32;
+} ligate_sampling;
+
+/* One result slot: score, start id (o * n_anchor + a, or -1 for an unused
+ * slot when K exceeds the start count) and the chosen step of each
+ * rotatable bond in sweep order (entries beyond the ligand's count are 0). */
+typedef struct {
+  float score;
+  int32_t start_id;
+  uint8_t tors[LIGATE_MAX_ROT];
+} ligate_pose;
+
+/* Launch shape of the persistent docking kernel (paper Sec. 3.3: batch
+ * shapes tuned per ligand size).  Size bucket b of a ligand is
+ * min(n_rot / 4, 3) + 4 * (n_atoms > 64); starts_per_item[b] is how many
+ * starts one warp takes from the work queue at a time (a multiple of the
+ * warp's start group, 32 / pow2ceil(S)).  A zeroed field means "default". */
+#define LIGATE_N_BUCKETS 8
+typedef struct {
+  int warps_per_cta;
+  int ctas_per_sm;
+  int starts_per_item[LIGATE_N_BUCKETS];
+} ligate_tile;
+
+/* ------------------------------------------------------------------------
+ * Docking plan: packs the work queue (ligand x start-chunk items, largest
+ * first), uploads the start frames, allocates the scratch and output
+ * buffers and captures the whole docking run (queue reset, persistent
+ * kernel, per-ligand merge and optional FP32 rescoring) into one CUDA graph
+ * on first run.  tile == NULL picks the autotuner's cached shape for this
+ * device (LIGATE_TUNE_CACHE file, see ligate_autotune) or the default.
+ * The plan borrows pocket and batch: keep both alive until it is
+ * destroyed.  Errors: INVALID, UNSUPPORTED (S, K or layout outside the
+ * limits, BF16/FP16 without the matching pocket copy), OOM, CUDA. */
+typedef struct ligate_plan ligate_plan;
+ligate_status ligate_plan_create(const ligate_pocket *pocket, const ligate_batch *batch,
+                                 const ligate_sampling *sampling, const ligate_tile *tile,
+                                 ligate_plan **out);
+/* Enqueue one docking run on `stream` (graph replay).  The result,
+ * ligate_pose[n_ligands][top_k] in ligand order, stays in the plan's device
+ * buffer (ligate_plan_output); if `out` is not NULL it is also copied there
+ * (host or device pointer) and, for host memory, the stream is
+ * synchronised. */
+ligate_status ligate_plan_run(ligate_plan *plan, ligate_pose *out, void *stream);
+ligate_status ligate_plan_output(const ligate_plan *plan, const ligate_pose **device_ptr);
+/* Kernel launches one run enqueues, and the shape in use. */
+ligate_status ligate_plan_get_tile(const ligate_plan *plan, ligate_tile *tile_out,
+                                   int *kernel_launches);
+/* Work done by one run, counted from the packed batch: unique poses
+ * (n_starts * (1 + R (S - 1)) per ligand), atom interpolations and
+ * clash-pair evaluations executed by the sweep. */
+typedef struct {
+  double poses;
+  double atom_evals;
+  double pair_evals;
+  double starts;
+} ligate_work;
+ligate_status ligate_plan_work(const ligate_plan *plan, ligate_work *out);
+void ligate_plan_destroy(ligate_plan *plan);
+
+/* One-call docking from HOST arrays to HOST results: packs the batch,
+ * uploads it, runs a plan and copies ligate_pose[n_ligands][top_k] back. */
+ligate_status ligate_dock_batch(const ligate_pocket *pocket, const ligate_ligands *ligands,
+                                const ligate_sampling *sampling, ligate_pose *out, void *stream);
+
+/* Scores of explicit poses (parity checks and rescoring): pose p is ligand
+ * lig_idx[p] of the batch at start start_id[p] with torsion steps
+ * tors[p][LIGATE_MAX_ROT] (sweep order).  All four arrays are DEVICE
+ * memory; out is FP32 [n_poses].  `precision`/`layout` select the maps. */
+ligate_status ligate_score_poses(const ligate_pocket *pocket, const ligate_batch *batch,
+                                 const ligate_sampling *sampling, int n_poses,
+                                 const int32_t *lig_idx, const int32_t *start_id,
+                                 const uint8_t *tors, float *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Autotuner (paper Sec. 3.3: per-size batch tuning).  Times candidate
+ * shapes on a sample of the batch's ligands per size bucket and writes the
+ * best to *best (and to the cache file named by LIGATE_TUNE_CACHE, when
+ * set).  budget_ms bounds the total measuring time. */
+ligate_status ligate_autotune(const ligate_pocket *pocket, const ligate_batch *batch,
+                              const ligate_sampling *sampling, double budget_ms,
+                              ligate_tile *best);
+
+/* ------------------------------------------------------------------------
+ * Ligand descriptors for the triage surrogate (paper Sec. 3.5: ligand
+ * features as input of an affinity predictor).  Per ligand 256 FP32:
+ * [0,8) log1p of the count of each atom type, [8,232) log1p of 8-bin
+ * histograms (edges 1.5, 3, ..., 10.5 A; last bin open) of intramolecular
+ * distances for the 28 unordered pairs of distinct types in lexicographic
+ * order, [232] log1p of the rotatable-bond count, [233,256) zero.  Needs
+ * exactly 8 atom types.  out: DEVICE FP32 [n_ligands][256]. */
+ligate_status ligate_descriptors(const ligate_batch *batch, float *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Triage surrogate: MLP 256 -> 512 -> 512 -> 512 -> 1, ReLU hidden layers,
+ * BF16 weights and activations on the tensor cores with FP32 accumulation,
+ * FP32 master weights, Adam; inputs standardised with the training set's
+ * per-feature mean/std, labels with the training labels' mean/std.
+ * init_weights: host FP32, all layers concatenated as W1[256][512], b1,
+ * W2[512][512], b2, W3[512][512], b3, W4[512][1], b4 (row-major, y = x W
+ * + b), or NULL for He-normal weights drawn from `seed`. */
+typedef struct ligate_surrogate ligate_surrogate;
+#define LIGATE_SURROGATE_PARAMS (256 * 512 + 512 + 512 * 512 + 512 + 512 * 512 + 512 + 512 + 1)
+ligate_status ligate_surrogate_create(const float *init_weights, uint64_t seed,
+                                      ligate_surrogate **out);
+void ligate_surrogate_destroy(ligate_surrogate *s);
+
+/* Train on DEVICE desc[n][256] and labels[n] for `epochs` passes in
+ * mini-batches of `batch` (the last partial batch is dropped), learning
+ * rate lr; the epoch order is a permutation drawn from `seed`.  Sets the
+ * standardisation statistics from these data on the first call.
+ * loss_out (optional, host) receives the mean loss of the last epoch. */
+ligate_status ligate_surrogate_train(ligate_surrogate *s, const float *desc, const float *labels,
+                                     int n, int epochs, int batch, float lr, uint64_t seed,
+                                     float *loss_out, void *stream);
+/* Predicted scores (label units) of DEVICE desc[n][256] into DEVICE
+ * pred[n]. */
+ligate_status ligate_surrogate_predict(const ligate_surrogate *s, const float *desc, int n,
+                                       float *pred, void *stream);
+/* Indices of the ceil(n * keep_frac) ligands with the lowest predicted
+ * score, best first (ties: smaller index), into DEVICE idx_out; pred_out
+ * (DEVICE, optional) receives every prediction. */
+ligate_status ligate_surrogate_rank(const ligate_surrogate *s, const float *desc, int n,
+                                    double keep_frac, int32_t *idx_out, float *pred_out,
+                                    void *stream);
+
+/* Low-level pieces of one training step, exposed for gradient checks:
+ * forward + MSE + backward of one mini-batch on standardised DEVICE inputs
+ * x[b][256] and targets t[b]; gradients (FP32, same layout as the weights)
+ * into DEVICE grad[LIGATE_SURROGATE_PARAMS]; *loss_out (host) = MSE. */
+ligate_status ligate_surrogate_grad(const ligate_surrogate *s, const float *x, const float *t,
+                                    int b, float *grad, float *loss_out, void *stream);
+/* Copy the FP32 master weights (host [LIGATE_SURROGATE_PARAMS]). */
+ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s, float *out);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIGATE_H */

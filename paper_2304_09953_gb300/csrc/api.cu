@@ -1,0 +1,1002 @@
+// Host runtime behind the C ABI of include/ligate.h: error reporting, the
+// pocket object, packing of ligand batches (DFS renumbering, bond table,
+// clash-pair masks), docking plans (work queue, scratch, CUDA graph) and the
+// autotuner.  Paper Sec. 2 (docking of every library ligand into a prepared
+// pocket) and Sec. 3.3 (batches of ligand-pocket pairs, ligands grouped by
+// atom and rotatable-bond count, batch shape tuned per size).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ligate_internal.h"
+
+namespace ligate {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+ligate_status cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return e == cudaErrorMemoryAllocation ? LIGATE_ERR_OOM : LIGATE_ERR_CUDA;
+}
+
+#define CK(call, what)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+template <class T>
+static cudaError_t dmalloc(T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+static int pow2ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace ligate
+
+using namespace ligate;
+
+// ===========================================================================
+
+extern "C" const char *ligate_last_error(void) { return g_err; }
+extern "C" const char *ligate_version(void) { return "ligate-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+extern "C" ligate_status ligate_pocket_create(const float *maps, int n_types, int nx, int ny,
+                                              int nz, const double origin[3], double spacing,
+                                              const float *anchors, int n_anchors,
+                                              unsigned precision_mask, ligate_pocket **out) {
+  if (!out) { set_error("pocket_create: out is NULL"); return LIGATE_ERR_INVALID; }
+  *out = nullptr;
+  if (!maps || !origin || (!anchors && n_anchors > 0)) {
+    set_error("pocket_create: NULL array");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n_types < 1 || n_types > LIGATE_MAX_TYPES || nx < 2 || ny < 2 || nz < 2 || n_anchors < 0 ||
+      !(spacing > 0) || !isfinite(origin[0]) || !isfinite(origin[1]) || !isfinite(origin[2])) {
+    set_error("pocket_create: invalid dimensions (types %d, grid %dx%dx%d, spacing %g)", n_types,
+              nx, ny, nz, spacing);
+    return LIGATE_ERR_INVALID;
+  }
+  if ((double)n_types * nx * ny * nz * 8.0 > 2147483647.0) {
+    set_error("pocket_create: grid too large for 32-bit corner offsets");
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  const size_t nodes = (size_t)nx * ny * nz;
+  for (size_t i = 0; i < nodes * n_types; ++i)
+    if (!isfinite(maps[i])) {
+      set_error("pocket_create: non-finite map value at %zu", i);
+      return LIGATE_ERR_INVALID;
+    }
+  for (int i = 0; i < 3 * n_anchors; ++i)
+    if (!isfinite(anchors[i])) {
+      set_error("pocket_create: non-finite anchor");
+      return LIGATE_ERR_INVALID;
+    }
+  ligate_pocket *p = new ligate_pocket();
+  PocketDev &d = p->d;
+  d.n_types = n_types; d.nx = nx; d.ny = ny; d.nz = nz;
+  for (int a = 0; a < 3; ++a) d.origin[a] = origin[a];
+  d.spacing = spacing;
+  d.n_anchors = n_anchors;
+  d.h_anchors.assign(anchors, anchors + 3 * n_anchors);
+  auto fail = [&](cudaError_t e, const char *w) {
+    ligate_status st = cuda_fail(e, w);
+    ligate_pocket_destroy(p);
+    return st;
+  };
+  cudaError_t e;
+  if ((e = dmalloc(&d.map_f32, nodes * n_types)) != cudaSuccess) return fail(e, "pocket maps");
+  if ((e = cudaMemcpy(d.map_f32, maps, nodes * n_types * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail(e, "pocket upload");
+  if ((e = dmalloc(&d.anchors, (size_t)3 * n_anchors)) != cudaSuccess) return fail(e, "anchors");
+  if (n_anchors &&
+      (e = cudaMemcpy(d.anchors, anchors, 12 * (size_t)n_anchors, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail(e, "anchor upload");
+  const size_t cells = d.n_cells() * n_types;
+  if (precision_mask & LIGATE_POCKET_FP32_CORNER) {
+    if ((e = dmalloc(&d.map_f32c, cells * 8)) != cudaSuccess) return fail(e, "corner maps");
+    if ((e = launch_corner_pack(d.map_f32, n_types, nx, ny, nz, 0, d.map_f32c, 0)) != cudaSuccess)
+      return fail(e, "corner pack");
+  }
+  if (precision_mask & LIGATE_POCKET_BF16_CORNER) {
+    if ((e = dmalloc(&d.map_bf16c, cells * 8)) != cudaSuccess) return fail(e, "bf16 maps");
+    if ((e = launch_corner_pack(d.map_f32, n_types, nx, ny, nz, 1, d.map_bf16c, 0)) != cudaSuccess)
+      return fail(e, "bf16 pack");
+  }
+  if (precision_mask & LIGATE_POCKET_FP16_CORNER) {
+    if ((e = dmalloc(&d.map_f16c, cells * 8)) != cudaSuccess) return fail(e, "fp16 maps");
+    if ((e = launch_corner_pack(d.map_f32, n_types, nx, ny, nz, 2, d.map_f16c, 0)) != cudaSuccess)
+      return fail(e, "fp16 pack");
+  }
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "pocket prepare");
+  *out = p;
+  return LIGATE_OK;
+}
+
+extern "C" void ligate_pocket_destroy(ligate_pocket *p) {
+  if (!p) return;
+  cudaFree(p->d.map_f32);
+  cudaFree(p->d.map_f32c);
+  cudaFree(p->d.map_bf16c);
+  cudaFree(p->d.map_f16c);
+  cudaFree(p->d.anchors);
+  delete p;
+}
+
+// ---------------------------------------------------------------------------
+// Batch packing.
+namespace {
+
+struct LigPack {
+  int n = 0, n_rot = 0, words = 0;
+  int max_type = 0;
+  std::vector<float4> atoms;
+  std::vector<BondRec> bonds;
+  std::vector<uint32_t> elig;
+  std::vector<uint8_t> types;
+};
+
+// Renumber one ligand in DFS pre-order, build its sweep-ordered bond table
+// and the clash-pair bit matrix (pairs >= 4 bonds apart).
+ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, size_t errlen) {
+  const int a0 = L->atom_offset[li], a1 = L->atom_offset[li + 1];
+  const int b0 = L->bond_offset[li], b1 = L->bond_offset[li + 1];
+  const int n = a1 - a0, nb = b1 - b0;
+  if (n < 1) { snprintf(err, errlen, "ligand %d has no atoms", li); return LIGATE_ERR_INVALID; }
+  if (n > LIGATE_MAX_ATOMS) {
+    snprintf(err, errlen, "ligand %d has %d atoms (limit %d)", li, n, LIGATE_MAX_ATOMS);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  if (nb != n - 1) {
+    snprintf(err, errlen, "ligand %d: %d bonds for %d atoms (a tree needs n-1)", li, nb, n);
+    return LIGATE_ERR_INVALID;
+  }
+  std::vector<std::vector<int>> adj(n);
+  for (int b = b0; b < b1; ++b) {
+    const int x = L->bonds[2 * b], y = L->bonds[2 * b + 1];
+    if (x < 0 || y < 0 || x >= n || y >= n || x == y) {
+      snprintf(err, errlen, "ligand %d: bond %d has bad atom index", li, b - b0);
+      return LIGATE_ERR_INVALID;
+    }
+    adj[x].push_back(y);
+    adj[y].push_back(x);
+  }
+  for (auto &v : adj) std::sort(v.begin(), v.end());
+  std::vector<int> pos(n, -1), order, parent(n, -1), size(n, 1), stack;
+  order.reserve(n);
+  stack.push_back(0);
+  parent[0] = -1;
+  std::vector<char> seen(n, 0);
+  seen[0] = 1;
+  while (!stack.empty()) {
+    const int a = stack.back();
+    stack.pop_back();
+    pos[a] = (int)order.size();
+    order.push_back(a);
+    for (int q = (int)adj[a].size() - 1; q >= 0; --q) {  // push descending: pop ascending
+      const int c = adj[a][q];
+      if (c == parent[a]) continue;
+      if (seen[c]) { snprintf(err, errlen, "ligand %d: bonds contain a cycle", li); return LIGATE_ERR_INVALID; }
+      seen[c] = 1;
+      parent[c] = a;
+      stack.push_back(c);
+    }
+  }
+  if ((int)order.size() != n) {
+    snprintf(err, errlen, "ligand %d: bonds do not connect all atoms", li);
+    return LIGATE_ERR_INVALID;
+  }
+  for (int p = n - 1; p > 0; --p) size[parent[order[p]]] += size[order[p]];
+  P.n = n;
+  P.words = (n + 31) / 32;
+  P.atoms.resize(n);
+  P.types.resize(n);
+  P.max_type = 0;
+  for (int p = 0; p < n; ++p) {
+    const int a = order[p];
+    const float *x = L->xyz + 3 * (size_t)(a0 + a);
+    if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
+      snprintf(err, errlen, "ligand %d: non-finite coordinate", li);
+      return LIGATE_ERR_INVALID;
+    }
+    const int t = L->type[a0 + a];
+    P.max_type = std::max(P.max_type, t);
+    P.types[p] = (uint8_t)t;
+    float4 v;
+    v.x = x[0]; v.y = x[1]; v.z = x[2];
+    int ti = t;
+    memcpy(&v.w, &ti, 4);
+    P.atoms[p] = v;
+  }
+  // rotatable bonds in sweep order (ascending DFS position of the child)
+  std::vector<BondRec> br;
+  for (int b = b0; b < b1; ++b) {
+    if (!L->rotatable[b]) continue;
+    const int x = L->bonds[2 * b], y = L->bonds[2 * b + 1];
+    const int child = parent[y] == x ? y : x;
+    const int par = child == y ? x : y;
+    BondRec r;
+    memset(&r, 0, sizeof(r));
+    r.u = pos[par];
+    r.v = pos[child];
+    r.end = r.v + size[child];
+    br.push_back(r);
+  }
+  if ((int)br.size() > LIGATE_MAX_ROT) {
+    snprintf(err, errlen, "ligand %d has %zu rotatable bonds (limit %d)", li, br.size(), LIGATE_MAX_ROT);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  std::sort(br.begin(), br.end(), [](const BondRec &a, const BondRec &b) { return a.v < b.v; });
+  for (auto &r : br) {
+    for (int a = 0; a < n; ++a)
+      if ((a < r.v || a >= r.end) && a != r.u) r.fixed[a >> 5] |= 1u << (a & 31);
+  }
+  P.n_rot = (int)br.size();
+  P.bonds = br;
+  // topological distances in DFS numbering (BFS from every atom)
+  std::vector<std::vector<int>> adjp(n);
+  for (int a = 0; a < n; ++a)
+    for (int c : adj[a]) adjp[pos[a]].push_back(pos[c]);
+  P.elig.assign((size_t)n * P.words, 0u);
+  std::vector<int> dist(n), q(n);
+  for (int s = 0; s < n; ++s) {
+    std::fill(dist.begin(), dist.end(), -1);
+    int h = 0, t = 0;
+    q[t++] = s;
+    dist[s] = 0;
+    while (h < t) {
+      const int a = q[h++];
+      for (int c : adjp[a])
+        if (dist[c] < 0) { dist[c] = dist[a] + 1; q[t++] = c; }
+    }
+    for (int j = 0; j < n; ++j)
+      if (dist[j] >= 4) P.elig[(size_t)s * P.words + (j >> 5)] |= 1u << (j & 31);
+  }
+  return LIGATE_OK;
+}
+
+}  // namespace
+
+extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_batch **out) {
+  if (!out || !L) { set_error("batch_create: NULL argument"); return LIGATE_ERR_INVALID; }
+  *out = nullptr;
+  const int n = L->n_ligands;
+  if (n < 0) { set_error("batch_create: negative ligand count"); return LIGATE_ERR_INVALID; }
+  if (n > 0 && (!L->atom_offset || !L->xyz || !L->type || !L->bond_offset || !L->bonds ||
+                !L->rotatable)) {
+    set_error("batch_create: NULL array");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n > 0 && (L->atom_offset[0] != 0 || L->bond_offset[0] != 0)) {
+    set_error("batch_create: offsets must start at 0");
+    return LIGATE_ERR_INVALID;
+  }
+  for (int i = 0; i < n; ++i)
+    if (L->atom_offset[i + 1] < L->atom_offset[i] || L->bond_offset[i + 1] < L->bond_offset[i]) {
+      set_error("batch_create: offsets not ascending at ligand %d", i);
+      return LIGATE_ERR_INVALID;
+    }
+  std::vector<LigPack> packs(n);
+  std::vector<ligate_status> st(n, LIGATE_OK);
+  std::vector<std::string> errs(n);
+  const unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  const int nthreads = n < 256 ? 1 : (int)nt;
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    char buf[256];
+    for (;;) {
+      const int i0 = next.fetch_add(64);
+      if (i0 >= n) break;
+      for (int i = i0; i < std::min(n, i0 + 64); ++i) {
+        buf[0] = 0;
+        st[i] = pack_one(L, i, packs[i], buf, sizeof(buf));
+        if (st[i] != LIGATE_OK) errs[i] = buf;
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthreads; ++t) th.emplace_back(worker);
+  worker();
+  for (auto &t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != LIGATE_OK) {
+      set_error("batch_create: %s", errs[i].c_str());
+      return st[i];
+    }
+  ligate_batch *B = new ligate_batch();
+  BatchDev &d = B->d;
+  d.n_ligands = n;
+  d.h_lig.resize(n);
+  d.h_rot.resize(n);
+  int64_t na = 0, nb = 0, ne = 0;
+  for (int i = 0; i < n; ++i) {
+    LigDesc &ld = d.h_lig[i];
+    memset(&ld, 0, sizeof(ld));
+    ld.atom_base = (int)na;
+    ld.n_atoms = packs[i].n;
+    ld.n_rot = packs[i].n_rot;
+    ld.n_orig_rot = packs[i].n_rot;
+    ld.bond_base = (int)nb;
+    ld.elig_base = (int)ne;
+    ld.n_words = packs[i].words;
+    na += packs[i].n;
+    nb += packs[i].n_rot;
+    ne += (int64_t)packs[i].n * packs[i].words;
+    d.max_atoms = std::max(d.max_atoms, packs[i].n);
+    d.max_rot = std::max(d.max_rot, packs[i].n_rot);
+    B->max_type = std::max(B->max_type, packs[i].max_type);
+    d.h_rot[i] = packs[i].n_rot;
+  }
+  if (na > 2147483647LL || ne > 2147483647LL) {
+    delete B;
+    set_error("batch_create: batch too large for 32-bit offsets");
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  d.total_atoms = na;
+  std::vector<float4> atoms(na);
+  d.h_bonds.resize(nb);
+  d.h_elig.resize(ne);
+  d.h_types.resize(na);
+  for (int i = 0; i < n; ++i) {
+    const LigDesc &ld = d.h_lig[i];
+    std::copy(packs[i].atoms.begin(), packs[i].atoms.end(), atoms.begin() + ld.atom_base);
+    std::copy(packs[i].types.begin(), packs[i].types.end(), d.h_types.begin() + ld.atom_base);
+    std::copy(packs[i].bonds.begin(), packs[i].bonds.end(), d.h_bonds.begin() + ld.bond_base);
+    std::copy(packs[i].elig.begin(), packs[i].elig.end(), d.h_elig.begin() + ld.elig_base);
+  }
+  cudaError_t e;
+  if ((e = dmalloc(&d.lig, n)) != cudaSuccess || (e = dmalloc(&d.atoms, na)) != cudaSuccess ||
+      (e = dmalloc(&d.bonds, nb)) != cudaSuccess || (e = dmalloc(&d.elig, ne)) != cudaSuccess) {
+    ligate_batch_destroy(B);
+    return cuda_fail(e, "batch allocation");
+  }
+  if ((n && (e = cudaMemcpy(d.lig, d.h_lig.data(), sizeof(LigDesc) * n, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (na && (e = cudaMemcpy(d.atoms, atoms.data(), sizeof(float4) * na, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (nb && (e = cudaMemcpy(d.bonds, d.h_bonds.data(), sizeof(BondRec) * nb, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (ne && (e = cudaMemcpy(d.elig, d.h_elig.data(), 4 * ne, cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    ligate_batch_destroy(B);
+    return cuda_fail(e, "batch upload");
+  }
+  *out = B;
+  return LIGATE_OK;
+}
+
+extern "C" void ligate_batch_destroy(ligate_batch *b) {
+  if (!b) return;
+  cudaFree(b->d.lig);
+  cudaFree(b->d.atoms);
+  cudaFree(b->d.bonds);
+  cudaFree(b->d.elig);
+  delete b;
+}
+
+extern "C" ligate_status ligate_batch_get_info(const ligate_batch *b, ligate_batch_info *out) {
+  if (!b || !out) { set_error("batch_get_info: NULL argument"); return LIGATE_ERR_INVALID; }
+  out->n_ligands = b->d.n_ligands;
+  out->max_atoms = b->d.max_atoms;
+  out->max_rot = b->d.max_rot;
+  out->total_atoms = b->d.total_atoms;
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_batch_rot_counts(const ligate_batch *b, int32_t *out) {
+  if (!b || (!out && b->d.n_ligands)) { set_error("batch_rot_counts: NULL argument"); return LIGATE_ERR_INVALID; }
+  std::copy(b->d.h_rot.begin(), b->d.h_rot.end(), out);
+  return LIGATE_OK;
+}
+
+// ===========================================================================
+// Plans.
+namespace {
+
+int bucket_of(const LigDesc &d) { return std::min(d.n_rot / 4, 3) + 4 * (d.n_atoms > 64); }
+
+// Work of one start of ligand i (atom interpolations, clash pairs).
+void start_work(const BatchDev &B, int i, int S, double &atoms, double &pairs) {
+  const LigDesc &d = B.h_lig[i];
+  atoms = d.n_atoms;
+  pairs = 0;
+  for (int b = 0; b < d.n_rot; ++b) {
+    const BondRec &r = B.h_bonds[d.bond_base + b];
+    atoms += (double)S * (r.end - r.v - 1);
+    for (int a = r.v + 1; a < r.end; ++a)
+      for (int w = 0; w < d.n_words; ++w)
+        pairs += (double)S * __builtin_popcount(B.h_elig[d.elig_base + (size_t)a * d.n_words + w] & r.fixed[w]);
+  }
+}
+
+ligate_status check_sampling(const ligate_pocket *P, const ligate_batch *B, const ligate_sampling *s,
+                             int *mode) {
+  if (!P || !B || !s) { set_error("NULL pocket, batch or sampling"); return LIGATE_ERR_INVALID; }
+  if (s->n_orient < 1 || s->n_anchor < 1 || !s->orientations) {
+    set_error("sampling: need n_orient >= 1, n_anchor >= 1 and orientations");
+    return LIGATE_ERR_INVALID;
+  }
+  if (s->n_anchor > P->d.n_anchors) {
+    set_error("sampling: n_anchor %d exceeds the pocket's %d anchors", s->n_anchor, P->d.n_anchors);
+    return LIGATE_ERR_INVALID;
+  }
+  if ((double)s->n_orient * s->n_anchor > 2147483647.0) {
+    set_error("sampling: too many starts");
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  if (s->torsion_steps < 1 || s->torsion_steps > LIGATE_MAX_STEPS) {
+    set_error("sampling: torsion_steps %d outside 1..%d", s->torsion_steps, LIGATE_MAX_STEPS);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  if (s->top_k < 1 || s->top_k > LIGATE_MAX_TOPK) {
+    set_error("sampling: top_k %d outside 1..%d", s->top_k, LIGATE_MAX_TOPK);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  if (!(s->clash_cutoff > 0) || !isfinite(s->clash_weight) || !isfinite(s->penalty)) {
+    set_error("sampling: clash_cutoff must be > 0, weight and penalty finite");
+    return LIGATE_ERR_INVALID;
+  }
+  for (int i = 0; i < 4 * s->n_orient; ++i)
+    if (!isfinite(s->orientations[i])) { set_error("sampling: non-finite quaternion"); return LIGATE_ERR_INVALID; }
+  for (int i = 0; i < s->n_orient; ++i) {
+    const double *q = s->orientations + 4 * i;
+    if (q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3] < 1e-12) {
+      set_error("sampling: zero quaternion %d", i);
+      return LIGATE_ERR_INVALID;
+    }
+  }
+  if (B->d.n_ligands > 0 && B->max_type >= P->d.n_types) {
+    set_error("batch uses atom type %d but the pocket has %d maps", B->max_type, P->d.n_types);
+    return LIGATE_ERR_INVALID;
+  }
+  const PocketDev &d = P->d;
+  if (s->precision == LIGATE_FP32 && s->layout == LIGATE_LAYOUT_PLAIN) *mode = MODE_F32_PLAIN;
+  else if (s->precision == LIGATE_FP32 && s->layout == LIGATE_LAYOUT_CORNER) *mode = MODE_F32_CORNER;
+  else if (s->precision == LIGATE_BF16 && s->layout == LIGATE_LAYOUT_CORNER) *mode = MODE_BF16_CORNER;
+  else if (s->precision == LIGATE_FP16 && s->layout == LIGATE_LAYOUT_CORNER) *mode = MODE_F16_CORNER;
+  else { set_error("sampling: unsupported precision/layout pair"); return LIGATE_ERR_UNSUPPORTED; }
+  const void *m = *mode == MODE_F32_PLAIN ? (const void *)d.map_f32
+                : *mode == MODE_F32_CORNER ? (const void *)d.map_f32c
+                : *mode == MODE_BF16_CORNER ? (const void *)d.map_bf16c : (const void *)d.map_f16c;
+  if (!m) {
+    set_error("sampling: the pocket was created without this map precision/layout");
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  return LIGATE_OK;
+}
+
+const void *mode_maps(const PocketDev &d, int mode) {
+  return mode == MODE_F32_PLAIN ? (const void *)d.map_f32
+       : mode == MODE_F32_CORNER ? (const void *)d.map_f32c
+       : mode == MODE_BF16_CORNER ? (const void *)d.map_bf16c : (const void *)d.map_f16c;
+}
+
+// Start frames + everything of DockParams that does not depend on items.
+ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const ligate_sampling *s,
+                          int mode, DockParams &p, float **rot, float **anc, float **quat) {
+  const PocketDev &d = P->d;
+  memset(&p, 0, sizeof(p));
+  p.lig = B->d.lig; p.atoms = B->d.atoms; p.bonds = B->d.bonds; p.elig = B->d.elig;
+  p.n_ligands = B->d.n_ligands;
+  p.maps = mode_maps(d, mode);
+  p.maps_f32 = d.map_f32;
+  p.g.nx = d.nx; p.g.ny = d.ny; p.g.nz = d.nz;
+  p.g.fx1 = (float)(d.nx - 1); p.g.fy1 = (float)(d.ny - 1); p.g.fz1 = (float)(d.nz - 1);
+  p.g.penalty = s->penalty;
+  p.n_anchor = s->n_anchor;
+  p.n_starts = s->n_orient * s->n_anchor;
+  p.S = s->torsion_steps;
+  p.L = pow2ceil(s->torsion_steps);
+  p.G = 32 / p.L;
+  p.K = s->top_k;
+  p.clash_w = s->clash_weight;
+  p.inv_dc2_ang = (float)(1.0 / ((double)s->clash_cutoff * s->clash_cutoff));
+  p.inv_dc2_grid = (float)(d.spacing * d.spacing / ((double)s->clash_cutoff * s->clash_cutoff));
+  p.rescore = s->rescore_fp32 ? 1 : 0;
+  p.nmax = std::max(32, (B->d.max_atoms + 31) / 32 * 32);
+  p.wmax = p.nmax / 32;
+  std::vector<float> qf(4 * (size_t)s->n_orient);
+  for (size_t i = 0; i < qf.size(); ++i) qf[i] = (float)s->orientations[i];
+  CK(dmalloc(quat, qf.size()), "quaternions");
+  CK(cudaMemcpy(*quat, qf.data(), 4 * qf.size(), cudaMemcpyHostToDevice), "quaternion upload");
+  CK(dmalloc(rot, 9 * (size_t)s->n_orient), "start frames");
+  CK(dmalloc(anc, 3 * (size_t)s->n_anchor), "start frames");
+  CK(launch_start_frames(nullptr, *quat, s->n_orient, d.anchors, s->n_anchor, d.origin, d.spacing,
+                         *rot, *anc, 0), "start frames");
+  p.rot = *rot;
+  p.anc = *anc;
+  return LIGATE_OK;
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+struct ligate_plan {
+  DockParams p;
+  int mode = 0;
+  ligate_tile tile;
+  int grid = 0, block = 0;
+  size_t smem = 0;
+  int n_ligands = 0;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  Item *items = nullptr;
+  int *lig_items = nullptr, *lig_slot0 = nullptr, *counters = nullptr;
+  PoseOut *partial = nullptr, *out = nullptr;
+  size_t counter_bytes = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ligate_work work;
+};
+
+static void free_plan(ligate_plan *pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+  cudaFree(pl->rot); cudaFree(pl->anc); cudaFree(pl->quat);
+  cudaFree(pl->items); cudaFree(pl->lig_items); cudaFree(pl->lig_slot0);
+  cudaFree(pl->counters); cudaFree(pl->partial); cudaFree(pl->out);
+  delete pl;
+}
+
+// Tile shape: explicit, from the autotuner cache file, or the default.
+static bool read_tune_cache(int S, int mode, ligate_tile *t);
+
+static void default_tile(const DockParams &p, int n_ligands, int sms, ligate_tile *t) {
+  if (t->warps_per_cta <= 0) t->warps_per_cta = 8;
+  const int total_warps = sms * std::max(1, t->ctas_per_sm > 0 ? t->ctas_per_sm : 4) * t->warps_per_cta;
+  const double starts = (double)n_ligands * p.n_starts;
+  int chunk = (int)std::min(2048.0, std::max(4.0 * p.G, starts / (4.0 * total_warps)));
+  chunk = std::max(p.G, chunk / p.G * p.G);
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
+    if (t->starts_per_item[b] <= 0) t->starts_per_item[b] = chunk;
+}
+
+extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate_batch *B,
+                                            const ligate_sampling *s, const ligate_tile *tile,
+                                            ligate_plan **out) {
+  if (!out) { set_error("plan_create: out is NULL"); return LIGATE_ERR_INVALID; }
+  *out = nullptr;
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  ligate_plan *pl = new ligate_plan();
+  pl->mode = mode;
+  pl->n_ligands = B->d.n_ligands;
+  st = base_params(P, B, s, mode, pl->p, &pl->rot, &pl->anc, &pl->quat);
+  if (st != LIGATE_OK) { free_plan(pl); return st; }
+  DockParams &p = pl->p;
+  const int sms = device_sms();
+  memset(&pl->tile, 0, sizeof(pl->tile));
+  if (tile) pl->tile = *tile;
+  else read_tune_cache(p.S, mode, &pl->tile);
+  default_tile(p, pl->n_ligands, sms, &pl->tile);
+  ligate_tile &t = pl->tile;
+  t.warps_per_cta = std::max(1, std::min(16, t.warps_per_cta));
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
+    t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
+  pl->block = 32 * t.warps_per_cta;
+  pl->smem = dock_smem_per_warp(p.nmax, p.G) * t.warps_per_cta;
+  if (pl->smem > 227 * 1024) {
+    free_plan(pl);
+    set_error("plan_create: %zu B shared memory per CTA exceeds 227 KB; use fewer warps", pl->smem);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  const int occ = dock_kernel_max_ctas_per_sm(mode, pl->block, pl->smem);
+  if (occ < 1) {
+    free_plan(pl);
+    set_error("plan_create: kernel cannot be resident with %d threads, %zu B shared memory",
+              pl->block, pl->smem);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  t.ctas_per_sm = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
+  pl->grid = sms * t.ctas_per_sm;
+
+  // work queue: (ligand, start chunk) items, most expensive first
+  const int n = pl->n_ligands;
+  std::vector<Item> items;
+  std::vector<int> lig_items(n), lig_slot0(n);
+  std::vector<double> cost;
+  double poses = 0, aev = 0, pev = 0;
+  for (int i = 0; i < n; ++i) {
+    double a, q;
+    start_work(B->d, i, p.S, a, q);
+    aev += a * p.n_starts;
+    pev += q * p.n_starts;
+    poses += (double)p.n_starts * (1.0 + (double)B->d.h_lig[i].n_rot * (p.S - 1));
+    const int chunk = t.starts_per_item[bucket_of(B->d.h_lig[i])];
+    lig_slot0[i] = (int)items.size();
+    int c = 0;
+    for (int s0 = 0; s0 < p.n_starts; s0 += chunk, ++c) {
+      Item it;
+      it.ligand = i;
+      it.s0 = s0;
+      it.s1 = std::min(p.n_starts, s0 + chunk);
+      it.slot = (int)items.size();
+      items.push_back(it);
+      cost.push_back((a + 0.35 * q + 40.0) * (it.s1 - it.s0));
+    }
+    lig_items[i] = c;
+  }
+  pl->work.poses = poses;
+  pl->work.atom_evals = aev;
+  pl->work.pair_evals = pev;
+  pl->work.starts = (double)n * p.n_starts;
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<Item> sorted(items.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+  const size_t ni = items.size();
+  cudaError_t e;
+  pl->counter_bytes = sizeof(int) * (size_t)(n + 1);
+  if ((e = dmalloc(&pl->items, ni)) != cudaSuccess || (e = dmalloc(&pl->lig_items, n)) != cudaSuccess ||
+      (e = dmalloc(&pl->lig_slot0, n)) != cudaSuccess ||
+      (e = dmalloc(&pl->counters, (size_t)n + 1)) != cudaSuccess ||
+      (e = dmalloc(&pl->partial, ni * p.K)) != cudaSuccess ||
+      (e = dmalloc(&pl->out, (size_t)n * p.K)) != cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "plan allocation");
+  }
+  if ((ni && (e = cudaMemcpy(pl->items, sorted.data(), sizeof(Item) * ni, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (n && (e = cudaMemcpy(pl->lig_items, lig_items.data(), 4 * (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (n && (e = cudaMemcpy(pl->lig_slot0, lig_slot0.data(), 4 * (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    free_plan(pl);
+    return cuda_fail(e, "plan upload");
+  }
+  p.items = pl->items;
+  p.n_items = (int)ni;
+  p.lig_items = pl->lig_items;
+  p.lig_slot0 = pl->lig_slot0;
+  p.queue = pl->counters;
+  p.done = pl->counters + 1;
+  p.partial = pl->partial;
+  p.out = pl->out;
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan setup"); }
+  *out = pl;
+  return LIGATE_OK;
+}
+
+// Capture reset + docking kernel into a graph (once per plan).
+static ligate_status plan_capture(ligate_plan *pl) {
+  if (pl->exec) return LIGATE_OK;
+  CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking), "capture stream");
+  CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = cudaMemsetAsync(pl->counters, 0, pl->counter_bytes, pl->cap_stream);
+  if (e == cudaSuccess && pl->p.n_items > 0)
+    e = launch_dock(pl->mode, pl->p, pl->grid, pl->block, pl->smem, pl->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(pl->cap_stream, &g);
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture docking run"); }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+  pl->graph = g;
+  CK(cudaGraphInstantiate(&pl->exec, g, 0), "graph instantiate");
+  return LIGATE_OK;
+}
+
+static bool is_host_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return true; }
+  return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+extern "C" ligate_status ligate_plan_run(ligate_plan *pl, ligate_pose *out, void *stream) {
+  if (!pl) { set_error("plan_run: NULL plan"); return LIGATE_ERR_INVALID; }
+  ligate_status st = plan_capture(pl);
+  if (st != LIGATE_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaGraphLaunch(pl->exec, s), "graph launch");
+  if (out) {
+    const size_t bytes = sizeof(PoseOut) * (size_t)pl->n_ligands * pl->p.K;
+    if (bytes) CK(cudaMemcpyAsync(out, pl->out, bytes, cudaMemcpyDefault, s), "result copy");
+    if (is_host_ptr(out)) CK(cudaStreamSynchronize(s), "stream synchronize");
+  }
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_output(const ligate_plan *pl, const ligate_pose **ptr) {
+  if (!pl || !ptr) { set_error("plan_output: NULL argument"); return LIGATE_ERR_INVALID; }
+  *ptr = reinterpret_cast<const ligate_pose *>(pl->out);
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_get_tile(const ligate_plan *pl, ligate_tile *t, int *launches) {
+  if (!pl) { set_error("plan_get_tile: NULL plan"); return LIGATE_ERR_INVALID; }
+  if (t) *t = pl->tile;
+  if (launches) *launches = pl->p.n_items > 0 ? 1 : 0;
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_work(const ligate_plan *pl, ligate_work *w) {
+  if (!pl || !w) { set_error("plan_work: NULL argument"); return LIGATE_ERR_INVALID; }
+  *w = pl->work;
+  return LIGATE_OK;
+}
+
+extern "C" void ligate_plan_destroy(ligate_plan *pl) { free_plan(pl); }
+
+extern "C" ligate_status ligate_dock_batch(const ligate_pocket *P, const ligate_ligands *L,
+                                           const ligate_sampling *s, ligate_pose *out,
+                                           void *stream) {
+  if (!out && L && L->n_ligands > 0) { set_error("dock_batch: out is NULL"); return LIGATE_ERR_INVALID; }
+  ligate_batch *B = nullptr;
+  ligate_status st = ligate_batch_create(L, &B);
+  if (st != LIGATE_OK) return st;
+  ligate_plan *pl = nullptr;
+  st = ligate_plan_create(P, B, s, nullptr, &pl);
+  if (st == LIGATE_OK) {
+    st = ligate_plan_run(pl, out, stream);
+    if (st == LIGATE_OK) {
+      cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+      if (e != cudaSuccess) st = cuda_fail(e, "dock_batch");
+    }
+  }
+  ligate_plan_destroy(pl);
+  ligate_batch_destroy(B);
+  return st;
+}
+
+extern "C" ligate_status ligate_score_poses(const ligate_pocket *P, const ligate_batch *B,
+                                            const ligate_sampling *s, int n_poses,
+                                            const int32_t *lig_idx, const int32_t *start_id,
+                                            const uint8_t *tors, float *out, void *stream) {
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  if (n_poses < 0 || (n_poses > 0 && (!lig_idx || !start_id || !tors || !out))) {
+    set_error("score_poses: bad pose arrays");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n_poses == 0) return LIGATE_OK;
+  DockParams p;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  st = base_params(P, B, s, mode, p, &rot, &anc, &quat);
+  cudaError_t e = cudaSuccess;
+  if (st == LIGATE_OK) {
+    e = launch_score_poses(mode, p, n_poses, lig_idx, start_id, tors, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  cudaFree(rot); cudaFree(anc); cudaFree(quat);
+  if (st != LIGATE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "score_poses");
+  return LIGATE_OK;
+}
+
+// ===========================================================================
+// Autotuner: per size bucket, time a sample of that bucket's ligands under
+// candidate chunk sizes; the CTA shape (warps per CTA) is tuned on the whole
+// sample.  Results are cached per (device, S, mode) in LIGATE_TUNE_CACHE.
+static std::string tune_key(int S, int mode) {
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::ostringstream k;
+  k << prop.name << "|sm" << prop.major << prop.minor << "|S" << S << "|mode" << mode;
+  std::string s = k.str();
+  for (auto &c : s) if (c == ' ') c = '_';
+  return s;
+}
+
+static bool read_tune_cache(int S, int mode, ligate_tile *t) {
+  const char *path = getenv("LIGATE_TUNE_CACHE");
+  if (!path || !*path) return false;
+  std::ifstream f(path);
+  if (!f) return false;
+  const std::string key = tune_key(S, mode);
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    std::string k;
+    is >> k;
+    if (k != key) continue;
+    ligate_tile r;
+    memset(&r, 0, sizeof(r));
+    is >> r.warps_per_cta >> r.ctas_per_sm;
+    for (int b = 0; b < LIGATE_N_BUCKETS; ++b) is >> r.starts_per_item[b];
+    if (!is) return false;
+    *t = r;
+    return true;
+  }
+  return false;
+}
+
+static void write_tune_cache(int S, int mode, const ligate_tile &t) {
+  const char *path = getenv("LIGATE_TUNE_CACHE");
+  if (!path || !*path) return;
+  const std::string key = tune_key(S, mode);
+  std::vector<std::string> keep;
+  {
+    std::ifstream f(path);
+    std::string line;
+    while (f && std::getline(f, line)) {
+      std::istringstream is(line);
+      std::string k;
+      is >> k;
+      if (k != key && !line.empty()) keep.push_back(line);
+    }
+  }
+  std::ofstream f(path, std::ios::trunc);
+  for (auto &l : keep) f << l << "\n";
+  f << key << " " << t.warps_per_cta << " " << t.ctas_per_sm;
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b) f << " " << t.starts_per_item[b];
+  f << "\n";
+}
+
+// Sub-batch of ligands `idx` (host re-packing from the packed batch).
+static ligate_status sub_batch(const ligate_batch *B, const std::vector<int> &idx, ligate_batch **out) {
+  *out = nullptr;
+  ligate_batch *S = new ligate_batch();
+  BatchDev &d = S->d;
+  const BatchDev &src = B->d;
+  d.n_ligands = (int)idx.size();
+  std::vector<float4> atoms;
+  std::vector<float4> all_atoms(src.total_atoms);
+  if (src.total_atoms &&
+      cudaMemcpy(all_atoms.data(), src.atoms, sizeof(float4) * src.total_atoms, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    delete S;
+    return cuda_fail(cudaGetLastError(), "autotune sample");
+  }
+  for (int i : idx) {
+    LigDesc ld = src.h_lig[i];
+    const LigDesc o = ld;
+    ld.atom_base = (int)atoms.size();
+    ld.bond_base = (int)d.h_bonds.size();
+    ld.elig_base = (int)d.h_elig.size();
+    for (int a = 0; a < o.n_atoms; ++a) {
+      atoms.push_back(all_atoms[o.atom_base + a]);
+      d.h_types.push_back(src.h_types[o.atom_base + a]);
+    }
+    for (int b = 0; b < o.n_rot; ++b) d.h_bonds.push_back(src.h_bonds[o.bond_base + b]);
+    for (int w = 0; w < o.n_atoms * o.n_words; ++w) d.h_elig.push_back(src.h_elig[o.elig_base + w]);
+    d.h_lig.push_back(ld);
+    d.h_rot.push_back(o.n_rot);
+    d.max_atoms = std::max(d.max_atoms, o.n_atoms);
+    d.max_rot = std::max(d.max_rot, o.n_rot);
+  }
+  S->max_type = B->max_type;
+  d.total_atoms = (int64_t)atoms.size();
+  cudaError_t e;
+  if ((e = dmalloc(&d.lig, d.h_lig.size())) != cudaSuccess ||
+      (e = dmalloc(&d.atoms, atoms.size())) != cudaSuccess ||
+      (e = dmalloc(&d.bonds, d.h_bonds.size())) != cudaSuccess ||
+      (e = dmalloc(&d.elig, d.h_elig.size())) != cudaSuccess) {
+    ligate_batch_destroy(S);
+    return cuda_fail(e, "autotune sample");
+  }
+  cudaMemcpy(d.lig, d.h_lig.data(), sizeof(LigDesc) * d.h_lig.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(d.atoms, atoms.data(), sizeof(float4) * atoms.size(), cudaMemcpyHostToDevice);
+  if (!d.h_bonds.empty()) cudaMemcpy(d.bonds, d.h_bonds.data(), sizeof(BondRec) * d.h_bonds.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(d.elig, d.h_elig.data(), 4 * d.h_elig.size(), cudaMemcpyHostToDevice);
+  if ((e = cudaGetLastError()) != cudaSuccess) { ligate_batch_destroy(S); return cuda_fail(e, "autotune sample"); }
+  *out = S;
+  return LIGATE_OK;
+}
+
+// Time one run of `tile` on batch B (ms); negative on failure.
+static double time_tile(const ligate_pocket *P, const ligate_batch *B, const ligate_sampling *s,
+                        const ligate_tile &tile, int reps) {
+  ligate_plan *pl = nullptr;
+  if (ligate_plan_create(P, B, s, &tile, &pl) != LIGATE_OK) return -1;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double best = -1;
+  if (ligate_plan_run(pl, nullptr, 0) == LIGATE_OK && cudaDeviceSynchronize() == cudaSuccess) {
+    for (int r = 0; r < reps; ++r) {
+      cudaEventRecord(a, 0);
+      ligate_plan_run(pl, nullptr, 0);
+      cudaEventRecord(b, 0);
+      cudaEventSynchronize(b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      if (best < 0 || ms < best) best = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ligate_plan_destroy(pl);
+  return best;
+}
+
+extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_batch *B,
+                                         const ligate_sampling *s, double budget_ms,
+                                         ligate_tile *best) {
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  if (!best) { set_error("autotune: best is NULL"); return LIGATE_ERR_INVALID; }
+  const auto t_start = std::chrono::steady_clock::now();
+  auto elapsed = [&]() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  };
+  // sample: up to `per` ligands of each bucket, spread over the batch
+  std::vector<std::vector<int>> by_bucket(LIGATE_N_BUCKETS);
+  for (int i = 0; i < B->d.n_ligands; ++i) by_bucket[bucket_of(B->d.h_lig[i])].push_back(i);
+  const int per = 48;
+  std::vector<int> sample;
+  std::vector<std::vector<int>> bsample(LIGATE_N_BUCKETS);
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
+    const auto &v = by_bucket[b];
+    const int m = std::min<int>(per, (int)v.size());
+    for (int j = 0; j < m; ++j) bsample[b].push_back(v[(size_t)j * v.size() / m]);
+    sample.insert(sample.end(), bsample[b].begin(), bsample[b].end());
+  }
+  ligate_tile cur;
+  memset(&cur, 0, sizeof(cur));
+  const int G = 32 / pow2ceil(s->torsion_steps);
+  if (sample.empty()) {
+    cur.warps_per_cta = 8;
+    for (int b = 0; b < LIGATE_N_BUCKETS; ++b) cur.starts_per_item[b] = std::max(G, 512 / G * G);
+    *best = cur;
+    return LIGATE_OK;
+  }
+  ligate_batch *SB = nullptr;
+  if ((st = sub_batch(B, sample, &SB)) != LIGATE_OK) return st;
+  // 1) CTA shape on the whole sample with a mid chunk
+  const int mid = std::max(G, 512 / G * G);
+  double best_ms = -1;
+  ligate_tile best_t = cur;
+  for (int w : {4, 8, 16}) {
+    ligate_tile t;
+    memset(&t, 0, sizeof(t));
+    t.warps_per_cta = w;
+    for (int b = 0; b < LIGATE_N_BUCKETS; ++b) t.starts_per_item[b] = mid;
+    const double ms = time_tile(P, SB, s, t, 3);
+    if (ms > 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; best_t = t; }
+    if (elapsed() > budget_ms) break;
+  }
+  ligate_batch_destroy(SB);
+  if (best_ms < 0) { set_error("autotune: no candidate shape ran"); return LIGATE_ERR_CUDA; }
+  cur = best_t;
+  // 2) chunk per bucket, timed on that bucket's sample alone
+  for (int b = 0; b < LIGATE_N_BUCKETS && elapsed() < budget_ms; ++b) {
+    if (bsample[b].empty()) continue;
+    ligate_batch *BB = nullptr;
+    if (sub_batch(B, bsample[b], &BB) != LIGATE_OK) continue;
+    double bms = -1;
+    int bchunk = cur.starts_per_item[b];
+    for (int c : {128, 256, 512, 1024, 2048}) {
+      const int chunk = std::max(G, c / G * G);
+      ligate_tile t = cur;
+      for (int q = 0; q < LIGATE_N_BUCKETS; ++q) t.starts_per_item[q] = chunk;
+      const double ms = time_tile(P, BB, s, t, 2);
+      if (ms > 0 && (bms < 0 || ms < bms * 0.98)) { bms = ms; bchunk = chunk; }
+      if (elapsed() > budget_ms) break;
+    }
+    cur.starts_per_item[b] = bchunk;
+    ligate_batch_destroy(BB);
+  }
+  *best = cur;
+  write_tune_cache(s->torsion_steps, mode, cur);
+  return LIGATE_OK;
+}

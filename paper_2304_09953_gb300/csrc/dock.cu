@@ -1,0 +1,621 @@
+// Persistent docking kernel for sm_103a: rigid starts (orientation x anchor),
+// greedy torsion sweep, trilinear grid score + intramolecular clash term,
+// warp-shuffle top-K per ligand, last-arriver merge and optional FP32
+// rescoring.  Paper Sec. 2 (multi-restart docking with a geometric score;
+// ligand score = best pose; optional re-scoring of the generated poses) and
+// Sec. 3.3 (one batch of ligand-pocket pairs per device launch).
+//
+// Work mapping.  A warp takes work items (ligand, range of starts) from a
+// global queue.  Inside the warp, lanes form G = 32 / L groups of L lanes
+// (L = S rounded up to a power of two); each group runs one start, and lane
+// k of a group evaluates torsion step k of the current bond.  Every lane of
+// the warp therefore executes the same bond, the same moved atom and the same
+// clash partner at the same time: no divergence, and each pose coordinate is
+// a shared-memory broadcast.  Only the moved side of the current bond is
+// re-scored (the rest of the score is the same for every k); the k = 0 lane
+// re-evaluates the current pose, so E += V(k*) - V(0).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "ligate_internal.h"
+
+namespace ligate {
+
+#define FULL 0xffffffffu
+#define EMPTY_SID 0x7fffffff
+
+// ---------------------------------------------------------------------------
+// Trilinear interpolation at grid coordinates (ux, uy, uz) of the map whose
+// first element (plain) or cell (corner layouts) is at `toff`.  Outside
+// [0, n-1] on any axis the atom scores the penalty.  Cell = min(floor, n-2),
+// then successive linear interpolation along x, y, z.
+template <int MODE>
+__device__ __forceinline__ float grid_eval(const void *__restrict__ maps, int toff, float ux,
+                                           float uy, float uz, const GridConst &g) {
+  if (!((ux >= 0.f) & (ux <= g.fx1) & (uy >= 0.f) & (uy <= g.fy1) & (uz >= 0.f) &
+        (uz <= g.fz1)))
+    return g.penalty;
+  const int ix = min((int)ux, g.nx - 2), iy = min((int)uy, g.ny - 2), iz = min((int)uz, g.nz - 2);
+  const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+  float v0, v1, v2, v3, v4, v5, v6, v7;
+  if (MODE == MODE_F32_PLAIN) {
+    const float *m = (const float *)maps + toff + (iz * g.ny + iy) * g.nx + ix;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    v0 = __ldg(m); v1 = __ldg(m + 1); v2 = __ldg(m + sy); v3 = __ldg(m + sy + 1);
+    v4 = __ldg(m + sz); v5 = __ldg(m + sz + 1); v6 = __ldg(m + sz + sy); v7 = __ldg(m + sz + sy + 1);
+  } else {
+    const size_t cell = (size_t)toff + ((size_t)iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+    if (MODE == MODE_F32_CORNER) {
+      const float4 *m = (const float4 *)maps + 2 * cell;
+      const float4 a = __ldg(m), b = __ldg(m + 1);
+      v0 = a.x; v1 = a.y; v2 = a.z; v3 = a.w; v4 = b.x; v5 = b.y; v6 = b.z; v7 = b.w;
+    } else {
+      const uint4 w = __ldg((const uint4 *)maps + cell);
+      if (MODE == MODE_BF16_CORNER) {
+        v0 = __uint_as_float(w.x << 16); v1 = __uint_as_float(w.x & 0xffff0000u);
+        v2 = __uint_as_float(w.y << 16); v3 = __uint_as_float(w.y & 0xffff0000u);
+        v4 = __uint_as_float(w.z << 16); v5 = __uint_as_float(w.z & 0xffff0000u);
+        v6 = __uint_as_float(w.w << 16); v7 = __uint_as_float(w.w & 0xffff0000u);
+      } else {
+        float2 f;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.x)); v0 = f.x; v1 = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.y)); v2 = f.x; v3 = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.z)); v4 = f.x; v5 = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.w)); v6 = f.x; v7 = f.y;
+      }
+    }
+  }
+  const float y0z0 = fmaf(fx, v1 - v0, v0);
+  const float y1z0 = fmaf(fx, v3 - v2, v2);
+  const float y0z1 = fmaf(fx, v5 - v4, v4);
+  const float y1z1 = fmaf(fx, v7 - v6, v6);
+  const float z0 = fmaf(fy, y1z0 - y0z0, y0z0);
+  const float z1 = fmaf(fy, y1z1 - y0z1, y0z1);
+  return fmaf(fz, z1 - z0, z0);
+}
+
+// Element stride of one atom type's map in a given mode (plain: nodes;
+// corner: cells).
+__host__ __device__ inline int type_stride(int mode, const GridConst &g) {
+  return mode == MODE_F32_PLAIN ? g.nx * g.ny * g.nz : (g.nx - 1) * (g.ny - 1) * (g.nz - 1);
+}
+
+// Rotation by angle (c = cos, s = sin) about unit axis n through point p:
+// y = R x + t, with R = c I + s [n]x + (1 - c) n n^T and t = p - R p.
+struct Rot {
+  float r00, r01, r02, r10, r11, r12, r20, r21, r22, tx, ty, tz;
+  __device__ __forceinline__ void make(float c, float s, float nx, float ny, float nz, float px,
+                                       float py, float pz) {
+    const float o = 1.f - c;
+    r00 = fmaf(o * nx, nx, c);       r01 = fmaf(o * nx, ny, -s * nz); r02 = fmaf(o * nx, nz, s * ny);
+    r10 = fmaf(o * ny, nx, s * nz);  r11 = fmaf(o * ny, ny, c);       r12 = fmaf(o * ny, nz, -s * nx);
+    r20 = fmaf(o * nz, nx, -s * ny); r21 = fmaf(o * nz, ny, s * nx);  r22 = fmaf(o * nz, nz, c);
+    tx = px - fmaf(r00, px, fmaf(r01, py, r02 * pz));
+    ty = py - fmaf(r10, px, fmaf(r11, py, r12 * pz));
+    tz = pz - fmaf(r20, px, fmaf(r21, py, r22 * pz));
+  }
+  __device__ __forceinline__ void apply(float x, float y, float z, float &ox, float &oy,
+                                        float &oz) const {
+    ox = fmaf(r00, x, fmaf(r01, y, fmaf(r02, z, tx)));
+    oy = fmaf(r10, x, fmaf(r11, y, fmaf(r12, z, ty)));
+    oz = fmaf(r20, x, fmaf(r21, y, fmaf(r22, z, tz)));
+  }
+};
+
+// Unit axis from atom u to atom v of a pose.
+__device__ __forceinline__ void bond_axis(const float4 &pu, const float4 &pv, float &nx, float &ny,
+                                          float &nz) {
+  nx = pv.x - pu.x; ny = pv.y - pu.y; nz = pv.z - pu.z;
+  const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+  nx *= inv; ny *= inv; nz *= inv;
+}
+
+// (E, s) lexicographic order; an empty slot is (+inf, EMPTY_SID).
+__device__ __forceinline__ bool pose_less(float e1, int s1, float e2, int s2) {
+  return e1 < e2 || (e1 == e2 && s1 < s2);
+}
+
+// Warp-distributed sorted top-K list: lane j < K holds entry j.
+struct TopK {
+  float e;
+  int s;
+  uint32_t t0, t1, t2, t3;
+  __device__ __forceinline__ void clear() {
+    e = __int_as_float(0x7f800000); s = EMPTY_SID; t0 = t1 = t2 = t3 = 0;
+  }
+  // Insert a warp-uniform candidate (all lanes pass the same values).
+  __device__ __forceinline__ void insert(float ce, int cs, uint32_t c0, uint32_t c1, uint32_t c2,
+                                         uint32_t c3, int K, int lane) {
+    const float ke = __shfl_sync(FULL, e, K - 1);
+    const int ks = __shfl_sync(FULL, s, K - 1);
+    if (!pose_less(ce, cs, ke, ks)) return;  // warp-uniform
+    const bool before = lane < K && pose_less(e, s, ce, cs);
+    const int pos = __popc(__ballot_sync(FULL, before));
+    const float ue = __shfl_up_sync(FULL, e, 1);
+    const int us = __shfl_up_sync(FULL, s, 1);
+    const uint32_t u0 = __shfl_up_sync(FULL, t0, 1), u1 = __shfl_up_sync(FULL, t1, 1),
+                   u2 = __shfl_up_sync(FULL, t2, 1), u3 = __shfl_up_sync(FULL, t3, 1);
+    if (lane > pos && lane < K) { e = ue; s = us; t0 = u0; t1 = u1; t2 = u2; t3 = u3; }
+    if (lane == pos) { e = ce; s = cs; t0 = c0; t1 = c1; t2 = c2; t3 = c3; }
+  }
+};
+
+// Per-warp shared-memory slot.
+struct WarpSmem {
+  float4 *ref;     // [nmax]  (x - c, y - c, z - c) Angstrom, .w = atom type (int bits)
+  float4 *pose;    // [G][nmax + 1] current pose, grid units, .w = map offset (int bits)
+  BondRec *bonds;  // [LIGATE_MAX_ROT]
+  uint32_t *elig;  // [nmax * wmax]
+};
+
+__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int wmax, int G) {
+  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + sizeof(BondRec) * LIGATE_MAX_ROT +
+         (size_t)nmax * wmax * 4;
+}
+
+size_t dock_smem_per_warp(int nmax, int G) {
+  return smem_bytes_per_warp(nmax, (nmax + 31) / 32, G);
+}
+
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int wmax, int G) {
+  WarpSmem w;
+  w.ref = reinterpret_cast<float4 *>(base);
+  w.pose = w.ref + nmax;
+  w.bonds = reinterpret_cast<BondRec *>(w.pose + (size_t)G * (nmax + 1));
+  w.elig = reinterpret_cast<uint32_t *>(w.bonds + LIGATE_MAX_ROT);
+  return w;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Load ligand `li` into the warp's slot: reference coordinates centred on
+// their centroid, bond table, clash masks.  Returns the clash sum (without
+// the weight) of the input conformation, which every pose shares up to the
+// torsion-dependent part.
+__device__ float load_ligand(const DockParams &p, const WarpSmem &w, int li, LigDesc &d,
+                             int lane) {
+  d = p.lig[li];
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 a = __ldg(p.atoms + d.atom_base + i);
+    w.ref[i] = a;
+    sx += a.x; sy += a.y; sz += a.z;
+  }
+  sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+  const float inv_n = 1.f / (float)d.n_atoms;
+  const float cx = sx * inv_n, cy = sy * inv_n, cz = sz * inv_n;
+  __syncwarp();
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    float4 a = w.ref[i];
+    a.x -= cx; a.y -= cy; a.z -= cz;
+    w.ref[i] = a;
+  }
+  for (int b = lane; b < d.n_rot; b += 32) w.bonds[b] = p.bonds[d.bond_base + b];
+  for (int q = lane; q < d.n_atoms * d.n_words; q += 32) w.elig[q] = __ldg(p.elig + d.elig_base + q);
+  __syncwarp();
+  float cl = 0.f;
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 xi = w.ref[i];
+    for (int wd = 0; wd < d.n_words; ++wd) {
+      uint32_t m = w.elig[i * d.n_words + wd];
+      const int lo = i + 1 - 32 * wd;  // keep only j > i
+      if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
+      while (m) {
+        const int j = 32 * wd + __ffs(m) - 1;
+        m &= m - 1;
+        const float4 xj = w.ref[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_ang, 1.f));
+        cl = fmaf(t, t, cl);
+      }
+    }
+  }
+  return warp_sum(cl);
+}
+
+// Rigid start frame: rows of R_o / h and (anchor - origin) / h.
+__device__ __forceinline__ void start_frame(const DockParams &p, int sid, float (&R)[9],
+                                            float (&T)[3]) {
+  const int o = sid / p.n_anchor, a = sid - o * p.n_anchor;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) R[q] = __ldg(p.rot + 9 * o + q);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) T[q] = __ldg(p.anc + 3 * a + q);
+}
+
+// cos/sin of 2 pi k / S (computed in FP64 once, rounded to FP32).
+__device__ __forceinline__ void step_cs(int k, int S, float &c, float &s) {
+  double sd, cd;
+  sincospi(2.0 * (double)k / (double)S, &sd, &cd);
+  c = (float)cd; s = (float)sd;
+}
+
+// Full FP32 score of pose (sid, tors) of the loaded ligand, warp-cooperative,
+// using the map `maps` read in mode MODE (scratch: pose slot `buf`).
+template <int MODE>
+__device__ float full_score(const DockParams &p, const void *maps, const WarpSmem &w, float4 *buf,
+                            const LigDesc &d, int sid, const uint32_t (&tors)[4], int lane) {
+  float R[9], T[3];
+  start_frame(p, sid, R, T);
+  const int ts = type_stride(MODE, p.g);
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 r = w.ref[i];
+    float4 u;
+    u.x = fmaf(R[0], r.x, fmaf(R[1], r.y, fmaf(R[2], r.z, T[0])));
+    u.y = fmaf(R[3], r.x, fmaf(R[4], r.y, fmaf(R[5], r.z, T[1])));
+    u.z = fmaf(R[6], r.x, fmaf(R[7], r.y, fmaf(R[8], r.z, T[2])));
+    u.w = __int_as_float(__float_as_int(r.w) * ts);
+    buf[i] = u;
+  }
+  __syncwarp();
+  for (int b = 0; b < d.n_rot; ++b) {
+    const int kb = (tors[b >> 2] >> (8 * (b & 3))) & 0xff;
+    if (kb % p.S == 0) continue;
+    const BondRec br = w.bonds[b];
+    float nx, ny, nz;
+    const float4 pv = buf[br.v];
+    bond_axis(buf[br.u], pv, nx, ny, nz);
+    float c, s;
+    step_cs(kb % p.S, p.S, c, s);
+    Rot rot;
+    rot.make(c, s, nx, ny, nz, pv.x, pv.y, pv.z);
+    __syncwarp();
+    for (int i = br.v + 1 + lane; i < br.end; i += 32) {
+      float4 q = buf[i];
+      rot.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+      buf[i] = q;
+    }
+    __syncwarp();
+  }
+  float e = 0.f, cl = 0.f;
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 xi = buf[i];
+    e += grid_eval<MODE>(maps, __float_as_int(xi.w), xi.x, xi.y, xi.z, p.g);
+    for (int wd = 0; wd < d.n_words; ++wd) {
+      uint32_t m = w.elig[i * d.n_words + wd];
+      const int lo = i + 1 - 32 * wd;
+      if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
+      while (m) {
+        const int j = 32 * wd + __ffs(m) - 1;
+        m &= m - 1;
+        const float4 xj = buf[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_grid, 1.f));
+        cl = fmaf(t, t, cl);
+      }
+    }
+  }
+  e = warp_sum(e);
+  cl = warp_sum(cl);
+  __syncwarp();
+  return fmaf(p.clash_w, cl, e);
+}
+
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.wmax, p.G),
+                               p.nmax, p.wmax, p.G);
+  const int L = p.L, G = p.G, S = p.S, K = p.K;
+  const int g = lane / L, k = lane - g * L;
+  const int glead = g * L;
+  float4 *pose = w.pose + (size_t)g * (p.nmax + 1);
+  float ck = 1.f, sk = 0.f;
+  if (k < S) step_cs(k, S, ck, sk);
+  const int ts = type_stride(MODE, p.g);
+  const float INF = __int_as_float(0x7f800000);
+
+  int cur = -1;
+  LigDesc d;
+  float clash_ref = 0.f;
+  TopK top;
+
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(p.queue, 1);
+    it = __shfl_sync(FULL, it, 0);
+    if (it >= p.n_items) break;
+    const Item item = p.items[it];
+    if (item.ligand != cur) {
+      __syncwarp();
+      clash_ref = load_ligand(p, w, item.ligand, d, lane);
+      cur = item.ligand;
+    }
+    top.clear();
+
+    for (int s0 = item.s0; s0 < item.s1; s0 += G) {
+      const int sid = min(s0 + g, item.s1 - 1);  // a group past the end repeats the last start
+      // -- rigid start: pose = R_o (x - c) / h + (a - origin) / h
+      float R[9], T[3];
+      start_frame(p, sid, R, T);
+      float e = 0.f;
+      for (int i = k; i < d.n_atoms; i += L) {
+        const float4 r = w.ref[i];
+        float4 u;
+        u.x = fmaf(R[0], r.x, fmaf(R[1], r.y, fmaf(R[2], r.z, T[0])));
+        u.y = fmaf(R[3], r.x, fmaf(R[4], r.y, fmaf(R[5], r.z, T[1])));
+        u.z = fmaf(R[6], r.x, fmaf(R[7], r.y, fmaf(R[8], r.z, T[2])));
+        const int toff = __float_as_int(r.w) * ts;
+        u.w = __int_as_float(toff);
+        pose[i] = u;
+        e += grid_eval<MODE>(p.maps, toff, u.x, u.y, u.z, p.g);
+      }
+      for (int o = L >> 1; o > 0; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
+      float E = fmaf(p.clash_w, clash_ref, e);
+      uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+      __syncwarp();
+
+      // -- greedy torsion sweep
+      for (int b = 0; b < d.n_rot; ++b) {
+        const BondRec br = w.bonds[b];
+        const float4 pv = pose[br.v];
+        float nx, ny, nz;
+        bond_axis(pose[br.u], pv, nx, ny, nz);
+        Rot rot;
+        rot.make(ck, sk, nx, ny, nz, pv.x, pv.y, pv.z);
+        float ag = 0.f, ac = 0.f;
+        for (int i = br.v + 1; i < br.end; ++i) {
+          const float4 q = pose[i];
+          float yx, yy, yz;
+          rot.apply(q.x, q.y, q.z, yx, yy, yz);
+          ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
+          const uint32_t *row = w.elig + i * d.n_words;
+          for (int wd = 0; wd < d.n_words; ++wd) {
+            uint32_t m = row[wd] & br.fixed[wd];
+            while (m) {
+              const int j = 32 * wd + __ffs(m) - 1;
+              m &= m - 1;
+              const float4 f = pose[j];
+              const float dx = yx - f.x, dy = yy - f.y, dz = yz - f.z;
+              const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_grid, 1.f));
+              ac = fmaf(t, t, ac);
+            }
+          }
+        }
+        const float V = (k < S) ? fmaf(p.clash_w, ac, ag) : INF;
+        float best = V;
+        int bk = k;
+        for (int o = L >> 1; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(FULL, best, o);
+          const int okk = __shfl_xor_sync(FULL, bk, o);
+          if (ob < best || (ob == best && okk < bk)) { best = ob; bk = okk; }
+        }
+        const float V0 = __shfl_sync(FULL, V, glead);
+        const float cb = __shfl_sync(FULL, ck, glead + bk);
+        const float sb = __shfl_sync(FULL, sk, glead + bk);
+        E += best - V0;
+        const uint32_t bits = (uint32_t)bk << (8 * (b & 3));
+        switch (b >> 2) { case 0: t0 |= bits; break; case 1: t1 |= bits; break;
+                          case 2: t2 |= bits; break; default: t3 |= bits; }
+        __syncwarp();
+        if (bk != 0) {
+          Rot rb;
+          rb.make(cb, sb, nx, ny, nz, pv.x, pv.y, pv.z);
+          for (int i = br.v + 1 + k; i < br.end; i += L) {
+            float4 q = pose[i];
+            rb.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+            pose[i] = q;
+          }
+        }
+        __syncwarp();
+      }
+
+      // -- candidates of this start group into the warp's top-K
+      for (int gg = 0; gg < G; ++gg) {
+        const int src = gg * L;
+        const float ce = __shfl_sync(FULL, E, src);
+        const uint32_t c0 = __shfl_sync(FULL, t0, src), c1 = __shfl_sync(FULL, t1, src),
+                       c2 = __shfl_sync(FULL, t2, src), c3 = __shfl_sync(FULL, t3, src);
+        if (s0 + gg < item.s1) top.insert(ce, s0 + gg, c0, c1, c2, c3, K, lane);
+      }
+    }
+
+    // -- publish this item's list; the last item of the ligand merges
+    if (lane < K) {
+      PoseOut o;
+      o.score = top.e; o.start_id = top.s;
+      o.tors[0] = top.t0; o.tors[1] = top.t1; o.tors[2] = top.t2; o.tors[3] = top.t3;
+      p.partial[(size_t)item.slot * K + lane] = o;
+    }
+    __threadfence();
+    __syncwarp();
+    int prev = 0;
+    if (lane == 0) prev = atomicAdd(p.done + item.ligand, 1);
+    prev = __shfl_sync(FULL, prev, 0);
+    if (prev != p.lig_items[item.ligand] - 1) continue;
+    __threadfence();
+
+    top.clear();
+    const int slot0 = p.lig_slot0[item.ligand], nit = p.lig_items[item.ligand];
+    for (int c = 0; c < nit; ++c) {
+      const PoseOut *src = p.partial + (size_t)(slot0 + c) * K;
+      float pe = INF;
+      int ps = EMPTY_SID;
+      uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+      if (lane < K) {
+        pe = __ldcg(&src[lane].score); ps = __ldcg(&src[lane].start_id);
+        q0 = __ldcg(&src[lane].tors[0]); q1 = __ldcg(&src[lane].tors[1]);
+        q2 = __ldcg(&src[lane].tors[2]); q3 = __ldcg(&src[lane].tors[3]);
+      }
+      for (int j = 0; j < K; ++j) {
+        const float ce = __shfl_sync(FULL, pe, j);
+        const int cs = __shfl_sync(FULL, ps, j);
+        const uint32_t c0 = __shfl_sync(FULL, q0, j), c1 = __shfl_sync(FULL, q1, j),
+                       c2 = __shfl_sync(FULL, q2, j), c3 = __shfl_sync(FULL, q3, j);
+        if (cs != EMPTY_SID) top.insert(ce, cs, c0, c1, c2, c3, K, lane);
+      }
+    }
+    int rank = lane;
+    if (p.rescore) {
+      for (int j = 0; j < K; ++j) {
+        const int cs = __shfl_sync(FULL, top.s, j);
+        if (cs == EMPTY_SID) break;
+        uint32_t tt[4];
+        tt[0] = __shfl_sync(FULL, top.t0, j); tt[1] = __shfl_sync(FULL, top.t1, j);
+        tt[2] = __shfl_sync(FULL, top.t2, j); tt[3] = __shfl_sync(FULL, top.t3, j);
+        const float en = full_score<MODE_F32_PLAIN>(p, p.maps_f32, w, w.pose, d, cs, tt, lane);
+        if (lane == j) top.e = en;
+      }
+      rank = 0;  // equal keys (empty slots) keep their lane order
+      for (int j = 0; j < K; ++j) {
+        const float oe = __shfl_sync(FULL, top.e, j);
+        const int os = __shfl_sync(FULL, top.s, j);
+        if (pose_less(oe, os, top.e, top.s) || (j < lane && !pose_less(top.e, top.s, oe, os))) ++rank;
+      }
+    }
+    if (lane < K) {
+      PoseOut o;
+      o.score = top.e;
+      o.start_id = top.s == EMPTY_SID ? -1 : top.s;
+      o.tors[0] = top.t0; o.tors[1] = top.t1; o.tors[2] = top.t2; o.tors[3] = top.t3;
+      p.out[(size_t)item.ligand * K + rank] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Explicit poses: one warp per pose.
+template <int MODE>
+__global__ void __launch_bounds__(256) score_poses_kernel(const DockParams p, int n_poses,
+                                                          const int32_t *__restrict__ lig_idx,
+                                                          const int32_t *__restrict__ start_id,
+                                                          const uint8_t *__restrict__ tors,
+                                                          float *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.wmax, 1),
+                               p.nmax, p.wmax, 1);
+  const int pi = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (pi >= n_poses) return;
+  const int li = lig_idx[pi], sid = start_id[pi];
+  if (li < 0 || li >= p.n_ligands || sid < 0 || sid >= p.n_starts) {  // caller's device data
+    if (lane == 0) out[pi] = __int_as_float(0x7fc00000);
+    return;
+  }
+  LigDesc d;
+  (void)load_ligand(p, w, li, d, lane);
+  uint32_t tt[4];
+  for (int q = 0; q < 4; ++q) {
+    const uint8_t *t = tors + (size_t)pi * LIGATE_MAX_ROT + 4 * q;
+    tt[q] = (uint32_t)t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
+  }
+  const float e = full_score<MODE>(p, p.maps, w, w.pose, d, sid, tt, lane);
+  if (lane == 0) out[pi] = e;
+}
+
+// ---------------------------------------------------------------------------
+// Start frames: rotation of each orientation quaternion (normalised, rows
+// re-orthonormalised by Gram-Schmidt in FP32) scaled by 1/h, and anchors in
+// grid units.
+__global__ void start_frames_kernel(const float4 *__restrict__ quat, int n_orient,
+                                    const float *__restrict__ anchors, int n_anchor, float ox,
+                                    float oy, float oz, float inv_h, float *__restrict__ rot,
+                                    float *__restrict__ anc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_orient) {
+    float4 q = quat[i];
+    const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+    float r0[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)};
+    float r1[3] = {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)};
+    float n0 = rsqrtf(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+    for (int a = 0; a < 3; ++a) r0[a] *= n0;
+    const float dp = r0[0] * r1[0] + r0[1] * r1[1] + r0[2] * r1[2];
+    for (int a = 0; a < 3; ++a) r1[a] -= dp * r0[a];
+    const float n1 = rsqrtf(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+    for (int a = 0; a < 3; ++a) r1[a] *= n1;
+    const float r2[3] = {r0[1] * r1[2] - r0[2] * r1[1], r0[2] * r1[0] - r0[0] * r1[2],
+                         r0[0] * r1[1] - r0[1] * r1[0]};
+    for (int a = 0; a < 3; ++a) {
+      rot[9 * i + a] = r0[a] * inv_h;
+      rot[9 * i + 3 + a] = r1[a] * inv_h;
+      rot[9 * i + 6 + a] = r2[a] * inv_h;
+    }
+  }
+  if (i < n_anchor) {
+    anc[3 * i] = (anchors[3 * i] - ox) * inv_h;
+    anc[3 * i + 1] = (anchors[3 * i + 1] - oy) * inv_h;
+    anc[3 * i + 2] = (anchors[3 * i + 2] - oz) * inv_h;
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int MODE>
+static cudaError_t launch_dock_t(const DockParams &p, int grid, int block, size_t smem,
+                                 cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(dock_kernel<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dock_kernel<MODE><<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dock(int mode, const DockParams &p, int grid, int block, size_t smem,
+                        cudaStream_t s) {
+  switch (mode) {
+    case MODE_F32_PLAIN: return launch_dock_t<MODE_F32_PLAIN>(p, grid, block, smem, s);
+    case MODE_F32_CORNER: return launch_dock_t<MODE_F32_CORNER>(p, grid, block, smem, s);
+    case MODE_BF16_CORNER: return launch_dock_t<MODE_BF16_CORNER>(p, grid, block, smem, s);
+    default: return launch_dock_t<MODE_F16_CORNER>(p, grid, block, smem, s);
+  }
+}
+
+int dock_kernel_max_ctas_per_sm(int mode, int block, size_t smem) {
+  int n = 0;
+  const void *f = mode == MODE_F32_PLAIN ? (const void *)dock_kernel<MODE_F32_PLAIN>
+                : mode == MODE_F32_CORNER ? (const void *)dock_kernel<MODE_F32_CORNER>
+                : mode == MODE_BF16_CORNER ? (const void *)dock_kernel<MODE_BF16_CORNER>
+                : (const void *)dock_kernel<MODE_F16_CORNER>;
+  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_start_frames(const double *, const float *quat_f32_dev, int n_orient,
+                                const float *anchors_dev, int n_anchor, const double origin[3],
+                                double h, float *rot_out, float *anc_out, cudaStream_t s) {
+  const int n = n_orient > n_anchor ? n_orient : n_anchor;
+  start_frames_kernel<<<(n + 127) / 128, 128, 0, s>>>(
+      reinterpret_cast<const float4 *>(quat_f32_dev), n_orient, anchors_dev, n_anchor,
+      (float)origin[0], (float)origin[1], (float)origin[2], (float)(1.0 / h), rot_out, anc_out);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_score_t(const DockParams &p, int n_poses, const int32_t *lig_idx,
+                                  const int32_t *start_id, const uint8_t *tors, float *out,
+                                  cudaStream_t s) {
+  const int warps = 4;
+  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, p.wmax, 1);
+  cudaError_t e = cudaFuncSetAttribute(score_poses_kernel<MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  score_poses_kernel<MODE><<<(n_poses + warps - 1) / warps, 32 * warps, smem, s>>>(
+      p, n_poses, lig_idx, start_id, tors, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_score_poses(int mode, const DockParams &p, int n_poses, const int32_t *lig_idx,
+                               const int32_t *start_id, const uint8_t *tors, float *out,
+                               cudaStream_t s) {
+  if (n_poses <= 0) return cudaSuccess;
+  switch (mode) {
+    case MODE_F32_PLAIN: return launch_score_t<MODE_F32_PLAIN>(p, n_poses, lig_idx, start_id, tors, out, s);
+    case MODE_F32_CORNER: return launch_score_t<MODE_F32_CORNER>(p, n_poses, lig_idx, start_id, tors, out, s);
+    case MODE_BF16_CORNER: return launch_score_t<MODE_BF16_CORNER>(p, n_poses, lig_idx, start_id, tors, out, s);
+    default: return launch_score_t<MODE_F16_CORNER>(p, n_poses, lig_idx, start_id, tors, out, s);
+  }
+}
+
+}  // namespace ligate

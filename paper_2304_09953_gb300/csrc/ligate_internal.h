@@ -1,0 +1,167 @@
+// Internal declarations shared by the library's translation units.
+// Device data layouts of the packed ligand batch, the pocket and the
+// docking run, plus the host-side launch wrappers the C ABI calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ligate.h"
+
+namespace ligate {
+
+// ---------------------------------------------------------------------------
+// Packed ligand batch (device).  Atoms of each ligand are renumbered in DFS
+// pre-order from atom 0 (children by ascending input index), so the subtree
+// moved by rotatable bond (u, v) is the contiguous range [v, end).
+struct LigDesc {
+  int atom_base;   // first atom in `atoms`
+  int n_atoms;
+  int n_rot;       // rotatable bonds, in sweep order at bond_base
+  int bond_base;   // first record in `bonds`
+  int elig_base;   // first word of the n_atoms x n_words clash-pair bit matrix
+  int n_words;     // (n_atoms + 31) / 32
+  int n_orig_rot;  // rotatable flags in the input (== n_rot)
+  int pad;
+};
+
+// One rotatable bond: u (fixed-side atom), v (child atom), end (one past the
+// subtree of v), and the "fixed side" mask (atoms outside [v, end) and != u)
+// over up to 4 words of 32 atoms.
+struct BondRec {
+  int u, v, end, pad;
+  uint32_t fixed[4];
+};
+
+struct BatchDev {
+  int n_ligands = 0;
+  int max_atoms = 0;
+  int max_rot = 0;
+  int64_t total_atoms = 0;
+  LigDesc *lig = nullptr;    // [n_ligands]
+  float4 *atoms = nullptr;   // [total_atoms] (x, y, z, type as int bits) DFS order
+  BondRec *bonds = nullptr;  // [total_rot]
+  uint32_t *elig = nullptr;  // clash-pair masks (topological distance >= 4)
+  // host copies used for planning
+  std::vector<LigDesc> h_lig;
+  std::vector<BondRec> h_bonds;
+  std::vector<uint32_t> h_elig;
+  std::vector<uint8_t> h_types;   // per atom, DFS order
+  std::vector<int32_t> h_rot;     // realised rotatable count per ligand
+};
+
+// ---------------------------------------------------------------------------
+struct PocketDev {
+  int n_types = 0, nx = 0, ny = 0, nz = 0;
+  double origin[3] = {0, 0, 0};
+  double spacing = 0;
+  int n_anchors = 0;
+  float *anchors = nullptr;        // device [n_anchors][3] Angstrom
+  std::vector<float> h_anchors;
+  float *map_f32 = nullptr;        // plain [T][nz][ny][nx]
+  float *map_f32c = nullptr;       // corner [T][cells][8]
+  uint16_t *map_bf16c = nullptr;   // corner [T][cells][8]
+  uint16_t *map_f16c = nullptr;    // corner [T][cells][8]
+  size_t n_nodes() const { return (size_t)nx * ny * nz; }
+  size_t n_cells() const { return (size_t)(nx - 1) * (ny - 1) * (nz - 1); }
+};
+
+// Map-read modes of the docking kernel.
+enum MapMode { MODE_F32_PLAIN = 0, MODE_F32_CORNER = 1, MODE_BF16_CORNER = 2, MODE_F16_CORNER = 3 };
+
+// Geometry constants of one run (grid units: u = (x - origin) / h).
+struct GridConst {
+  int nx, ny, nz;
+  float fx1, fy1, fz1;  // n - 1 as float (inclusive upper bound)
+  float penalty;
+};
+
+// One result slot in device memory (same bytes as ligate_pose).
+struct PoseOut {
+  float score;
+  int32_t start_id;
+  uint32_t tors[4];
+};
+static_assert(sizeof(PoseOut) == sizeof(ligate_pose), "pose layout");
+
+// Work item: ligand, start range, slot of its partial top-K list.
+struct Item {
+  int ligand;
+  int s0, s1;
+  int slot;
+};
+
+struct DockParams {
+  // batch
+  const LigDesc *lig;
+  const float4 *atoms;
+  const BondRec *bonds;
+  const uint32_t *elig;
+  int n_ligands;
+  // pocket
+  const void *maps;        // map read by the sweep (mode)
+  const float *maps_f32;   // FP32 map for rescoring (plain)
+  GridConst g;
+  // start frames
+  const float *rot;        // [n_orient][9] rotation / h (grid units)
+  const float *anc;        // [n_anchor][3] (anchor - origin) / h
+  int n_anchor;
+  int n_starts;
+  // sampling
+  int S, L, G;             // torsion steps, lanes per start (pow2 >= S), groups per warp
+  int K;
+  float clash_w;
+  float inv_dc2_grid;      // h^2 / d_c^2
+  float inv_dc2_ang;       // 1 / d_c^2
+  int rescore;
+  // work queue
+  const Item *items;
+  int n_items;
+  const int *lig_items;    // [n_ligands] items per ligand
+  const int *lig_slot0;    // [n_ligands] first partial slot of each ligand
+  int *queue;              // [1] next item
+  int *done;               // [n_ligands] finished items per ligand
+  PoseOut *partial;        // [n_items][K]
+  PoseOut *out;            // [n_ligands][K]
+  // shared-memory shape
+  int nmax;                // atoms capacity per warp slot (multiple of 32)
+  int wmax;                // words per clash-mask row
+};
+
+// Host launch wrappers (dock.cu).
+size_t dock_smem_per_warp(int nmax, int G);
+cudaError_t launch_dock(int mode, const DockParams &p, int grid, int block, size_t smem,
+                        cudaStream_t s);
+cudaError_t launch_start_frames(const double *quat_unused, const float *quat_f32_dev,
+                                int n_orient, const float *anchors_dev, int n_anchor,
+                                const double origin[3], double h, float *rot_out,
+                                float *anc_out, cudaStream_t s);
+cudaError_t launch_score_poses(int mode, const DockParams &p, int n_poses, const int32_t *lig_idx,
+                               const int32_t *start_id, const uint8_t *tors, float *out,
+                               cudaStream_t s);
+int dock_kernel_max_ctas_per_sm(int mode, int block, size_t smem);
+
+// Pocket kernels (pocket.cu).
+cudaError_t launch_corner_pack(const float *plain, int n_types, int nx, int ny, int nz,
+                               int out_kind, void *out, cudaStream_t s);
+
+// Descriptor + surrogate kernels (surrogate.cu): declared there.
+
+// Error helpers (api.cu).
+void set_error(const char *fmt, ...);
+ligate_status cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace ligate
+
+// Opaque handles of the C ABI.
+struct ligate_pocket {
+  ligate::PocketDev d;
+};
+struct ligate_batch {
+  ligate::BatchDev d;
+  int max_type = 0;
+};
+

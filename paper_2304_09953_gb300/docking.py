@@ -1,0 +1,92 @@
+"""Convenience layer over the C ABI: RAII wrappers for pockets, batches and
+plans, returning numpy structured arrays of poses.  No computation here."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import native as N
+
+
+class PocketHandle:
+    def __init__(self, pocket, mask=N.LIGATE_POCKET_FP32_CORNER | N.LIGATE_POCKET_BF16_CORNER
+                 | N.LIGATE_POCKET_FP16_CORNER):
+        self.h = N.ligate_pocket_create(pocket.maps, pocket.origin, pocket.spacing, pocket.anchors, mask)
+
+    def close(self):
+        if self.h:
+            N.ligate_pocket_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+class BatchHandle:
+    def __init__(self, ligands):
+        self.n = ligands.n
+        self.h = N.ligate_batch_create(ligands)
+
+    def close(self):
+        if self.h:
+            N.ligate_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+MODES = {
+    "fp32": (N.LIGATE_FP32, N.LIGATE_LAYOUT_PLAIN),
+    "fp32c": (N.LIGATE_FP32, N.LIGATE_LAYOUT_CORNER),
+    "bf16": (N.LIGATE_BF16, N.LIGATE_LAYOUT_CORNER),
+    "fp16": (N.LIGATE_FP16, N.LIGATE_LAYOUT_CORNER),
+}
+
+
+class Plan:
+    def __init__(self, pocket: PocketHandle, batch: BatchHandle, sampling, mode="fp32", rescore=None,
+                 tile=None, top_k=None):
+        prec, layout = MODES[mode]
+        if rescore is None:
+            rescore = prec != N.LIGATE_FP32
+        self.s = N.make_sampling(sampling, prec, layout, rescore, top_k)
+        self.k = self.s.top_k
+        self.n = batch.n
+        self._refs = (pocket, batch)
+        self.h = N.ligate_plan_create(pocket.h, batch.h, self.s, tile)
+
+    def run(self, stream=None):
+        N.ligate_plan_run(self.h, None, stream)
+
+    def result(self, stream=None) -> np.ndarray:
+        out = np.zeros((self.n, self.k), N.POSE_DTYPE)
+        N.ligate_plan_run(self.h, out, stream)
+        return out
+
+    def device_output(self) -> int:
+        """Device address of the last run's ligate_pose[n][K] result."""
+        return N.ligate_plan_output(self.h)
+
+    def tile(self):
+        return N.ligate_plan_get_tile(self.h)
+
+    def work(self):
+        return N.ligate_plan_work(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.ligate_plan_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
+def dock(pocket, ligands, sampling, mode="fp32", rescore=None, tile=None, top_k=None):
+    """One-shot docking of a workload on the current CUDA device."""
+    ph = PocketHandle(pocket)
+    bh = BatchHandle(ligands)
+    pl = Plan(ph, bh, sampling, mode, rescore, tile, top_k)
+    try:
+        return pl.result()
+    finally:
+        pl.close()
+        bh.close()
+        ph.close()

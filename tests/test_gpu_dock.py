@@ -1,0 +1,153 @@
+"""GPU docking path vs the FP64 oracle, through the C ABI.
+
+FP32 maps: every reported pose within 1e-4 relative of its FP64 score, each
+greedy step optimal within that tolerance along the GPU's own path, and the
+top-K list equal to the oracle's except where a near-tie explains a
+difference (see tests/parity.py).  Sizes: the 1-ligand configuration, the
+first 64 ligands of the 10,000-ligand library, and the full library in the
+launch configuration the benchmark times (sampled ligands checked)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_09953_gb300 import docking as D
+from paper_2304_09953_gb300 import native as N
+from paper_2304_09953_gb300.workload import Sampling, make_ligands, make_workload
+from tests.parity import compare_ligand, near_tie_starts, path_check, tol
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def full():
+    return make_workload("batched")
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp32c"])
+def test_tiny_matches_oracle(tiny, mode):
+    res = D.dock(tiny.pocket, tiny.ligands, tiny.sampling, mode=mode)
+    info = compare_ligand(tiny.ligands.ligand(0), tiny.pocket, tiny.sampling, res[0])
+    assert abs(info["gpu_best"] - info["oracle_best"]) <= tol(info["oracle_best"])
+
+
+def test_every_start_matches_oracle(tiny):
+    """32 starts with K = 32: the GPU returns every start; each start's
+    torsion path equals the oracle's unless the oracle path has a near-tie,
+    and every score is within tolerance."""
+    lig = tiny.ligands.ligand(0)
+    for sub in range(4):
+        samp = Sampling(tiny.sampling.quats[4 * sub:4 * sub + 4], 8, 8, 32)
+        res = D.dock(tiny.pocket, tiny.ligands, samp, mode="fp32")[0]
+        assert np.all(res["start_id"] >= 0)
+        e, tors, tr = oracle.greedy(lig, tiny.pocket, samp, trials=True)
+        ties = near_tie_starts(tr)
+        s = res["start_id"]
+        R = tors.shape[1]
+        same = np.array([np.array_equal(res["tors"][j, :R], tors[s[j]]) for j in range(32)])
+        assert np.all(same | ties[s])
+        ok = np.abs(res["score"] - e[s]) <= tol(e[s])
+        assert np.all(ok | ties[s])
+        path_check(lig, tiny.pocket, samp, s, res["tors"], res["score"])
+
+
+def test_first_64_ligands(batched_small):
+    w = batched_small
+    res = D.dock(w.pocket, w.ligands, w.sampling, mode="fp32")
+    for i in range(0, w.ligands.n, 4):
+        compare_ligand(w.ligands.ligand(i), w.pocket, w.sampling, res[i])
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+@pytest.mark.parametrize("mode,limit", [("fp32", None), ("fp32c", None), ("bf16", 0.5), ("fp16", 0.1)])
+def test_explicit_pose_scores(batched_small, mode, limit):
+    """ligate_score_poses on random (ligand, start, torsions) vs FP64."""
+    w = batched_small
+    rng = np.random.default_rng(7)
+    n = 600
+    li = rng.integers(0, w.ligands.n, n).astype(np.int32)
+    st = rng.integers(0, w.sampling.n_starts, n).astype(np.int32)
+    tors = rng.integers(0, w.sampling.torsion_steps, (n, 16)).astype(np.uint8)
+    for j in range(n):
+        tors[j, w.ligands.n_rot[li[j]]:] = 0
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    prec, layout = D.MODES[mode]
+    s = N.make_sampling(w.sampling, prec, layout)
+    out = torch.zeros(n, dtype=torch.float32, device="cuda")
+    N.ligate_score_poses(ph.h, bh.h, s, n, _dev(li, torch.int32), _dev(st, torch.int32),
+                         _dev(tors, torch.uint8), out)
+    got = out.cpu().numpy().astype(np.float64)
+    want = np.array([oracle.score_poses(w.ligands.ligand(int(li[j])), w.pocket, w.sampling, [st[j]],
+                                        tors[j:j + 1, :w.ligands.n_rot[li[j]]])[0] for j in range(n)])
+    err = np.abs(got - want)
+    if limit is None:
+        assert np.all(err <= tol(want)), err.max()
+    else:
+        assert err.max() <= limit, err.max()
+
+
+def test_full_library_bench_configuration(full):
+    """All 10,000 ligands in one persistent launch (default tile), 24 seeded
+    ligands checked in full against the oracle."""
+    res = D.dock(full.pocket, full.ligands, full.sampling, mode="fp32")
+    assert res.shape == (10000, 16)
+    assert np.all(res["start_id"] >= 0)
+    rng = np.random.default_rng(1234)
+    for i in rng.choice(full.ligands.n, 24, replace=False):
+        compare_ligand(full.ligands.ligand(int(i)), full.pocket, full.sampling, res[i])
+
+
+def test_tile_shapes_give_identical_results(full):
+    sub = make_workload("batched", n_ligands=300, pocket=full.pocket)
+    a = D.dock(sub.pocket, sub.ligands, sub.sampling, mode="fp32c")
+    t = N.ligate_tile()
+    t.warps_per_cta = 4
+    for b in range(N.LIGATE_N_BUCKETS):
+        t.starts_per_item[b] = 96 + 32 * b
+    b_ = D.dock(sub.pocket, sub.ligands, sub.sampling, mode="fp32c", tile=t)
+    assert np.array_equal(a, b_)
+
+
+def test_edge_cases(tiny):
+    P = tiny.pocket
+    # empty batch
+    empty = make_workload("tiny", n_ligands=0, pocket=P)
+    r = D.dock(P, empty.ligands, tiny.sampling)
+    assert r.shape == (0, 4)
+    # 1 and 2 atoms, R = 0, and K larger than the number of starts
+    ligs = make_ligands(21, np.array([1, 2, 9], np.int32), np.array([0, 0, 0], np.int32), 6)
+    samp = Sampling(tiny.sampling.quats[:2], 2, 8, 8)
+    r = D.dock(P, ligs, samp)
+    for i in range(3):
+        assert np.all(r[i, :4]["start_id"] >= 0) and np.all(r[i, 4:]["start_id"] == -1)
+        assert np.all(np.isinf(r[i, 4:]["score"]))
+        compare_ligand(ligs.ligand(i), P, samp, r[i], K=8)
+
+
+@pytest.mark.parametrize("S", [1, 3, 32])
+def test_torsion_step_counts(tiny, S):
+    samp = Sampling(tiny.sampling.quats[:8], 4, S, 6)
+    r = D.dock(tiny.pocket, tiny.ligands, samp)
+    compare_ligand(tiny.ligands.ligand(0), tiny.pocket, samp, r[0])
+
+
+def test_largest_ligands():
+    """128 atoms and 16 rotatable bonds, the library limits."""
+    w = make_workload("tiny", n_ligands=0)
+    big = make_ligands(5, np.array([128, 100], np.int32), np.array([16, 16], np.int32), 6)
+    assert big.n_rot.max() == 16
+    maps = np.zeros((6, 80, 80, 80), np.float32)
+    maps += w.pocket.maps.mean()
+    from paper_2304_09953_gb300.workload import Pocket
+    rng = np.random.default_rng(0)
+    maps = (maps + rng.normal(size=maps.shape).astype(np.float32)).astype(np.float32)
+    P = Pocket(maps, np.zeros(3), 0.5, np.array([[19.75, 19.75, 19.75]], np.float32))
+    samp = Sampling(tiny.sampling.quats[:4], 1, 4, 4)
+    r = D.dock(P, big, samp)
+    for i in range(2):
+        compare_ligand(big.ligand(i), P, samp, r[i])
