@@ -69,7 +69,7 @@ def _load():
         lib.or_trilinear.argtypes = [P, D, I, I, P, P]
         lib.or_trilinear.restype = None
         lib.or_score_coords.argtypes = [P, P, P, P, P]
-        lib.or_score_poses.argtypes = [P, P, P, I, P, P, I, P]
+        lib.or_score_poses.argtypes = [P, P, P, I, P, P, I, P, P]
         lib.or_greedy.argtypes = [P, P, P, I, P, P, P, I, P]
         lib.or_exhaustive.argtypes = [P, P, P, I, P, P]
         lib.or_descriptor.argtypes = [P, I, P]
@@ -198,7 +198,9 @@ def score_coords(lig, pocket, sampling, coords) -> float:
     return out.value
 
 
-def score_poses(lig, pocket, sampling, starts, tors) -> np.ndarray:
+def score_poses(lig, pocket, sampling, starts, tors, with_scale: bool = False):
+    """FP64 scores of (start, tors) poses; with ``with_scale`` also each
+    score's sum of absolute term values (the scale of its rounding error)."""
     lib = _load()
     k = _Keep()
     L = _lig(k, *lig)
@@ -209,9 +211,10 @@ def score_poses(lig, pocket, sampling, starts, tors) -> np.ndarray:
     if tors.shape[1] == 0:
         tors = np.zeros((len(starts), 1), np.int32)
     out = np.zeros(len(starts))
+    mag = np.zeros(len(starts))
     lib.or_score_poses(_ref(L), _ref(P), _ref(S), len(starts), starts.ctypes.data,
-                       tors.ctypes.data, tors.shape[1], out.ctypes.data)
-    return out
+                       tors.ctypes.data, tors.shape[1], out.ctypes.data, mag.ctypes.data)
+    return (out, mag) if with_scale else out
 
 
 def greedy(lig, pocket, sampling, starts=None, trials: bool = False):

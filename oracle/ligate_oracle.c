@@ -257,10 +257,17 @@ typedef struct {
   int min_sep;   /* pairs at least this many bonds apart */
 } or_clash;
 
-static double score_coords(const or_lig *L, const or_pocket *P, const or_clash *C,
-                           double (*x)[3]) {
-  double e = 0.0;
-  for (int a = 0; a < L->n; ++a) e += trilinear(P, L->type[a], x[a]);
+/* Score of coordinates x; *mag (optional) receives the sum of the absolute
+ * values of its terms, the scale against which rounding error of the sum is
+ * measured. */
+static double score_coords_mag(const or_lig *L, const or_pocket *P, const or_clash *C,
+                               double (*x)[3], double *mag) {
+  double e = 0.0, m = 0.0;
+  for (int a = 0; a < L->n; ++a) {
+    double g = trilinear(P, L->type[a], x[a]);
+    e += g;
+    m += fabs(g);
+  }
   double cl = 0.0, inv = 1.0 / (C->dc * C->dc);
   for (int i = 0; i < L->n; ++i)
     for (int j = i + 1; j < L->n; ++j) {
@@ -269,7 +276,13 @@ static double score_coords(const or_lig *L, const or_pocket *P, const or_clash *
       double t = 1.0 - (dx * dx + dy * dy + dz * dz) * inv;
       if (t > 0.0) cl += t * t;
     }
+  if (mag) *mag = m + fabs(C->w) * cl;
   return e + C->w * cl;
+}
+
+static double score_coords(const or_lig *L, const or_pocket *P, const or_clash *C,
+                           double (*x)[3]) {
+  return score_coords_mag(L, P, C, x, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -388,10 +401,11 @@ OR_EXPORT int or_score_coords(const or_ligand_in *li, const or_pocket_in *pi, co
   return 0;
 }
 
-/* Scores of n_poses (start, tors) poses, parallel over poses. */
+/* Scores of n_poses (start, tors) poses, parallel over poses; mag_out
+ * (optional) receives each score's sum of absolute term values. */
 OR_EXPORT int or_score_poses(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
                              int n_poses, const int *starts, const int *tors, int tors_stride,
-                             double *out) {
+                             double *out, double *mag_out) {
   or_lig L;
   if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
   or_pocket P;
@@ -405,7 +419,7 @@ OR_EXPORT int or_score_poses(const or_ligand_in *li, const or_pocket_in *pi, con
       double R[9], anc[3];
       start_frame(sp, starts[p], R, anc);
       build_pose(&L, R, anc, tors + (size_t)p * tors_stride, sp->S, x);
-      out[p] = score_coords(&L, &P, &C, x);
+      out[p] = score_coords_mag(&L, &P, &C, x, mag_out ? mag_out + p : NULL);
     }
     free(x);
   }
