@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Ligand docking throughput on GB300: ligands docked/s and poses scored/s.
+
+One step = one docking pass of the whole batch (10,000 seeded synthetic
+ligands, 15-60 heavy atoms, 0-12 rotatable bonds, 8 x 64^3 grid maps at
+0.375 A, 256 orientations x 32 anchors x 16 torsion steps, top-16) through
+the library's persistent, CUDA-graph-captured docking plan.  Two forms:
+  chosen : BF16 corner-packed maps, autotuned tile, FP32 rescoring of the
+           top-16 poses (the reported value);
+  plain  : FP32 maps, default tile, no rescoring.
+Inputs are resident in HBM before the timed region; L2 is flushed (256 MB
+write) between timed steps.  `e2e` times the host-array C-ABI call
+ligate_dock_batch (packing, upload, docking, download) per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank docks its own 10,000-ligand slice of the library
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ligands docked/s & poses scored/s on 1 GB300, chosen vs plain form at stated error"
+WORKLOAD = ("batched: 10000 ligands (N~U{15..60}, R~U{0..12}), 8x64^3 maps @0.375 A, "
+            "256 orient x 32 anchors x S=16, top-16")
+# Algorithmic FP32 operations (FMA = 2) per unit of work, see the design doc:
+#   atom interpolation: 9 FMA rotation + 3 fraction subs + 7 lerps (sub + FMA) + 1 add = 43
+#   clash pair: 3 subs + (mul + 2 FMA) + FMA + FMA = 12
+FLOP_PER_ATOM_EVAL = 43.0
+FLOP_PER_PAIR_EVAL = 12.0
+
+
+def fp32_peak_tflops(sms=152, lanes=128, mhz=2070.0):
+    return sms * lanes * 2 * mhz * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-ligands", type=int, default=10000)
+    ap.add_argument("--tune-budget-ms", type=float, default=20000.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default tile instead of the autotuner")
+    ap.add_argument("--cpu-sample", type=int, default=48)
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(w, n_sample):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample."""
+    import oracle
+    sub = list(range(min(n_sample, w.ligands.n)))
+    t0 = time.perf_counter()
+    poses = 0.0
+    for i in sub:
+        oracle.dock_ligand(w.ligands.ligand(i), w.pocket, w.sampling)
+        poses += w.sampling.n_starts * (1 + int(w.ligands.n_rot[i]) * (w.sampling.torsion_steps - 1))
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": len(sub) / dt, "unit": "ligands/s", "poses_per_s": poses / dt, "cores": cores,
+            "kind": "oracle", "sample": f"first {len(sub)} ligands of the batched library, full "
+            f"{w.sampling.n_starts} starts each, FP64 C + OpenMP"}, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2304_09953_gb300.workload import make_workload
+    w = make_workload("batched", n_ligands=args.n_ligands)
+    per_step = 12
+    for _ in range(args.warmup):
+        cpu_baseline(make_workload("batched", n_ligands=per_step, pocket=w.pocket), per_step)
+    times, vals, pps = [], [], []
+    for k in range(args.steps):
+        sub = make_workload("batched", n_ligands=per_step, first_index=k * per_step, pocket=w.pocket)
+        cb, dt = cpu_baseline(sub, per_step)
+        times.append(dt)
+        vals.append(cb["value"])
+        pps.append(cb["poses_per_s"])
+    value = per_step * len(times) / sum(times)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle",
+                                            "sample_per_step": f"{per_step} ligands"},
+            "poses_per_s": per_step * 0 + float(np.mean(pps)),
+            "cpu_baseline": {"value": value, "unit": "ligands/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} ligands per step, full sampling"},
+            "e2e": {"value": value, "unit": "ligands/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_2304_09953_gb300 import build as B
+    B.build()
+    from paper_2304_09953_gb300 import docking as D
+    from paper_2304_09953_gb300 import native as N
+    from paper_2304_09953_gb300.workload import make_workload
+
+    w = make_workload("batched", n_ligands=args.n_ligands, first_index=rank * args.n_ligands)
+    tune_path = os.path.join(tempfile.gettempdir(), f"ligate_tune_{os.getpid()}.txt")
+    os.environ["LIGATE_TUNE_CACHE"] = tune_path
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    s_chosen = N.make_sampling(w.sampling, N.LIGATE_BF16, N.LIGATE_LAYOUT_CORNER, rescore=True)
+    t0 = time.perf_counter()
+    tile = None if args.no_tune else N.ligate_autotune(ph.h, bh.h, s_chosen, args.tune_budget_ms)
+    tune_s = time.perf_counter() - t0
+    chosen = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile)
+    plain = D.Plan(ph, bh, w.sampling, mode="fp32", rescore=False)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(plan, steps):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            N.ligate_plan_run(plan.h, None, sh)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    for _ in range(args.warmup):
+        N.ligate_plan_run(chosen.h, None, sh)
+        N.ligate_plan_run(plain.h, None, sh)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms_chosen = timed(chosen, args.steps)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    ms_plain = timed(plain, args.steps)
+    torch.cuda.synchronize()
+    t_chosen = sum(ms_chosen) / 1000.0
+    if ws > 1:
+        t = torch.tensor([t_chosen], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_chosen = float(t.item())
+    work = chosen.work()
+    work_plain = plain.work()
+    n_lig = args.n_ligands
+    value = ws * n_lig * args.steps / t_chosen
+    poses_s = ws * work.poses * args.steps / t_chosen
+    mean_ms = t_chosen * 1000 / args.steps
+    flops = work.atom_evals * FLOP_PER_ATOM_EVAL + work.pair_evals * FLOP_PER_PAIR_EVAL
+    achieved = flops / (mean_ms / 1000) / 1e12
+    peak = fp32_peak_tflops()
+    plain_ms = sum(ms_plain) / len(ms_plain)
+    plain_flops = work_plain.atom_evals * FLOP_PER_ATOM_EVAL + work_plain.pair_evals * FLOP_PER_PAIR_EVAL
+
+    # end to end through the host-array C-ABI call
+    e2e = None
+    if not args.no_e2e:
+        lig = w.ligands
+        out = np.zeros((n_lig, w.sampling.top_k), N.POSE_DTYPE)
+        h2d = sum(a.nbytes for a in (lig.atom_offset, lig.xyz, lig.type, lig.bond_offset, lig.bonds,
+                                     lig.rotatable))
+        h2d += w.sampling.quats.nbytes
+        N.ligate_dock_batch(ph.h, lig, s_chosen, out, sh)  # warm
+        et = []
+        for _ in range(max(1, min(args.steps, 3))):
+            t0 = time.perf_counter()
+            N.ligate_dock_batch(ph.h, lig, s_chosen, out, sh)
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": ws * n_lig / statistics.mean(et), "unit": "ligands/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes),
+               "ms_per_step": 1000 * statistics.mean(et)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, _ = cpu_baseline(w, args.cpu_sample)
+    t_, launches_per_run = chosen.tile()
+    line = {
+        "metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "chosen: bf16 corner maps + autotuned tile + fp32 top-16 rescore",
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "tile": {"warps_per_cta": t_.warps_per_cta, "ctas_per_sm": t_.ctas_per_sm,
+                            "starts_per_item": list(t_.starts_per_item)},
+                   "autotune_s": round(tune_s, 2), "parallelism": f"replicas x{ws}"},
+        "poses_per_s": poses_s,
+        "plain": {"value": ws * n_lig / (plain_ms / 1000), "unit": "ligands/s",
+                  "poses_per_s": ws * work_plain.poses / (plain_ms / 1000), "ms_per_step": plain_ms,
+                  "form": "fp32 plain maps, default tile, no rescore",
+                  "roofline_frac": plain_flops / (plain_ms / 1000) / 1e12 / peak},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                     "kernel": "dock_kernel<BF16_CORNER>",
+                     "work_per_launch": {"atom_evals": work.atom_evals, "pair_evals": work.pair_evals,
+                                         "poses": work.poses}},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
+        "gpu_launches": launches_per_run * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p in (chosen, plain):
+        p.close()
+    bh.close()
+    ph.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

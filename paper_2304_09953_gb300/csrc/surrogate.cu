@@ -4,7 +4,11 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "ligate_internal.h"
+#include "mlp.h"
 
 namespace ligate {
 
@@ -74,38 +78,309 @@ extern "C" ligate_status ligate_descriptors(const ligate_batch *b, float *out, v
   return LIGATE_OK;
 }
 
-// --- surrogate network: see mlp kernels below -------------------------------
+// ---------------------------------------------------------------------------
+// Surrogate network object: FP32 master weights + Adam moments, BF16 copy
+// for the tensor cores, standardisation statistics, activation workspace.
+namespace {
+
+constexpr int F0 = 256, F1 = 512;
+// offsets of W1, b1, W2, b2, W3, b3, W4, b4 in the flat parameter vector
+constexpr int OW1 = 0, OB1 = OW1 + F0 * F1, OW2 = OB1 + F1, OB2 = OW2 + F1 * F1, OW3 = OB2 + F1,
+              OB3 = OW3 + F1 * F1, OW4 = OB3 + F1, OB4 = OW4 + F1, NPAR = OB4 + 1;
+static_assert(NPAR == LIGATE_SURROGATE_PARAMS, "parameter count");
+
+uint64_t sm64(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+double u01(uint64_t &s) { return (double)(sm64(s) >> 11) * 0x1.0p-53; }
+
+}  // namespace
+
 struct ligate_surrogate {
-  int dummy;
+  float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+  __nv_bfloat16 *wb = nullptr;
+  float *mu = nullptr, *inv_sd = nullptr;
+  double *lstat = nullptr, *sse = nullptr;
+  double label_mu = 0.0, label_sd = 1.0;
+  bool stats = false;
+  long long step = 0;
+  int cap = 0;
+  __nv_bfloat16 *x = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
+  __nv_bfloat16 *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
+  float *t = nullptr, *y = nullptr, *dy = nullptr;
+  int *idx = nullptr;
+  int idx_cap = 0;
 };
 
-extern "C" ligate_status ligate_surrogate_create(const float *, uint64_t, ligate_surrogate **out) {
-  if (out) *out = nullptr;
-  set_error("surrogate: not built yet");
-  return LIGATE_ERR_UNSUPPORTED;
+namespace {
+
+void free_work(ligate_surrogate *s) {
+  cudaFree(s->x); cudaFree(s->h1); cudaFree(s->h2); cudaFree(s->h3);
+  cudaFree(s->dz1); cudaFree(s->dz2); cudaFree(s->dz3);
+  cudaFree(s->t); cudaFree(s->y); cudaFree(s->dy);
+  s->x = s->h1 = s->h2 = s->h3 = s->dz1 = s->dz2 = s->dz3 = nullptr;
+  s->t = s->y = s->dy = nullptr;
+  s->cap = 0;
 }
-extern "C" void ligate_surrogate_destroy(ligate_surrogate *s) { delete s; }
-extern "C" ligate_status ligate_surrogate_train(ligate_surrogate *, const float *, const float *, int,
-                                                int, int, float, uint64_t, float *, void *) {
-  set_error("surrogate: not built yet");
-  return LIGATE_ERR_UNSUPPORTED;
+
+cudaError_t ensure_work(ligate_surrogate *s, int rows) {
+  if (rows <= s->cap) return cudaSuccess;
+  free_work(s);
+  const size_t r = (size_t)rows;
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->x, r * F0 * 2)) || (e = cudaMalloc(&s->h1, r * F1 * 2)) ||
+      (e = cudaMalloc(&s->h2, r * F1 * 2)) || (e = cudaMalloc(&s->h3, r * F1 * 2)) ||
+      (e = cudaMalloc(&s->dz1, r * F1 * 2)) || (e = cudaMalloc(&s->dz2, r * F1 * 2)) ||
+      (e = cudaMalloc(&s->dz3, r * F1 * 2)) || (e = cudaMalloc(&s->t, r * 4)) ||
+      (e = cudaMalloc(&s->y, r * 4)) || (e = cudaMalloc(&s->dy, r * 4))) {
+    free_work(s);
+    return e;
+  }
+  s->cap = rows;
+  return cudaSuccess;
 }
-extern "C" ligate_status ligate_surrogate_predict(const ligate_surrogate *, const float *, int, float *,
-                                                  void *) {
-  set_error("surrogate: not built yet");
-  return LIGATE_ERR_UNSUPPORTED;
+
+mlp::GemmArgs fwd_args(const __nv_bfloat16 *in, int fan_in, const __nv_bfloat16 *W, const float *b,
+                       __nv_bfloat16 *out, int rows) {
+  mlp::GemmArgs a{};
+  a.A = in; a.B = W; a.M = rows; a.N = F1; a.K = fan_in;
+  a.sAm = fan_in; a.sAk = 1; a.sBk = F1; a.sBn = 1;
+  a.bias = b; a.Cb = out; a.ldc = F1;
+  return a;
 }
-extern "C" ligate_status ligate_surrogate_rank(const ligate_surrogate *, const float *, int, double,
-                                               int32_t *, float *, void *) {
-  set_error("surrogate: not built yet");
-  return LIGATE_ERR_UNSUPPORTED;
+
+// Forward of the hidden layers on x (standardised BF16 rows).
+cudaError_t forward_hidden(ligate_surrogate *s, int rows, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = mlp::gemm(mlp::GEMM_FWD, fwd_args(s->x, F0, s->wb + OW1, s->w + OB1, s->h1, rows), st))) return e;
+  if ((e = mlp::gemm(mlp::GEMM_FWD, fwd_args(s->h1, F1, s->wb + OW2, s->w + OB2, s->h2, rows), st))) return e;
+  return mlp::gemm(mlp::GEMM_FWD, fwd_args(s->h2, F1, s->wb + OW3, s->w + OB3, s->h3, rows), st);
 }
-extern "C" ligate_status ligate_surrogate_grad(const ligate_surrogate *, const float *, const float *,
-                                               int, float *, float *, void *) {
-  set_error("surrogate: not built yet");
-  return LIGATE_ERR_UNSUPPORTED;
+
+// Backward from dz3 (set by the head kernel) into s->g.
+cudaError_t backward(ligate_surrogate *s, int rows, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = mlp::head_grad(s->h3, s->dy, rows, s->g + OW4, s->g + OB4, st))) return e;
+  struct L { const __nv_bfloat16 *in; int fan_in; int ow, ob; __nv_bfloat16 *dz, *dz_prev; const __nv_bfloat16 *hin; };
+  const L layers[3] = {{s->h2, F1, OW3, OB3, s->dz3, s->dz2, s->h2},
+                       {s->h1, F1, OW2, OB2, s->dz2, s->dz1, s->h1},
+                       {s->x, F0, OW1, OB1, s->dz1, nullptr, nullptr}};
+  for (const L &l : layers) {
+    mlp::GemmArgs wg{};  // dW = in^T dZ
+    wg.A = l.in; wg.B = l.dz; wg.M = l.fan_in; wg.N = F1; wg.K = rows;
+    wg.sAm = 1; wg.sAk = l.fan_in; wg.sBk = F1; wg.sBn = 1;
+    wg.Cf = s->g + l.ow; wg.ldc = F1;
+    if ((e = mlp::gemm(mlp::GEMM_WGRAD, wg, st))) return e;
+    if ((e = mlp::colsum(l.dz, rows, F1, s->g + l.ob, st))) return e;
+    if (l.dz_prev) {  // dZ_prev = (dZ W^T) * (H_prev > 0)
+      mlp::GemmArgs dg{};
+      dg.A = l.dz; dg.B = s->wb + l.ow; dg.M = rows; dg.N = l.fan_in; dg.K = F1;
+      dg.sAm = F1; dg.sAk = 1; dg.sBk = 1; dg.sBn = F1;
+      dg.mask = l.hin; dg.Cb = l.dz_prev; dg.ldc = l.fan_in;
+      if ((e = mlp::gemm(mlp::GEMM_DGRAD, dg, st))) return e;
+    }
+  }
+  return cudaSuccess;
 }
-extern "C" ligate_status ligate_surrogate_get_weights(const ligate_surrogate *, float *) {
-  set_error("surrogate: not built yet");
-  return LIGATE_ERR_UNSUPPORTED;
+
+}  // namespace
+
+extern "C" ligate_status ligate_surrogate_create(const float *init, uint64_t seed, ligate_surrogate **out) {
+  if (!out) { set_error("surrogate_create: out is NULL"); return LIGATE_ERR_INVALID; }
+  *out = nullptr;
+  std::vector<float> h(NPAR, 0.f);
+  if (init) {
+    for (int i = 0; i < NPAR; ++i)
+      if (!isfinite(init[i])) { set_error("surrogate_create: non-finite weight %d", i); return LIGATE_ERR_INVALID; }
+    std::copy(init, init + NPAR, h.begin());
+  } else {  // He-normal weights (Box-Muller over SplitMix64), zero biases
+    uint64_t st = seed ^ 0x5851F42D4C957F2DULL;
+    auto fill = [&](int off, int fan_in, int count) {
+      const double sd = sqrt(2.0 / fan_in);
+      for (int i = 0; i < count; i += 2) {
+        double a = u01(st), b = u01(st);
+        if (a < 1e-300) a = 1e-300;
+        const double r = sqrt(-2.0 * log(a));
+        h[off + i] = (float)(sd * r * cos(6.283185307179586 * b));
+        if (i + 1 < count) h[off + i + 1] = (float)(sd * r * sin(6.283185307179586 * b));
+      }
+    };
+    fill(OW1, F0, F0 * F1);
+    fill(OW2, F1, F1 * F1);
+    fill(OW3, F1, F1 * F1);
+    fill(OW4, F1, F1);
+  }
+  ligate_surrogate *s = new ligate_surrogate();
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->w, NPAR * 4)) || (e = cudaMalloc(&s->m, NPAR * 4)) ||
+      (e = cudaMalloc(&s->v, NPAR * 4)) || (e = cudaMalloc(&s->g, NPAR * 4)) ||
+      (e = cudaMalloc(&s->wb, NPAR * 2)) || (e = cudaMalloc(&s->mu, F0 * 4)) ||
+      (e = cudaMalloc(&s->inv_sd, F0 * 4)) || (e = cudaMalloc(&s->lstat, 16)) ||
+      (e = cudaMalloc(&s->sse, 8)) || (e = cudaMemcpy(s->w, h.data(), NPAR * 4, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemset(s->m, 0, NPAR * 4)) || (e = cudaMemset(s->v, 0, NPAR * 4)) ||
+      (e = cudaMemset(s->g, 0, NPAR * 4)) || (e = mlp::to_bf16(s->w, s->wb, NPAR, 0)) ||
+      (e = cudaDeviceSynchronize())) {
+    ligate_surrogate_destroy(s);
+    return cuda_fail(e, "surrogate_create");
+  }
+  std::vector<float> mu(F0, 0.f), one(F0, 1.f);
+  cudaMemcpy(s->mu, mu.data(), F0 * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(s->inv_sd, one.data(), F0 * 4, cudaMemcpyHostToDevice);
+  *out = s;
+  return LIGATE_OK;
+}
+
+extern "C" void ligate_surrogate_destroy(ligate_surrogate *s) {
+  if (!s) return;
+  free_work(s);
+  cudaFree(s->w); cudaFree(s->m); cudaFree(s->v); cudaFree(s->g); cudaFree(s->wb);
+  cudaFree(s->mu); cudaFree(s->inv_sd); cudaFree(s->lstat); cudaFree(s->sse); cudaFree(s->idx);
+  delete s;
+}
+
+extern "C" ligate_status ligate_surrogate_train(ligate_surrogate *s, const float *desc,
+                                                const float *labels, int n, int epochs, int batch,
+                                                float lr, uint64_t seed, float *loss_out, void *stream) {
+  if (!s || !desc || !labels) { set_error("surrogate_train: NULL argument"); return LIGATE_ERR_INVALID; }
+  if (n < 1 || batch < 8 || batch % 8 != 0 || batch > n || epochs < 0 || !(lr > 0)) {
+    set_error("surrogate_train: need 8 <= batch <= n, batch % 8 == 0, epochs >= 0, lr > 0");
+    return LIGATE_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!s->stats) {
+    if ((e = mlp::feature_stats(desc, n, s->mu, s->inv_sd, st)) || (e = mlp::label_stats(labels, n, s->lstat, st)))
+      return cuda_fail(e, "surrogate statistics");
+    double ls[2];
+    if ((e = cudaMemcpyAsync(ls, s->lstat, 16, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+      return cuda_fail(e, "surrogate statistics");
+    s->label_mu = ls[0];
+    s->label_sd = ls[1] > 1e-12 ? ls[1] : 1.0;
+    s->stats = true;
+  }
+  if ((e = ensure_work(s, batch))) return cuda_fail(e, "surrogate workspace");
+  if (s->idx_cap < n) {
+    cudaFree(s->idx);
+    s->idx = nullptr;
+    s->idx_cap = 0;
+    if ((e = cudaMalloc(&s->idx, (size_t)n * 4))) return cuda_fail(e, "surrogate workspace");
+    s->idx_cap = n;
+  }
+  const int steps = n / batch;
+  std::vector<int> perm(n);
+  const float ly_inv = (float)(1.0 / s->label_sd);
+  double last = 0.0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    uint64_t rs = seed * 0x9E3779B97F4A7C15ULL + (uint64_t)ep + 1;
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = n - 1; i > 0; --i) {  // Fisher-Yates
+      const int j = (int)(u01(rs) * (i + 1));
+      std::swap(perm[i], perm[j < i + 1 ? j : i]);
+    }
+    if ((e = cudaMemcpyAsync(s->idx, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemsetAsync(s->sse, 0, 8, st)))
+      return cuda_fail(e, "surrogate epoch");
+    for (int k = 0; k < steps; ++k) {
+      ++s->step;
+      const double c1 = 1.0 / (1.0 - pow(0.9, (double)s->step));
+      const double c2 = 1.0 / (1.0 - pow(0.999, (double)s->step));
+      if ((e = mlp::gather_std(desc, s->idx + (size_t)k * batch, batch, 0, s->mu, s->inv_sd, labels,
+                               (float)s->label_mu, ly_inv, s->x, s->t, st)) ||
+          (e = forward_hidden(s, batch, st)) ||
+          (e = mlp::head(s->h3, s->wb + OW4, s->w + OB4, batch, s->t, s->y, s->dy, 2.f / batch,
+                         s->sse, s->dz3, st)) ||
+          (e = backward(s, batch, st)) ||
+          (e = mlp::adam(s->w, s->g, s->m, s->v, s->wb, NPAR, lr, 0.9f, 0.999f, 1e-8f, (float)c1,
+                         (float)c2, st)))
+        return cuda_fail(e, "surrogate step");
+    }
+    double sse = 0.0;
+    if ((e = cudaMemcpyAsync(&sse, s->sse, 8, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+      return cuda_fail(e, "surrogate epoch");
+    last = steps > 0 ? sse / ((double)steps * batch) : 0.0;
+  }
+  if (loss_out) *loss_out = (float)last;
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_surrogate_grad(const ligate_surrogate *cs, const float *x, const float *t,
+                                               int b, float *grad, float *loss_out, void *stream) {
+  ligate_surrogate *s = const_cast<ligate_surrogate *>(cs);
+  if (!s || !x || !t || !grad) { set_error("surrogate_grad: NULL argument"); return LIGATE_ERR_INVALID; }
+  if (b < 1) { set_error("surrogate_grad: b < 1"); return LIGATE_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = ensure_work(s, b))) return cuda_fail(e, "surrogate workspace");
+  double sse = 0.0;
+  if ((e = mlp::to_bf16(x, s->x, b * F0, st)) ||
+      (e = cudaMemcpyAsync(s->t, t, (size_t)b * 4, cudaMemcpyDeviceToDevice, st)) ||
+      (e = cudaMemsetAsync(s->sse, 0, 8, st)) || (e = forward_hidden(s, b, st)) ||
+      (e = mlp::head(s->h3, s->wb + OW4, s->w + OB4, b, s->t, s->y, s->dy, 2.f / b, s->sse, s->dz3, st)) ||
+      (e = backward(s, b, st)) ||
+      (e = cudaMemcpyAsync(grad, s->g, NPAR * 4, cudaMemcpyDeviceToDevice, st)) ||
+      (e = cudaMemcpyAsync(&sse, s->sse, 8, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+    return cuda_fail(e, "surrogate_grad");
+  if (loss_out) *loss_out = (float)(sse / b);
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_surrogate_predict(const ligate_surrogate *cs, const float *desc, int n,
+                                                  float *pred, void *stream) {
+  ligate_surrogate *s = const_cast<ligate_surrogate *>(cs);
+  if (!s || (n > 0 && (!desc || !pred)) || n < 0) { set_error("surrogate_predict: bad argument"); return LIGATE_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = 32768;
+  cudaError_t e;
+  if ((e = ensure_work(s, n < chunk ? (n > 0 ? n : 1) : chunk))) return cuda_fail(e, "surrogate workspace");
+  for (int r0 = 0; r0 < n; r0 += chunk) {
+    const int rows = n - r0 < chunk ? n - r0 : chunk;
+    if ((e = mlp::gather_std(desc, nullptr, rows, r0, s->mu, s->inv_sd, nullptr, 0.f, 0.f, s->x, nullptr, st)) ||
+        (e = forward_hidden(s, rows, st)) ||
+        (e = mlp::head(s->h3, s->wb + OW4, s->w + OB4, rows, nullptr, pred + r0, nullptr, 0.f, nullptr,
+                       nullptr, st)) ||
+        (e = mlp::unstd(pred + r0, rows, (float)s->label_mu, (float)s->label_sd, st)))
+      return cuda_fail(e, "surrogate_predict");
+  }
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_surrogate_rank(const ligate_surrogate *s, const float *desc, int n,
+                                               double keep_frac, int32_t *idx_out, float *pred_out,
+                                               void *stream) {
+  if (!s || n < 0 || !(keep_frac >= 0.0 && keep_frac <= 1.0) || (n > 0 && (!desc || !idx_out))) {
+    set_error("surrogate_rank: bad argument");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n == 0) return LIGATE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int k = (int)ceil((double)n * keep_frac - 1e-9);
+  int n2 = 2048;
+  while (n2 < n) n2 <<= 1;
+  float *pred = pred_out;
+  unsigned long long *keys = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!pred && (e = cudaMalloc(&pred, (size_t)n * 4))) return cuda_fail(e, "surrogate_rank");
+  if ((e = cudaMalloc(&keys, (size_t)n2 * 8))) {
+    if (!pred_out) cudaFree(pred);
+    return cuda_fail(e, "surrogate_rank");
+  }
+  ligate_status r = ligate_surrogate_predict(s, desc, n, pred, stream);
+  if (r == LIGATE_OK) {
+    e = mlp::sort_select(pred, n, k, keys, n2, idx_out, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) r = cuda_fail(e, "surrogate_rank");
+  }
+  cudaFree(keys);
+  if (!pred_out) cudaFree(pred);
+  return r;
+}
+
+extern "C" ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s, float *out) {
+  if (!s || !out) { set_error("surrogate_get_weights: NULL argument"); return LIGATE_ERR_INVALID; }
+  cudaError_t e = cudaMemcpy(out, s->w, NPAR * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate_get_weights");
+  return LIGATE_OK;
 }

@@ -150,7 +150,7 @@ def test_largest_ligands():
     rng = np.random.default_rng(0)
     maps = (maps + rng.normal(size=maps.shape).astype(np.float32)).astype(np.float32)
     P = Pocket(maps, np.zeros(3), 0.5, np.array([[19.75, 19.75, 19.75]], np.float32))
-    samp = Sampling(tiny.sampling.quats[:4], 1, 4, 4)
+    samp = Sampling(w.sampling.quats[:4], 1, 4, 4)
     r = D.dock(P, big, samp)
     for i in range(2):
         compare_ligand(big.ligand(i), P, samp, r[i])
