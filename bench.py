@@ -36,11 +36,18 @@ sys.path.insert(0, ROOT)
 METRIC = "ligands docked/s & poses scored/s on 1 GB300, chosen vs plain form at stated error"
 WORKLOAD = ("batched: 10000 ligands (N~U{15..60}, R~U{0..12}), 8x64^3 maps @0.375 A, "
             "256 orient x 32 anchors x S=16, top-16")
-# Algorithmic FP32 operations (FMA = 2) per unit of work, see the design doc:
+# FP32 operations (FMA = 2) per unit of executed work, see the design doc:
 #   atom interpolation: 9 FMA rotation + 3 fraction subs + 7 lerps (sub + FMA) + 1 add = 43
-#   clash pair: 3 subs + (mul + 2 FMA) + FMA + FMA = 12
+#   clash candidate test (once per bond): distance, axial/radial split, P, Q, bound = 40
+#   surviving clash pair, per torsion step: 2 FMA (d^2 in closed form) + 1 FMA (t^2) = 6
 FLOP_PER_ATOM_EVAL = 43.0
-FLOP_PER_PAIR_EVAL = 12.0
+FLOP_PER_PAIR_TEST = 40.0
+FLOP_PER_PAIR_STEP = 6.0
+
+
+def executed_flops(work, S):
+    return (work.done_atom_evals * FLOP_PER_ATOM_EVAL + work.done_pair_tests * FLOP_PER_PAIR_TEST
+            + work.done_pair_survivors * S * FLOP_PER_PAIR_STEP)
 
 
 def fp32_peak_tflops(sms=152, lanes=128, mhz=2070.0):
@@ -233,11 +240,12 @@ def main():
     value = ws * n_lig * args.steps / t_chosen
     poses_s = ws * work.poses * args.steps / t_chosen
     mean_ms = t_chosen * 1000 / args.steps
-    flops = work.atom_evals * FLOP_PER_ATOM_EVAL + work.pair_evals * FLOP_PER_PAIR_EVAL
+    S = w.sampling.torsion_steps
+    flops = executed_flops(work, S)
     achieved = flops / (mean_ms / 1000) / 1e12
     peak = fp32_peak_tflops()
     plain_ms = sum(ms_plain) / len(ms_plain)
-    plain_flops = work_plain.atom_evals * FLOP_PER_ATOM_EVAL + work_plain.pair_evals * FLOP_PER_PAIR_EVAL
+    plain_flops = executed_flops(work_plain, S)
 
     # end to end through the host-array C-ABI call
     e2e = None
@@ -279,8 +287,10 @@ def main():
                      "frac": achieved / peak, "traffic": None,
                      "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz",
                      "kernel": "dock_kernel<BF16_CORNER>",
-                     "work_per_launch": {"atom_evals": work.atom_evals, "pair_evals": work.pair_evals,
-                                         "poses": work.poses}},
+                     "work_per_launch": {"atom_evals": work.done_atom_evals,
+                                         "pair_tests": work.done_pair_tests,
+                                         "pair_survivors": work.done_pair_survivors,
+                                         "pair_candidates_x_S": work.pair_evals, "poses": work.poses}},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
         "gpu_launches": launches_per_run * args.steps,
     }

@@ -213,9 +213,15 @@ ligate_status ligate_plan_get_tile(const ligate_plan *plan, ligate_tile *tile_ou
  * clash-pair evaluations executed by the sweep. */
 typedef struct {
   double poses;
-  double atom_evals;
-  double pair_evals;
+  double atom_evals;   /* atom interpolations of the sweep (moved atoms x S per bond + N per start) */
+  double pair_evals;   /* candidate clash pairs x S, before pruning */
   double starts;
+  /* Counted on the device during the last run: atom interpolations, clash
+   * candidate pairs tested against the circle bound (once per bond), and
+   * surviving pairs (each evaluated at all S steps). 0 before a run. */
+  double done_atom_evals;
+  double done_pair_tests;
+  double done_pair_survivors;
 } ligate_work;
 ligate_status ligate_plan_work(const ligate_plan *plan, ligate_work *out);
 void ligate_plan_destroy(ligate_plan *plan);

@@ -514,6 +514,7 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   p.clash_w = s->clash_weight;
   p.inv_dc2_ang = (float)(1.0 / ((double)s->clash_cutoff * s->clash_cutoff));
   p.inv_dc2_grid = (float)(d.spacing * d.spacing / ((double)s->clash_cutoff * s->clash_cutoff));
+  p.dc2_grid_margin = (float)((double)s->clash_cutoff * s->clash_cutoff / (d.spacing * d.spacing) * (1.0 + 1e-4));
   p.rescore = s->rescore_fp32 ? 1 : 0;
   p.nmax = std::max(32, (B->d.max_atoms + 31) / 32 * 32);
   p.wmax = p.nmax / 32;
@@ -551,6 +552,7 @@ struct ligate_plan {
   int *lig_items = nullptr, *lig_slot0 = nullptr, *counters = nullptr;
   PoseOut *partial = nullptr, *out = nullptr;
   size_t counter_bytes = 0;
+  unsigned long long *stats = nullptr;  // [3] executed-work counters of the last run
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -564,7 +566,7 @@ static void free_plan(ligate_plan *pl) {
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   cudaFree(pl->rot); cudaFree(pl->anc); cudaFree(pl->quat);
   cudaFree(pl->items); cudaFree(pl->lig_items); cudaFree(pl->lig_slot0);
-  cudaFree(pl->counters); cudaFree(pl->partial); cudaFree(pl->out);
+  cudaFree(pl->counters); cudaFree(pl->partial); cudaFree(pl->out); cudaFree(pl->stats);
   delete pl;
 }
 
@@ -659,6 +661,10 @@ extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate
   const size_t ni = items.size();
   cudaError_t e;
   pl->counter_bytes = sizeof(int) * (size_t)(n + 1);
+  if ((e = dmalloc(&pl->stats, 3)) != cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "plan allocation");
+  }
   if ((e = dmalloc(&pl->items, ni)) != cudaSuccess || (e = dmalloc(&pl->lig_items, n)) != cudaSuccess ||
       (e = dmalloc(&pl->lig_slot0, n)) != cudaSuccess ||
       (e = dmalloc(&pl->counters, (size_t)n + 1)) != cudaSuccess ||
@@ -679,6 +685,7 @@ extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate
   p.lig_slot0 = pl->lig_slot0;
   p.queue = pl->counters;
   p.done = pl->counters + 1;
+  p.stats = pl->stats;
   p.partial = pl->partial;
   p.out = pl->out;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan setup"); }
@@ -692,6 +699,7 @@ static ligate_status plan_capture(ligate_plan *pl) {
   CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking), "capture stream");
   CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t e = cudaMemsetAsync(pl->counters, 0, pl->counter_bytes, pl->cap_stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->stats, 0, 3 * sizeof(unsigned long long), pl->cap_stream);
   if (e == cudaSuccess && pl->p.n_items > 0)
     e = launch_dock(pl->mode, pl->p, pl->grid, pl->block, pl->smem, pl->cap_stream);
   cudaGraph_t g = nullptr;
@@ -739,6 +747,14 @@ extern "C" ligate_status ligate_plan_get_tile(const ligate_plan *pl, ligate_tile
 extern "C" ligate_status ligate_plan_work(const ligate_plan *pl, ligate_work *w) {
   if (!pl || !w) { set_error("plan_work: NULL argument"); return LIGATE_ERR_INVALID; }
   *w = pl->work;
+  unsigned long long c[3] = {0, 0, 0};
+  if (pl->exec) {
+    cudaError_t e = cudaMemcpy(c, pl->stats, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "plan_work");
+  }
+  w->done_atom_evals = (double)c[0];
+  w->done_pair_tests = (double)c[1];
+  w->done_pair_survivors = (double)c[2];
   return LIGATE_OK;
 }
 

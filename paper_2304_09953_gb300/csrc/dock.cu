@@ -145,13 +145,18 @@ struct TopK {
 struct WarpSmem {
   float4 *ref;     // [nmax]  (x - c, y - c, z - c) Angstrom, .w = atom type (int bits)
   float4 *pose;    // [G][nmax + 1] current pose, grid units, .w = map offset (int bits)
+  float4 *list;    // [G][PAIR_CAP] clash pairs that survive the circle bound of a bond
   BondRec *bonds;  // [LIGATE_MAX_ROT]
   uint32_t *elig;  // [nmax * wmax]
 };
 
+// Surviving clash pairs buffered per start group before they are evaluated
+// for every torsion step (the buffer is flushed whenever it may overflow).
+constexpr int PAIR_CAP = 96;
+
 __host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int wmax, int G) {
-  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + sizeof(BondRec) * LIGATE_MAX_ROT +
-         (size_t)nmax * wmax * 4;
+  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)G * PAIR_CAP * 16 +
+         sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)nmax * wmax * 4;
 }
 
 size_t dock_smem_per_warp(int nmax, int G) {
@@ -162,7 +167,8 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int
   WarpSmem w;
   w.ref = reinterpret_cast<float4 *>(base);
   w.pose = w.ref + nmax;
-  w.bonds = reinterpret_cast<BondRec *>(w.pose + (size_t)G * (nmax + 1));
+  w.list = w.pose + (size_t)G * (nmax + 1);
+  w.bonds = reinterpret_cast<BondRec *>(w.list + (size_t)G * PAIR_CAP);
   w.elig = reinterpret_cast<uint32_t *>(w.bonds + LIGATE_MAX_ROT);
   return w;
 }
@@ -329,9 +335,11 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
       cur = item.ligand;
     }
     top.clear();
+    unsigned n_atom = 0, n_test = 0, n_pair = 0;  // work counters of this lane's group
 
     for (int s0 = item.s0; s0 < item.s1; s0 += G) {
       const int sid = min(s0 + g, item.s1 - 1);  // a group past the end repeats the last start
+      const unsigned n_atom0 = n_atom, n_test0 = n_test, n_pair0 = n_pair;
       // -- rigid start: pose = R_o (x - c) / h + (a - origin) / h
       float R[9], T[3];
       start_frame(p, sid, R, T);
@@ -349,6 +357,7 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
       }
       for (int o = L >> 1; o > 0; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
       float E = fmaf(p.clash_w, clash_ref, e);
+      n_atom += d.n_atoms;
       uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
       __syncwarp();
 
@@ -360,24 +369,78 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
         bond_axis(pose[br.u], pv, nx, ny, nz);
         Rot rot;
         rot.make(ck, sk, nx, ny, nz, pv.x, pv.y, pv.z);
+        // grid part: every moved atom at this lane's torsion step
         float ag = 0.f, ac = 0.f;
         for (int i = br.v + 1; i < br.end; ++i) {
           const float4 q = pose[i];
           float yx, yy, yz;
           rot.apply(q.x, q.y, q.z, yx, yy, yz);
           ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
-          const uint32_t *row = w.elig + i * d.n_words;
-          for (int wd = 0; wd < d.n_words; ++wd) {
-            uint32_t m = row[wd] & br.fixed[wd];
-            while (m) {
-              const int j = 32 * wd + __ffs(m) - 1;
-              m &= m - 1;
-              const float4 f = pose[j];
-              const float dx = yx - f.x, dy = yy - f.y, dz = yz - f.z;
-              const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_grid, 1.f));
-              ac = fmaf(t, t, ac);
+        }
+        n_atom += br.end - br.v - 1;
+        // clash part.  Moved atom i travels on a circle about the axis; with
+        // u = radial vector of i, m = n x u, w = radial vector of fixed atom
+        // j, P = u.w, Q = m.w and D0 = |x_i - x_j|^2 at the current pose,
+        //   d^2(theta) = D0 + 2P (1 - cos theta) - 2Q sin theta,
+        // whose minimum over the circle is D0 + 2P - 2 sqrt(P^2 + Q^2).  A
+        // pair whose minimum is beyond d_c contributes exactly zero at every
+        // step and is dropped; the others are evaluated in closed form.
+        {
+          float4 *list = w.list + g * PAIR_CAP;
+          const unsigned lmask = L == 32 ? FULL : ((1u << L) - 1u);
+          const unsigned below = (1u << k) - 1u;
+          const float omc = 1.f - ck;
+          int cnt = 0;
+          auto flush = [&]() {
+            __syncwarp();
+            const int top = __reduce_max_sync(FULL, (unsigned)cnt);
+            for (int q = 0; q < top; ++q) {
+              if (q < cnt) {
+                const float4 e = list[q];
+                const float t = fmaxf(0.f, fmaf(e.z, sk, fmaf(e.y, omc, e.x)));
+                ac = fmaf(t, t, ac);
+              }
+            }
+            n_pair += cnt;
+            cnt = 0;
+            __syncwarp();
+          };
+          for (int i = br.v + 1; i < br.end; ++i) {
+            const float4 xi = pose[i];
+            const float ex = xi.x - pv.x, ey = xi.y - pv.y, ez = xi.z - pv.z;
+            const float ai = fmaf(ex, nx, fmaf(ey, ny, ez * nz));
+            const float ux = fmaf(-ai, nx, ex), uy = fmaf(-ai, ny, ey), uz = fmaf(-ai, nz, ez);
+            const float mx = ny * uz - nz * uy, my = nz * ux - nx * uz, mz = nx * uy - ny * ux;
+            const uint32_t *row = w.elig + i * d.n_words;
+            for (int wd = 0; wd < d.n_words; ++wd) {
+              const uint32_t cand = row[wd] & br.fixed[wd];
+              if (!cand) continue;
+              n_test += __popc(cand);
+              for (int h = 0; h < 32; h += L) {
+                bool surv = false;
+                float4 e;
+                if ((cand >> (h + k)) & 1u) {
+                  const float4 xj = pose[32 * wd + h + k];
+                  const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+                  const float D0 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                  const float fx = xj.x - pv.x, fy = xj.y - pv.y, fz = xj.z - pv.z;
+                  const float aj = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
+                  const float wx = fmaf(-aj, nx, fx), wy = fmaf(-aj, ny, fy), wz = fmaf(-aj, nz, fz);
+                  const float P = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
+                  const float Q = fmaf(mx, wx, fmaf(my, wy, mz * wz));
+                  const float s = D0 + 2.f * P - p.dc2_grid_margin;
+                  surv = s < 0.f || s * s < 4.f * fmaf(P, P, Q * Q);
+                  e = make_float4(fmaf(-D0, p.inv_dc2_grid, 1.f), -2.f * P * p.inv_dc2_grid,
+                                  2.f * Q * p.inv_dc2_grid, 0.f);
+                }
+                const unsigned gm = (__ballot_sync(FULL, surv) >> (g * L)) & lmask;
+                if (surv) list[cnt + __popc(gm & below)] = e;
+                cnt += __popc(gm);
+                if (__any_sync(FULL, cnt > PAIR_CAP - L)) flush();
+              }
             }
           }
+          flush();
         }
         const float V = (k < S) ? fmaf(p.clash_w, ac, ag) : INF;
         float best = V;
@@ -407,6 +470,8 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
         __syncwarp();
       }
 
+      if (s0 + g >= item.s1) { n_atom = n_atom0; n_test = n_test0; n_pair = n_pair0; }
+
       // -- candidates of this start group into the warp's top-K
       for (int gg = 0; gg < G; ++gg) {
         const int src = gg * L;
@@ -414,6 +479,20 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
         const uint32_t c0 = __shfl_sync(FULL, t0, src), c1 = __shfl_sync(FULL, t1, src),
                        c2 = __shfl_sync(FULL, t2, src), c3 = __shfl_sync(FULL, t3, src);
         if (s0 + gg < item.s1) top.insert(ce, s0 + gg, c0, c1, c2, c3, K, lane);
+      }
+    }
+
+    if (p.stats) {  // one count per start group (its lane 0)
+      unsigned long long a = k == 0 ? n_atom : 0, t = k == 0 ? n_test : 0, q = k == 0 ? n_pair : 0;
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL, a, o);
+        t += __shfl_xor_sync(FULL, t, o);
+        q += __shfl_xor_sync(FULL, q, o);
+      }
+      if (lane == 0) {
+        atomicAdd(p.stats + 0, a);
+        atomicAdd(p.stats + 1, t);
+        atomicAdd(p.stats + 2, q);
       }
     }
 

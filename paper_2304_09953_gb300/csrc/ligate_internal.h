@@ -116,6 +116,8 @@ struct DockParams {
   float clash_w;
   float inv_dc2_grid;      // h^2 / d_c^2
   float inv_dc2_ang;       // 1 / d_c^2
+  float dc2_grid_margin;   // (d_c / h)^2 (1 + 1e-4): pairs beyond it never clash
+  unsigned long long *stats;  // optional [3]: atom interpolations, pair tests, pair evaluations
   int rescore;
   // work queue
   const Item *items;

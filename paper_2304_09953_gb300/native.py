@@ -65,7 +65,9 @@ class ligate_tile(ctypes.Structure):
 
 class ligate_work(ctypes.Structure):
     _fields_ = [("poses", ctypes.c_double), ("atom_evals", ctypes.c_double),
-                ("pair_evals", ctypes.c_double), ("starts", ctypes.c_double)]
+                ("pair_evals", ctypes.c_double), ("starts", ctypes.c_double),
+                ("done_atom_evals", ctypes.c_double), ("done_pair_tests", ctypes.c_double),
+                ("done_pair_survivors", ctypes.c_double)]
 
 
 # name -> (restype, argtypes)
