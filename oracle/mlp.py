@@ -33,8 +33,16 @@ def bf16_round(x) -> np.ndarray:
     return out
 
 
-def forward(params, X):
-    """Returns (y[B], cache) with cache = pre-activations and activations."""
+def _bf16(a):
+    return bf16_round(np.asarray(a, np.float32)).astype(np.float64)
+
+
+def forward(params, X, bf16_acts: bool = False):
+    """Returns (y[B], cache) with cache = pre-activations and activations.
+
+    ``bf16_acts`` applies the network's storage precision: the hidden
+    activations are held in BF16, so each ReLU output is rounded to BF16
+    before it feeds the next layer (all arithmetic stays FP64)."""
     X = np.asarray(X, np.float64)
     acts = [X]
     pres = []
@@ -44,9 +52,14 @@ def forward(params, X):
         W, b = np.asarray(params[2 * l], np.float64), np.asarray(params[2 * l + 1], np.float64)
         z = h @ W + b
         pres.append(z)
-        h = np.maximum(z, 0.0) if l < n_layers - 1 else z
+        if l < n_layers - 1:
+            h = np.maximum(z, 0.0)
+            if bf16_acts:
+                h = _bf16(h)
+        else:
+            h = z
         acts.append(h)
-    return h[:, 0], (acts, pres)
+    return h[:, 0], (acts, pres, bf16_acts)
 
 
 def mse(y, t) -> float:
@@ -56,8 +69,12 @@ def mse(y, t) -> float:
 
 
 def backward(params, cache, y, t):
-    """Gradients of mse(y, t) with respect to every parameter (same layout)."""
-    acts, pres = cache
+    """Gradients of mse(y, t) with respect to every parameter (same layout).
+
+    When the forward pass held activations in BF16, the gradients with
+    respect to the hidden pre-activations are held in BF16 too (rounded
+    after the ReLU mask), matching the network's storage precision."""
+    acts, pres, bf16_acts = cache
     B = len(y)
     n_layers = len(params) // 2
     grads = [None] * len(params)
@@ -65,6 +82,8 @@ def backward(params, cache, y, t):
     for l in reversed(range(n_layers)):
         if l < n_layers - 1:
             d = d * (pres[l] > 0.0)
+            if bf16_acts:
+                d = _bf16(d)
         grads[2 * l] = acts[l].T @ d
         grads[2 * l + 1] = d.sum(axis=0)
         if l > 0:

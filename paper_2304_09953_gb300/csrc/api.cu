@@ -606,6 +606,11 @@ extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate
   t.warps_per_cta = std::max(1, std::min(16, t.warps_per_cta));
   for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
     t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
+  {  // fewer warps per CTA when large ligands or many start groups need more shared memory
+    const size_t per_warp = dock_smem_per_warp(p.nmax, p.G);
+    const int fit = (int)std::max<size_t>(1, (size_t)(227 * 1024) / per_warp);
+    t.warps_per_cta = std::min(t.warps_per_cta, fit);
+  }
   pl->block = 32 * t.warps_per_cta;
   pl->smem = dock_smem_per_warp(p.nmax, p.G) * t.warps_per_cta;
   if (pl->smem > 227 * 1024) {

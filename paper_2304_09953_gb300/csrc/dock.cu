@@ -150,12 +150,13 @@ struct WarpSmem {
   uint32_t *elig;  // [nmax * wmax]
 };
 
-// Surviving clash pairs buffered per start group before they are evaluated
-// for every torsion step (the buffer is flushed whenever it may overflow).
-constexpr int PAIR_CAP = 96;
+// Surviving clash pairs buffered per warp before they are evaluated for
+// every torsion step: 128 entries, 128 / G = 4 L per start group (the
+// buffer is flushed whenever a group may overflow).
+constexpr int PAIR_WARP = 128;
 
 __host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int wmax, int G) {
-  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)G * PAIR_CAP * 16 +
+  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
          sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)nmax * wmax * 4;
 }
 
@@ -168,7 +169,7 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int
   w.ref = reinterpret_cast<float4 *>(base);
   w.pose = w.ref + nmax;
   w.list = w.pose + (size_t)G * (nmax + 1);
-  w.bonds = reinterpret_cast<BondRec *>(w.list + (size_t)G * PAIR_CAP);
+  w.bonds = reinterpret_cast<BondRec *>(w.list + PAIR_WARP);
   w.elig = reinterpret_cast<uint32_t *>(w.bonds + LIGATE_MAX_ROT);
   return w;
 }
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
           rot.apply(q.x, q.y, q.z, yx, yy, yz);
           ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
         }
-        n_atom += br.end - br.v - 1;
+        n_atom += (unsigned)(br.end - br.v - 1) * (unsigned)S;
         // clash part.  Moved atom i travels on a circle about the axis; with
         // u = radial vector of i, m = n x u, w = radial vector of fixed atom
         // j, P = u.w, Q = m.w and D0 = |x_i - x_j|^2 at the current pose,
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
         // pair whose minimum is beyond d_c contributes exactly zero at every
         // step and is dropped; the others are evaluated in closed form.
         {
-          float4 *list = w.list + g * PAIR_CAP;
+          const int cap = PAIR_WARP / G;  // = 4 L
+          float4 *list = w.list + g * cap;
           const unsigned lmask = L == 32 ? FULL : ((1u << L) - 1u);
           const unsigned below = (1u << k) - 1u;
           const float omc = 1.f - ck;
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
                 const unsigned gm = (__ballot_sync(FULL, surv) >> (g * L)) & lmask;
                 if (surv) list[cnt + __popc(gm & below)] = e;
                 cnt += __popc(gm);
-                if (__any_sync(FULL, cnt > PAIR_CAP - L)) flush();
+                if (__any_sync(FULL, cnt > cap - L)) flush();
               }
             }
           }

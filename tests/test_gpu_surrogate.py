@@ -69,18 +69,26 @@ def test_forward_and_gradients_match_oracle():
         g = torch.zeros(N.LIGATE_SURROGATE_PARAMS, dtype=torch.float32, device="cuda")
         loss = N.ligate_surrogate_grad(s, xd, td, B, g)
         params = [p.astype(np.float64) for p in split(wf)]
-        y, cache = omlp.forward(params, x.astype(np.float64))
-        assert abs(loss - omlp.mse(y, t)) <= 1e-2 * omlp.mse(y, t)
-        want = omlp.backward(params, cache, y, t)
         got = split(g.cpu().numpy().astype(np.float64))
+        # oracle with the network's BF16 storage points (activations and their
+        # gradients): the GPU must match it closely
+        y, cache = omlp.forward(params, x.astype(np.float64), bf16_acts=True)
+        assert abs(loss - omlp.mse(y, t)) <= 1e-3 * omlp.mse(y, t)
+        want = omlp.backward(params, cache, y, t)
         for a, b in zip(got, want):
             rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-            assert rel <= 1e-2, rel
+            assert rel <= 5e-3, rel
+        # all-FP64 oracle: the gap is the BF16 storage itself (reported)
+        y64, c64 = omlp.forward(params, x.astype(np.float64))
+        want64 = omlp.backward(params, c64, y64, t)
+        rels = [np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30) for a, b in zip(got, want64)]
+        print("rel-L2 vs all-FP64 oracle per tensor:", np.round(rels, 4))
+        assert max(rels) <= 0.1
         # forward through the public predict path (standardisation off: mu 0, sd 1)
         pred = torch.zeros(B, dtype=torch.float32, device="cuda")
         N.ligate_surrogate_predict(s, xd, B, pred)
         yp = pred.cpu().numpy()
-        assert np.linalg.norm(yp - y) / np.linalg.norm(y) <= 1e-2
+        assert np.linalg.norm(yp - y) / np.linalg.norm(y) <= 1e-3
     finally:
         N.ligate_surrogate_destroy(s)
 

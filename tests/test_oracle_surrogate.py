@@ -129,3 +129,27 @@ def test_he_init_scale():
     p = mlp.he_init(draws)
     assert [w.shape for w in p[::2]] == [(256, 512), (512, 512), (512, 512), (512, 1)]
     assert abs(p[0].std() - np.sqrt(2 / 256)) < 0.01 * np.sqrt(2 / 256) * 10
+
+
+def test_bf16_activation_rounding_points():
+    """With BF16 storage the only change is rounding of the hidden
+    activations (forward) and of their gradients (backward): exactly
+    representable values pass unchanged, others round to nearest even."""
+    dims = (2, 1, 1, 1, 1)
+    params = [np.array([[1.0], [2.0 ** -9]]), np.zeros(1), np.array([[1.0]]), np.zeros(1),
+              np.array([[1.0]]), np.zeros(1), np.array([[3.0]]), np.zeros(1)]
+    X = np.array([[1.0, 1.0], [2.0, 0.0]])
+    y64, c64 = mlp.forward(params, X)
+    y16, c16 = mlp.forward(params, X, bf16_acts=True)
+    # h1 = 1 + 2^-9 is a tie between 1 and 1 + 2^-7 -> 1 (even); row 2 exact
+    assert y64[0] == 3.0 * (1 + 2.0 ** -9) and y16[0] == 3.0
+    assert y64[1] == y16[1] == 6.0
+    t = np.array([0.0, 5.0])
+    g64 = mlp.backward(params, c64, y64, t)
+    g16 = mlp.backward(params, c16, y16, t)
+    # dy = (3, 1); backward signal into layer 3 = 3 dy: exact in BF16 here
+    d = np.array([3.0, 1.0])
+    assert g16[6][0, 0] == d @ np.array([1.0, 2.0])
+    assert g16[4][0, 0] == (3 * d) @ np.array([1.0, 2.0])
+    assert g64[4][0, 0] == (3 * np.array([3 * (1 + 2.0 ** -9), 1.0])) @ np.array([1 + 2.0 ** -9, 2.0])
+    assert len(dims) == 5
