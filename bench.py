@@ -276,7 +276,7 @@ def main():
         "config": {"workload": WORKLOAD, "form": "chosen: bf16 corner maps + autotuned tile + fp32 top-16 rescore",
                    "l2": "flushed (256 MB write) between timed steps",
                    "tile": {"warps_per_cta": t_.warps_per_cta, "ctas_per_sm": t_.ctas_per_sm,
-                            "starts_per_item": list(t_.starts_per_item)},
+                            "starts_per_item": list(t_.starts_per_item), "reg_cap": t_.reg_cap},
                    "autotune_s": round(tune_s, 2), "parallelism": f"replicas x{ws}"},
         "poses_per_s": poses_s,
         "plain": {"value": ws * n_lig / (plain_ms / 1000), "unit": "ligands/s",

@@ -160,6 +160,7 @@ struct LigPack {
   std::vector<BondRec> bonds;
   std::vector<uint32_t> elig;
   std::vector<uint8_t> types;
+  std::vector<uint16_t> cand;
 };
 
 // Renumber one ligand in DFS pre-order, build its sweep-ordered bond table
@@ -253,12 +254,7 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     return LIGATE_ERR_UNSUPPORTED;
   }
   std::sort(br.begin(), br.end(), [](const BondRec &a, const BondRec &b) { return a.v < b.v; });
-  for (auto &r : br) {
-    for (int a = 0; a < n; ++a)
-      if ((a < r.v || a >= r.end) && a != r.u) r.fixed[a >> 5] |= 1u << (a & 31);
-  }
   P.n_rot = (int)br.size();
-  P.bonds = br;
   // topological distances in DFS numbering (BFS from every atom)
   std::vector<std::vector<int>> adjp(n);
   for (int a = 0; a < n; ++a)
@@ -278,6 +274,20 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     for (int j = 0; j < n; ++j)
       if (dist[j] >= 4) P.elig[(size_t)s * P.words + (j >> 5)] |= 1u << (j & 31);
   }
+  // clash candidates of each bond: moved atom i (v < i < end) x fixed atom j
+  // (outside [v, end), j != u), at least 4 bonds apart
+  P.cand.clear();
+  for (auto &r : br) {
+    r.cand_off = (int)P.cand.size();
+    for (int i = r.v + 1; i < r.end; ++i)
+      for (int j = 0; j < n; ++j) {
+        if ((j >= r.v && j < r.end) || j == r.u) continue;
+        if (P.elig[(size_t)i * P.words + (j >> 5)] >> (j & 31) & 1u)
+          P.cand.push_back((uint16_t)(i | (j << 8)));
+      }
+    r.n_cand = (int)P.cand.size() - r.cand_off;
+  }
+  P.bonds = br;
   return LIGATE_OK;
 }
 
@@ -334,20 +344,21 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   d.n_ligands = n;
   d.h_lig.resize(n);
   d.h_rot.resize(n);
-  int64_t na = 0, nb = 0, ne = 0;
+  int64_t na = 0, nb = 0, ne = 0, nc = 0;
   for (int i = 0; i < n; ++i) {
     LigDesc &ld = d.h_lig[i];
     memset(&ld, 0, sizeof(ld));
     ld.atom_base = (int)na;
     ld.n_atoms = packs[i].n;
     ld.n_rot = packs[i].n_rot;
-    ld.n_orig_rot = packs[i].n_rot;
     ld.bond_base = (int)nb;
     ld.elig_base = (int)ne;
     ld.n_words = packs[i].words;
+    ld.cand_base = nc;
     na += packs[i].n;
     nb += packs[i].n_rot;
     ne += (int64_t)packs[i].n * packs[i].words;
+    nc += (int64_t)packs[i].cand.size();
     d.max_atoms = std::max(d.max_atoms, packs[i].n);
     d.max_rot = std::max(d.max_rot, packs[i].n_rot);
     B->max_type = std::max(B->max_type, packs[i].max_type);
@@ -363,23 +374,27 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   d.h_bonds.resize(nb);
   d.h_elig.resize(ne);
   d.h_types.resize(na);
+  d.h_cand.resize(nc);
   for (int i = 0; i < n; ++i) {
     const LigDesc &ld = d.h_lig[i];
     std::copy(packs[i].atoms.begin(), packs[i].atoms.end(), atoms.begin() + ld.atom_base);
     std::copy(packs[i].types.begin(), packs[i].types.end(), d.h_types.begin() + ld.atom_base);
     std::copy(packs[i].bonds.begin(), packs[i].bonds.end(), d.h_bonds.begin() + ld.bond_base);
     std::copy(packs[i].elig.begin(), packs[i].elig.end(), d.h_elig.begin() + ld.elig_base);
+    std::copy(packs[i].cand.begin(), packs[i].cand.end(), d.h_cand.begin() + ld.cand_base);
   }
   cudaError_t e;
   if ((e = dmalloc(&d.lig, n)) != cudaSuccess || (e = dmalloc(&d.atoms, na)) != cudaSuccess ||
-      (e = dmalloc(&d.bonds, nb)) != cudaSuccess || (e = dmalloc(&d.elig, ne)) != cudaSuccess) {
+      (e = dmalloc(&d.bonds, nb)) != cudaSuccess || (e = dmalloc(&d.elig, ne)) != cudaSuccess ||
+      (e = dmalloc(&d.cand, nc)) != cudaSuccess) {
     ligate_batch_destroy(B);
     return cuda_fail(e, "batch allocation");
   }
   if ((n && (e = cudaMemcpy(d.lig, d.h_lig.data(), sizeof(LigDesc) * n, cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (na && (e = cudaMemcpy(d.atoms, atoms.data(), sizeof(float4) * na, cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (nb && (e = cudaMemcpy(d.bonds, d.h_bonds.data(), sizeof(BondRec) * nb, cudaMemcpyHostToDevice)) != cudaSuccess) ||
-      (ne && (e = cudaMemcpy(d.elig, d.h_elig.data(), 4 * ne, cudaMemcpyHostToDevice)) != cudaSuccess)) {
+      (ne && (e = cudaMemcpy(d.elig, d.h_elig.data(), 4 * ne, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (nc && (e = cudaMemcpy(d.cand, d.h_cand.data(), 2 * nc, cudaMemcpyHostToDevice)) != cudaSuccess)) {
     ligate_batch_destroy(B);
     return cuda_fail(e, "batch upload");
   }
@@ -393,6 +408,7 @@ extern "C" void ligate_batch_destroy(ligate_batch *b) {
   cudaFree(b->d.atoms);
   cudaFree(b->d.bonds);
   cudaFree(b->d.elig);
+  cudaFree(b->d.cand);
   delete b;
 }
 
@@ -425,9 +441,7 @@ void start_work(const BatchDev &B, int i, int S, double &atoms, double &pairs) {
   for (int b = 0; b < d.n_rot; ++b) {
     const BondRec &r = B.h_bonds[d.bond_base + b];
     atoms += (double)S * (r.end - r.v - 1);
-    for (int a = r.v + 1; a < r.end; ++a)
-      for (int w = 0; w < d.n_words; ++w)
-        pairs += (double)S * __builtin_popcount(B.h_elig[d.elig_base + (size_t)a * d.n_words + w] & r.fixed[w]);
+    pairs += (double)S * r.n_cand;
   }
 }
 
@@ -499,6 +513,7 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   const PocketDev &d = P->d;
   memset(&p, 0, sizeof(p));
   p.lig = B->d.lig; p.atoms = B->d.atoms; p.bonds = B->d.bonds; p.elig = B->d.elig;
+  p.cand = B->d.cand;
   p.n_ligands = B->d.n_ligands;
   p.maps = mode_maps(d, mode);
   p.maps_f32 = d.map_f32;
@@ -603,7 +618,8 @@ extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate
   else read_tune_cache(p.S, mode, &pl->tile);
   default_tile(p, pl->n_ligands, sms, &pl->tile);
   ligate_tile &t = pl->tile;
-  t.warps_per_cta = std::max(1, std::min(16, t.warps_per_cta));
+  t.warps_per_cta = std::max(1, std::min(8, t.warps_per_cta));
+  t.reg_cap = t.reg_cap ? 1 : 0;
   for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
     t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
   {  // fewer warps per CTA when large ligands or many start groups need more shared memory
@@ -618,7 +634,7 @@ extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate
     set_error("plan_create: %zu B shared memory per CTA exceeds 227 KB; use fewer warps", pl->smem);
     return LIGATE_ERR_UNSUPPORTED;
   }
-  const int occ = dock_kernel_max_ctas_per_sm(mode, pl->block, pl->smem);
+  const int occ = dock_kernel_max_ctas_per_sm(mode, t.reg_cap, pl->block, pl->smem);
   if (occ < 1) {
     free_plan(pl);
     set_error("plan_create: kernel cannot be resident with %d threads, %zu B shared memory",
@@ -706,7 +722,7 @@ static ligate_status plan_capture(ligate_plan *pl) {
   cudaError_t e = cudaMemsetAsync(pl->counters, 0, pl->counter_bytes, pl->cap_stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->stats, 0, 3 * sizeof(unsigned long long), pl->cap_stream);
   if (e == cudaSuccess && pl->p.n_items > 0)
-    e = launch_dock(pl->mode, pl->p, pl->grid, pl->block, pl->smem, pl->cap_stream);
+    e = launch_dock(pl->mode, pl->tile.reg_cap, pl->p, pl->grid, pl->block, pl->smem, pl->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(pl->cap_stream, &g);
   if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "capture docking run"); }
@@ -844,6 +860,7 @@ static bool read_tune_cache(int S, int mode, ligate_tile *t) {
     memset(&r, 0, sizeof(r));
     is >> r.warps_per_cta >> r.ctas_per_sm;
     for (int b = 0; b < LIGATE_N_BUCKETS; ++b) is >> r.starts_per_item[b];
+    is >> r.reg_cap;
     if (!is) return false;
     *t = r;
     return true;
@@ -870,7 +887,7 @@ static void write_tune_cache(int S, int mode, const ligate_tile &t) {
   for (auto &l : keep) f << l << "\n";
   f << key << " " << t.warps_per_cta << " " << t.ctas_per_sm;
   for (int b = 0; b < LIGATE_N_BUCKETS; ++b) f << " " << t.starts_per_item[b];
-  f << "\n";
+  f << " " << t.reg_cap << "\n";
 }
 
 // Sub-batch of ligands `idx` (host re-packing from the packed batch).
@@ -893,6 +910,13 @@ static ligate_status sub_batch(const ligate_batch *B, const std::vector<int> &id
     ld.atom_base = (int)atoms.size();
     ld.bond_base = (int)d.h_bonds.size();
     ld.elig_base = (int)d.h_elig.size();
+    ld.cand_base = (long long)d.h_cand.size();
+    long long nc = 0;
+    for (int b = 0; b < o.n_rot; ++b) {
+      const BondRec &r = src.h_bonds[o.bond_base + b];
+      nc = std::max(nc, (long long)r.cand_off + r.n_cand);
+    }
+    for (long long c = 0; c < nc; ++c) d.h_cand.push_back(src.h_cand[o.cand_base + c]);
     for (int a = 0; a < o.n_atoms; ++a) {
       atoms.push_back(all_atoms[o.atom_base + a]);
       d.h_types.push_back(src.h_types[o.atom_base + a]);
@@ -910,10 +934,12 @@ static ligate_status sub_batch(const ligate_batch *B, const std::vector<int> &id
   if ((e = dmalloc(&d.lig, d.h_lig.size())) != cudaSuccess ||
       (e = dmalloc(&d.atoms, atoms.size())) != cudaSuccess ||
       (e = dmalloc(&d.bonds, d.h_bonds.size())) != cudaSuccess ||
-      (e = dmalloc(&d.elig, d.h_elig.size())) != cudaSuccess) {
+      (e = dmalloc(&d.elig, d.h_elig.size())) != cudaSuccess ||
+      (e = dmalloc(&d.cand, d.h_cand.size())) != cudaSuccess) {
     ligate_batch_destroy(S);
     return cuda_fail(e, "autotune sample");
   }
+  if (!d.h_cand.empty()) cudaMemcpy(d.cand, d.h_cand.data(), 2 * d.h_cand.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d.lig, d.h_lig.data(), sizeof(LigDesc) * d.h_lig.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d.atoms, atoms.data(), sizeof(float4) * atoms.size(), cudaMemcpyHostToDevice);
   if (!d.h_bonds.empty()) cudaMemcpy(d.bonds, d.h_bonds.data(), sizeof(BondRec) * d.h_bonds.size(), cudaMemcpyHostToDevice);
@@ -987,10 +1013,11 @@ extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_ba
   const int mid = std::max(G, 512 / G * G);
   double best_ms = -1;
   ligate_tile best_t = cur;
-  for (int w : {4, 8, 16}) {
+  for (int shape = 0; shape < 4; ++shape) {
     ligate_tile t;
     memset(&t, 0, sizeof(t));
-    t.warps_per_cta = w;
+    t.warps_per_cta = (shape & 1) ? 8 : 4;
+    t.reg_cap = shape >> 1;
     for (int b = 0; b < LIGATE_N_BUCKETS; ++b) t.starts_per_item[b] = mid;
     const double ms = time_tile(P, SB, s, t, 3);
     if (ms > 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; best_t = t; }

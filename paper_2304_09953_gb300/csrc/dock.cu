@@ -145,7 +145,9 @@ struct TopK {
 struct WarpSmem {
   float4 *ref;     // [nmax]  (x - c, y - c, z - c) Angstrom, .w = atom type (int bits)
   float4 *pose;    // [G][nmax + 1] current pose, grid units, .w = map offset (int bits)
-  float4 *list;    // [G][PAIR_CAP] clash pairs that survive the circle bound of a bond
+  float4 *list;    // [PAIR_WARP] clash pairs that survive the circle bound of a bond
+  float4 *cw;      // [G][nmax] radial vector of each atom about the current bond axis
+  float2 *cab;     // [G][nmax] (axial coordinate, radial distance) about that axis
   BondRec *bonds;  // [LIGATE_MAX_ROT]
   uint32_t *elig;  // [nmax * wmax]
 };
@@ -157,7 +159,7 @@ constexpr int PAIR_WARP = 128;
 
 __host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int wmax, int G) {
   return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
-         sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)nmax * wmax * 4;
+         (size_t)G * nmax * (16 + 8) + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)nmax * wmax * 4;
 }
 
 size_t dock_smem_per_warp(int nmax, int G) {
@@ -169,7 +171,9 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int
   w.ref = reinterpret_cast<float4 *>(base);
   w.pose = w.ref + nmax;
   w.list = w.pose + (size_t)G * (nmax + 1);
-  w.bonds = reinterpret_cast<BondRec *>(w.list + PAIR_WARP);
+  w.cw = w.list + PAIR_WARP;
+  w.cab = reinterpret_cast<float2 *>(w.cw + (size_t)G * nmax);
+  w.bonds = reinterpret_cast<BondRec *>(w.cab + (size_t)G * nmax);
   w.elig = reinterpret_cast<uint32_t *>(w.bonds + LIGATE_MAX_ROT);
   return w;
 }
@@ -304,8 +308,10 @@ __device__ float full_score(const DockParams &p, const void *maps, const WarpSme
 }
 
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
+// MINB = CTAs of 256 threads that must fit on one SM: 1 leaves the compiler up
+// to 255 registers, 3 caps them at 85 (more resident warps, a few spills).
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.wmax, p.G),
@@ -389,10 +395,21 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
         {
           const int cap = PAIR_WARP / G;  // = 4 L
           float4 *list = w.list + g * cap;
+          float2 *cab = w.cab + g * p.nmax;  // (axial a, radial distance b) of each atom
+          float4 *cw = w.cw + g * p.nmax;    // radial vector w of each atom
           const unsigned lmask = L == 32 ? FULL : ((1u << L) - 1u);
           const unsigned below = (1u << k) - 1u;
           const float omc = 1.f - ck;
           int cnt = 0;
+          for (int j = k; j < d.n_atoms; j += L) {
+            const float4 xj = pose[j];
+            const float fx = xj.x - pv.x, fy = xj.y - pv.y, fz = xj.z - pv.z;
+            const float a = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
+            const float wx = fmaf(-a, nx, fx), wy = fmaf(-a, ny, fy), wz = fmaf(-a, nz, fz);
+            cab[j] = make_float2(a, sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz))));
+            cw[j] = make_float4(wx, wy, wz, 0.f);
+          }
+          __syncwarp();
           auto flush = [&]() {
             __syncwarp();
             const int top = __reduce_max_sync(FULL, (unsigned)cnt);
@@ -407,40 +424,35 @@ __global__ void __launch_bounds__(512) dock_kernel(const DockParams p) {
             cnt = 0;
             __syncwarp();
           };
-          for (int i = br.v + 1; i < br.end; ++i) {
-            const float4 xi = pose[i];
-            const float ex = xi.x - pv.x, ey = xi.y - pv.y, ez = xi.z - pv.z;
-            const float ai = fmaf(ex, nx, fmaf(ey, ny, ez * nz));
-            const float ux = fmaf(-ai, nx, ex), uy = fmaf(-ai, ny, ey), uz = fmaf(-ai, nz, ez);
-            const float mx = ny * uz - nz * uy, my = nz * ux - nx * uz, mz = nx * uy - ny * ux;
-            const uint32_t *row = w.elig + i * d.n_words;
-            for (int wd = 0; wd < d.n_words; ++wd) {
-              const uint32_t cand = row[wd] & br.fixed[wd];
-              if (!cand) continue;
-              n_test += __popc(cand);
-              for (int h = 0; h < 32; h += L) {
-                bool surv = false;
-                float4 e;
-                if ((cand >> (h + k)) & 1u) {
-                  const float4 xj = pose[32 * wd + h + k];
-                  const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-                  const float D0 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                  const float fx = xj.x - pv.x, fy = xj.y - pv.y, fz = xj.z - pv.z;
-                  const float aj = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
-                  const float wx = fmaf(-aj, nx, fx), wy = fmaf(-aj, ny, fy), wz = fmaf(-aj, nz, fz);
-                  const float P = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
-                  const float Q = fmaf(mx, wx, fmaf(my, wy, mz * wz));
-                  const float s = D0 + 2.f * P - p.dc2_grid_margin;
-                  surv = s < 0.f || s * s < 4.f * fmaf(P, P, Q * Q);
-                  e = make_float4(fmaf(-D0, p.inv_dc2_grid, 1.f), -2.f * P * p.inv_dc2_grid,
-                                  2.f * Q * p.inv_dc2_grid, 0.f);
-                }
-                const unsigned gm = (__ballot_sync(FULL, surv) >> (g * L)) & lmask;
-                if (surv) list[cnt + __popc(gm & below)] = e;
-                cnt += __popc(gm);
-                if (__any_sync(FULL, cnt > cap - L)) flush();
+          // candidates of this bond, L per pass; with u = radial vector of the
+          // moved atom, the minimum distance over its circle is
+          // sqrt(da^2 + (b_j - b_i)^2)
+          const uint16_t *cand = p.cand + d.cand_base + br.cand_off;
+          n_test += br.n_cand;
+          for (int c0 = 0; c0 < br.n_cand; c0 += L) {
+            bool surv = false;
+            float4 e;
+            if (c0 + k < br.n_cand) {
+              const unsigned pr = __ldg(cand + c0 + k);
+              const int i = pr & 0xffu, j = pr >> 8;
+              const float2 hi = cab[i], hj = cab[j];
+              const float da = hi.x - hj.x, db = hj.y - hi.y;
+              surv = fmaf(da, da, db * db) < p.dc2_grid_margin;
+              if (surv) {
+                const float4 ui = cw[i], wj = cw[j];
+                const float P = fmaf(ui.x, wj.x, fmaf(ui.y, wj.y, ui.z * wj.z));
+                const float cx = ui.y * wj.z - ui.z * wj.y, cy = ui.z * wj.x - ui.x * wj.z,
+                            cz = ui.x * wj.y - ui.y * wj.x;
+                const float Q = fmaf(nx, cx, fmaf(ny, cy, nz * cz));  // (n x u).w
+                const float D0 = fmaf(da, da, fmaf(hi.y, hi.y, fmaf(hj.y, hj.y, -2.f * P)));
+                e = make_float4(fmaf(-D0, p.inv_dc2_grid, 1.f), -2.f * P * p.inv_dc2_grid,
+                                2.f * Q * p.inv_dc2_grid, 0.f);
               }
             }
+            const unsigned gm = (__ballot_sync(FULL, surv) >> (g * L)) & lmask;
+            if (surv) list[cnt + __popc(gm & below)] = e;
+            cnt += __popc(gm);
+            if (__any_sync(FULL, cnt > cap - L)) flush();
           }
           flush();
         }
@@ -628,37 +640,30 @@ __global__ void start_frames_kernel(const float4 *__restrict__ quat, int n_orien
 }
 
 // ---------------------------------------------------------------------------
-template <int MODE>
-static cudaError_t launch_dock_t(const DockParams &p, int grid, int block, size_t smem,
-                                 cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(dock_kernel<MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
+static const void *dock_fn(int mode, int reg_cap) {
+  switch (mode * 2 + (reg_cap ? 1 : 0)) {
+    case 0: return (const void *)dock_kernel<MODE_F32_PLAIN, 1>;
+    case 1: return (const void *)dock_kernel<MODE_F32_PLAIN, 3>;
+    case 2: return (const void *)dock_kernel<MODE_F32_CORNER, 1>;
+    case 3: return (const void *)dock_kernel<MODE_F32_CORNER, 3>;
+    case 4: return (const void *)dock_kernel<MODE_BF16_CORNER, 1>;
+    case 5: return (const void *)dock_kernel<MODE_BF16_CORNER, 3>;
+    case 6: return (const void *)dock_kernel<MODE_F16_CORNER, 1>;
+    default: return (const void *)dock_kernel<MODE_F16_CORNER, 3>;
   }
-  dock_kernel<MODE><<<grid, block, smem, s>>>(p);
-  return cudaGetLastError();
 }
 
-cudaError_t launch_dock(int mode, const DockParams &p, int grid, int block, size_t smem,
+cudaError_t launch_dock(int mode, int reg_cap, const DockParams &p, int grid, int block, size_t smem,
                         cudaStream_t s) {
-  switch (mode) {
-    case MODE_F32_PLAIN: return launch_dock_t<MODE_F32_PLAIN>(p, grid, block, smem, s);
-    case MODE_F32_CORNER: return launch_dock_t<MODE_F32_CORNER>(p, grid, block, smem, s);
-    case MODE_BF16_CORNER: return launch_dock_t<MODE_BF16_CORNER>(p, grid, block, smem, s);
-    default: return launch_dock_t<MODE_F16_CORNER>(p, grid, block, smem, s);
-  }
+  void *args[] = {(void *)&p};
+  return cudaLaunchKernel(dock_fn(mode, reg_cap), dim3(grid), dim3(block), args, smem, s);
 }
 
-int dock_kernel_max_ctas_per_sm(int mode, int block, size_t smem) {
+int dock_kernel_max_ctas_per_sm(int mode, int reg_cap, int block, size_t smem) {
   int n = 0;
-  const void *f = mode == MODE_F32_PLAIN ? (const void *)dock_kernel<MODE_F32_PLAIN>
-                : mode == MODE_F32_CORNER ? (const void *)dock_kernel<MODE_F32_CORNER>
-                : mode == MODE_BF16_CORNER ? (const void *)dock_kernel<MODE_BF16_CORNER>
-                : (const void *)dock_kernel<MODE_F16_CORNER>;
-  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  const void *f = dock_fn(mode, reg_cap);
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+    return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 0;
   return n;
 }

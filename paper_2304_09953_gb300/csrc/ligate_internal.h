@@ -24,16 +24,18 @@ struct LigDesc {
   int bond_base;   // first record in `bonds`
   int elig_base;   // first word of the n_atoms x n_words clash-pair bit matrix
   int n_words;     // (n_atoms + 31) / 32
-  int n_orig_rot;  // rotatable flags in the input (== n_rot)
-  int pad;
+  long long cand_base;  // first clash candidate of this ligand in `cand`
 };
 
 // One rotatable bond: u (fixed-side atom), v (child atom), end (one past the
-// subtree of v), and the "fixed side" mask (atoms outside [v, end) and != u)
-// over up to 4 words of 32 atoms.
+// subtree of v), and its clash candidates: the pairs (i, j) with i moved by
+// the bond (v < i < end), j on the fixed side (outside [v, end), j != u) and
+// at least 4 bonds apart, stored as i | j << 8 at cand[cand_base + cand_off].
+// Only these pairs change distance while the bond turns.
 struct BondRec {
-  int u, v, end, pad;
-  uint32_t fixed[4];
+  int u, v, end, n_cand;
+  int cand_off;
+  int pad[3];
 };
 
 struct BatchDev {
@@ -45,10 +47,12 @@ struct BatchDev {
   float4 *atoms = nullptr;   // [total_atoms] (x, y, z, type as int bits) DFS order
   BondRec *bonds = nullptr;  // [total_rot]
   uint32_t *elig = nullptr;  // clash-pair masks (topological distance >= 4)
+  uint16_t *cand = nullptr;  // per-bond clash candidates (see BondRec)
   // host copies used for planning
   std::vector<LigDesc> h_lig;
   std::vector<BondRec> h_bonds;
   std::vector<uint32_t> h_elig;
+  std::vector<uint16_t> h_cand;
   std::vector<uint8_t> h_types;   // per atom, DFS order
   std::vector<int32_t> h_rot;     // realised rotatable count per ligand
 };
@@ -100,6 +104,7 @@ struct DockParams {
   const float4 *atoms;
   const BondRec *bonds;
   const uint32_t *elig;
+  const uint16_t *cand;
   int n_ligands;
   // pocket
   const void *maps;        // map read by the sweep (mode)
@@ -135,7 +140,7 @@ struct DockParams {
 
 // Host launch wrappers (dock.cu).
 size_t dock_smem_per_warp(int nmax, int G);
-cudaError_t launch_dock(int mode, const DockParams &p, int grid, int block, size_t smem,
+cudaError_t launch_dock(int mode, int reg_cap, const DockParams &p, int grid, int block, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_start_frames(const double *quat_unused, const float *quat_f32_dev,
                                 int n_orient, const float *anchors_dev, int n_anchor,
@@ -144,7 +149,7 @@ cudaError_t launch_start_frames(const double *quat_unused, const float *quat_f32
 cudaError_t launch_score_poses(int mode, const DockParams &p, int n_poses, const int32_t *lig_idx,
                                const int32_t *start_id, const uint8_t *tors, float *out,
                                cudaStream_t s);
-int dock_kernel_max_ctas_per_sm(int mode, int block, size_t smem);
+int dock_kernel_max_ctas_per_sm(int mode, int reg_cap, int block, size_t smem);
 
 // Pocket kernels (pocket.cu).
 cudaError_t launch_corner_pack(const float *plain, int n_types, int nx, int ny, int nz,

@@ -60,7 +60,7 @@ assert POSE_DTYPE.itemsize == ctypes.sizeof(ligate_pose) == 24
 
 class ligate_tile(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("starts_per_item", ctypes.c_int * LIGATE_N_BUCKETS)]
+                ("starts_per_item", ctypes.c_int * LIGATE_N_BUCKETS), ("reg_cap", ctypes.c_int)]
 
 
 class ligate_work(ctypes.Structure):
