@@ -232,6 +232,32 @@ void ligate_plan_destroy(ligate_plan *plan);
 ligate_status ligate_dock_batch(const ligate_pocket *pocket, const ligate_ligands *ligands,
                                 const ligate_sampling *sampling, ligate_pose *out, void *stream);
 
+/* Allocation-free docking run.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as a serving
+ * process that reserves all device memory for its own pool at start-up, or
+ * a latency-bound loop where cudaMalloc's implicit device synchronisation
+ * is not acceptable.  It runs the same docking kernel as ligate_plan_run
+ * (same results) but keeps all of its scratch (start frames, work items,
+ * counters, partial top-K lists) in one fixed device array of
+ * LIGATE_NOALLOC_SCRATCH_BYTES inside the library, so the call allocates
+ * nothing on the device or the host heap.  pocket and batch are inputs the
+ * caller created earlier; out is DEVICE ligate_pose[n_ligands][top_k].
+ * The call only enqueues work on `stream`.
+ *  - Every GPU that loads the library holds the array until the process
+ *    exits.  The first call on a device looks up the array's device
+ *    address (once per device, with that device current); make that first
+ *    call before any stream capture.
+ *  - All calls share the array, which keeps the previous call's contents;
+ *    each call clears the counters that must start at zero.  Calls whose
+ *    GPU work overlaps (other streams, other host threads) race on it.
+ *  - Limits: n_orient <= 1024, n_anchor <= 1024, and the run's scratch
+ *    (about n_ligands * ceil(starts / 1024) * (16 + 24 * top_k) bytes) must
+ *    fit the array; larger requests return LIGATE_ERR_UNSUPPORTED with the
+ *    sizes in ligate_last_error(). */
+#define LIGATE_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+ligate_status ligate_dock_noalloc(const ligate_pocket *pocket, const ligate_batch *batch,
+                                  const ligate_sampling *sampling, ligate_pose *out, void *stream);
+
 /* Scores of explicit poses (parity checks and rescoring): pose p is ligand
  * lig_idx[p] of the batch at start start_id[p] with torsion steps
  * tors[p][LIGATE_MAX_ROT] (sweep order).  All four arrays are DEVICE

@@ -88,6 +88,7 @@ _SIGS = {
     "ligate_plan_work": (ctypes.c_int, [P, P]),
     "ligate_plan_destroy": (None, [P]),
     "ligate_dock_batch": (ctypes.c_int, [P, P, P, P, P]),
+    "ligate_dock_noalloc": (ctypes.c_int, [P, P, P, P, P]),
     "ligate_score_poses": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_autotune": (ctypes.c_int, [P, P, P, ctypes.c_double, P]),
     "ligate_descriptors": (ctypes.c_int, [P, P, P]),
@@ -256,6 +257,12 @@ def ligate_dock_batch(pocket, lig, sampling_struct, out: np.ndarray, stream=None
     s = make_ligands_struct(lig)
     check(load().ligate_dock_batch(pocket, ctypes.byref(s), ctypes.byref(sampling_struct),
                                    _ptr(out), stream), "ligate_dock_batch")
+
+
+def ligate_dock_noalloc(pocket, batch, sampling_struct, out, stream=None):
+    """Allocation-free docking run into DEVICE `out` (enqueue only)."""
+    check(load().ligate_dock_noalloc(pocket, batch, ctypes.byref(sampling_struct), _ptr(out), stream),
+          "ligate_dock_noalloc")
 
 
 def ligate_score_poses(pocket, batch, sampling_struct, n, lig_idx, start_id, tors, out, stream=None):
