@@ -199,6 +199,13 @@ typedef struct ligate_plan ligate_plan;
 ligate_status ligate_plan_create(const ligate_pocket *pocket, const ligate_batch *batch,
                                  const ligate_sampling *sampling, const ligate_tile *tile,
                                  ligate_plan **out);
+/* Plan over a subset of the batch (paper Sec. 3.5: dock only the ligands a
+ * cheaper predictor ranks best): ligands[0..n_ligands) are HOST indices into
+ * the batch; output row r holds the poses of ligand ligands[r].  Errors as
+ * ligate_plan_create, plus INVALID for an index outside the batch. */
+ligate_status ligate_plan_create_subset(const ligate_pocket *pocket, const ligate_batch *batch,
+                                        const ligate_sampling *sampling, const ligate_tile *tile,
+                                        const int32_t *ligands, int n_ligands, ligate_plan **out);
 /* Enqueue one docking run on `stream` (graph replay).  The result,
  * ligate_pose[n_ligands][top_k] in ligand order, stays in the plan's device
  * buffer (ligate_plan_output); if `out` is not NULL it is also copied there

@@ -598,17 +598,27 @@ static void default_tile(const DockParams &p, int n_ligands, int sms, ligate_til
     if (t->starts_per_item[b] <= 0) t->starts_per_item[b] = chunk;
 }
 
-extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate_batch *B,
-                                            const ligate_sampling *s, const ligate_tile *tile,
-                                            ligate_plan **out) {
+// Plan over all ligands of B (sel == NULL) or over the ligands sel[0..n_sel),
+// whose results fill output rows 0..n_sel-1 in that order.
+static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch *B,
+                                      const ligate_sampling *s, const ligate_tile *tile,
+                                      const int32_t *sel, int n_sel, ligate_plan **out) {
   if (!out) { set_error("plan_create: out is NULL"); return LIGATE_ERR_INVALID; }
   *out = nullptr;
   int mode = 0;
   ligate_status st = check_sampling(P, B, s, &mode);
   if (st != LIGATE_OK) return st;
+  if (sel) {
+    if (n_sel < 0) { set_error("plan_create_subset: negative count"); return LIGATE_ERR_INVALID; }
+    for (int r = 0; r < n_sel; ++r)
+      if (sel[r] < 0 || sel[r] >= B->d.n_ligands) {
+        set_error("plan_create_subset: index %d at position %d outside the batch", sel[r], r);
+        return LIGATE_ERR_INVALID;
+      }
+  }
   ligate_plan *pl = new ligate_plan();
   pl->mode = mode;
-  pl->n_ligands = B->d.n_ligands;
+  pl->n_ligands = sel ? n_sel : B->d.n_ligands;
   st = base_params(P, B, s, mode, pl->p, &pl->rot, &pl->anc, &pl->quat);
   if (st != LIGATE_OK) { free_plan(pl); return st; }
   DockParams &p = pl->p;
@@ -650,25 +660,28 @@ extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate
   std::vector<int> lig_items(n), lig_slot0(n);
   std::vector<double> cost;
   double poses = 0, aev = 0, pev = 0;
-  for (int i = 0; i < n; ++i) {
+  for (int r = 0; r < n; ++r) {
+    const int i = sel ? sel[r] : r;
     double a, q;
     start_work(B->d, i, p.S, a, q);
     aev += a * p.n_starts;
     pev += q * p.n_starts;
     poses += (double)p.n_starts * (1.0 + (double)B->d.h_lig[i].n_rot * (p.S - 1));
     const int chunk = t.starts_per_item[bucket_of(B->d.h_lig[i])];
-    lig_slot0[i] = (int)items.size();
+    lig_slot0[r] = (int)items.size();
     int c = 0;
     for (int s0 = 0; s0 < p.n_starts; s0 += chunk, ++c) {
       Item it;
+      memset(&it, 0, sizeof(it));
       it.ligand = i;
+      it.row = r;
       it.s0 = s0;
       it.s1 = std::min(p.n_starts, s0 + chunk);
       it.slot = (int)items.size();
       items.push_back(it);
       cost.push_back((a + 0.35 * q + 40.0) * (it.s1 - it.s0));
     }
-    lig_items[i] = c;
+    lig_items[r] = c;
   }
   pl->work.poses = poses;
   pl->work.atom_evals = aev;
@@ -712,6 +725,21 @@ extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan setup"); }
   *out = pl;
   return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_create(const ligate_pocket *P, const ligate_batch *B,
+                                            const ligate_sampling *s, const ligate_tile *tile,
+                                            ligate_plan **out) {
+  return plan_create_impl(P, B, s, tile, nullptr, 0, out);
+}
+
+extern "C" ligate_status ligate_plan_create_subset(const ligate_pocket *P, const ligate_batch *B,
+                                                   const ligate_sampling *s, const ligate_tile *tile,
+                                                   const int32_t *ligands, int n_ligands,
+                                                   ligate_plan **out) {
+  if (!ligands && n_ligands > 0) { set_error("plan_create_subset: ligands is NULL"); return LIGATE_ERR_INVALID; }
+  static const int32_t none = 0;
+  return plan_create_impl(P, B, s, tile, ligands ? ligands : &none, n_ligands, out);
 }
 
 // Capture reset + docking kernel into a graph (once per plan).

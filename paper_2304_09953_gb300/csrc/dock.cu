@@ -376,14 +376,25 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
         bond_axis(pose[br.u], pv, nx, ny, nz);
         Rot rot;
         rot.make(ck, sk, nx, ny, nz, pv.x, pv.y, pv.z);
-        // grid part: every moved atom at this lane's torsion step
-        float ag = 0.f, ac = 0.f;
-        for (int i = br.v + 1; i < br.end; ++i) {
+        // grid part: every moved atom at this lane's torsion step, two atoms
+        // per iteration so two map gathers are in flight per lane
+        float ag = 0.f, ag2 = 0.f, ac = 0.f;
+        int i = br.v + 1;
+        for (; i + 1 < br.end; i += 2) {
+          const float4 q = pose[i], q2 = pose[i + 1];
+          float yx, yy, yz, zx, zy, zz;
+          rot.apply(q.x, q.y, q.z, yx, yy, yz);
+          rot.apply(q2.x, q2.y, q2.z, zx, zy, zz);
+          ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
+          ag2 += grid_eval<MODE>(p.maps, __float_as_int(q2.w), zx, zy, zz, p.g);
+        }
+        if (i < br.end) {
           const float4 q = pose[i];
           float yx, yy, yz;
           rot.apply(q.x, q.y, q.z, yx, yy, yz);
           ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
         }
+        ag += ag2;
         n_atom += (unsigned)(br.end - br.v - 1) * (unsigned)S;
         // clash part.  Moved atom i travels on a circle about the axis; with
         // u = radial vector of i, m = n x u, w = radial vector of fixed atom
@@ -429,11 +440,13 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
           // sqrt(da^2 + (b_j - b_i)^2)
           const uint16_t *cand = p.cand + d.cand_base + br.cand_off;
           n_test += br.n_cand;
+          unsigned pr_next = k < br.n_cand ? __ldg(cand + k) : 0u;  // one pass ahead
           for (int c0 = 0; c0 < br.n_cand; c0 += L) {
             bool surv = false;
             float4 e;
+            const unsigned pr = pr_next;
+            if (c0 + L + k < br.n_cand) pr_next = __ldg(cand + c0 + L + k);
             if (c0 + k < br.n_cand) {
-              const unsigned pr = __ldg(cand + c0 + k);
               const int i = pr & 0xffu, j = pr >> 8;
               const float2 hi = cab[i], hj = cab[j];
               const float da = hi.x - hj.x, db = hj.y - hi.y;
@@ -520,13 +533,13 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
     __threadfence();
     __syncwarp();
     int prev = 0;
-    if (lane == 0) prev = atomicAdd(p.done + item.ligand, 1);
+    if (lane == 0) prev = atomicAdd(p.done + item.row, 1);
     prev = __shfl_sync(FULL, prev, 0);
-    if (prev != p.lig_items[item.ligand] - 1) continue;
+    if (prev != p.lig_items[item.row] - 1) continue;
     __threadfence();
 
     top.clear();
-    const int slot0 = p.lig_slot0[item.ligand], nit = p.lig_items[item.ligand];
+    const int slot0 = p.lig_slot0[item.row], nit = p.lig_items[item.row];
     for (int c = 0; c < nit; ++c) {
       const PoseOut *src = p.partial + (size_t)(slot0 + c) * K;
       float pe = INF;
@@ -568,7 +581,7 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
       o.score = top.e;
       o.start_id = top.s == EMPTY_SID ? -1 : top.s;
       o.tors[0] = top.t0; o.tors[1] = top.t1; o.tors[2] = top.t2; o.tors[3] = top.t3;
-      p.out[(size_t)item.ligand * K + rank] = o;
+      p.out[(size_t)item.row * K + rank] = o;
     }
   }
 }

@@ -91,11 +91,14 @@ struct PoseOut {
 };
 static_assert(sizeof(PoseOut) == sizeof(ligate_pose), "pose layout");
 
-// Work item: ligand, start range, slot of its partial top-K list.
+// Work item: ligand of the batch, output row of the run (the ligand itself,
+// or its position in a subset), start range, slot of its partial top-K list.
 struct Item {
   int ligand;
+  int row;
   int s0, s1;
   int slot;
+  int pad[3];
 };
 
 struct DockParams {

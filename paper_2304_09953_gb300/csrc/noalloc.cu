@@ -51,6 +51,8 @@ __global__ void noalloc_items_kernel(Item *__restrict__ items, int *__restrict__
     const int li = (int)(it / per_lig), c = (int)(it % per_lig);
     Item m;
     m.ligand = li;
+    m.row = li;
+    m.pad[0] = m.pad[1] = m.pad[2] = 0;
     m.s0 = c * chunk;
     m.s1 = min(n_starts, (c + 1) * chunk);
     m.slot = (int)it;

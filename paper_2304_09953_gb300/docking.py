@@ -43,7 +43,7 @@ MODES = {
 
 class Plan:
     def __init__(self, pocket: PocketHandle, batch: BatchHandle, sampling, mode="fp32", rescore=None,
-                 tile=None, top_k=None):
+                 tile=None, top_k=None, subset=None):
         prec, layout = MODES[mode]
         if rescore is None:
             rescore = prec != N.LIGATE_FP32
@@ -51,7 +51,11 @@ class Plan:
         self.k = self.s.top_k
         self.n = batch.n
         self._refs = (pocket, batch)
-        self.h = N.ligate_plan_create(pocket.h, batch.h, self.s, tile)
+        if subset is None:
+            self.h = N.ligate_plan_create(pocket.h, batch.h, self.s, tile)
+        else:
+            self.n = len(subset)
+            self.h = N.ligate_plan_create_subset(pocket.h, batch.h, self.s, subset, tile)
 
     def run(self, stream=None):
         N.ligate_plan_run(self.h, None, stream)

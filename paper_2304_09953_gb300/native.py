@@ -82,6 +82,7 @@ _SIGS = {
     "ligate_batch_get_info": (ctypes.c_int, [P, P]),
     "ligate_batch_rot_counts": (ctypes.c_int, [P, P]),
     "ligate_plan_create": (ctypes.c_int, [P, P, P, P, P]),
+    "ligate_plan_create_subset": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, P]),
     "ligate_plan_run": (ctypes.c_int, [P, P, P]),
     "ligate_plan_output": (ctypes.c_int, [P, P]),
     "ligate_plan_get_tile": (ctypes.c_int, [P, P, P]),
@@ -223,6 +224,16 @@ def ligate_plan_create(pocket, batch, sampling_struct, tile=None):
     check(load().ligate_plan_create(pocket, batch, ctypes.byref(sampling_struct),
                                     ctypes.byref(tile) if tile is not None else None,
                                     ctypes.byref(h)), "ligate_plan_create")
+    return h
+
+
+def ligate_plan_create_subset(pocket, batch, sampling_struct, ligands, tile=None):
+    h = P()
+    sel = np.ascontiguousarray(ligands, np.int32)
+    check(load().ligate_plan_create_subset(pocket, batch, ctypes.byref(sampling_struct),
+                                           ctypes.byref(tile) if tile is not None else None,
+                                           sel.ctypes.data, len(sel), ctypes.byref(h)),
+          "ligate_plan_create_subset")
     return h
 
 

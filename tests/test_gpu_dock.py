@@ -154,3 +154,18 @@ def test_largest_ligands():
     r = D.dock(P, big, samp)
     for i in range(2):
         compare_ligand(big.ligand(i), P, samp, r[i])
+
+
+def test_subset_plan_equals_rows_of_full_run(batched_small):
+    """A plan over a subset of the batch gives, row for row, the poses of
+    the same ligands in the full run."""
+    w = batched_small
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    full = D.Plan(ph, bh, w.sampling, mode="bf16").result()
+    sel = np.array([63, 5, 17, 17, 0, 42], np.int32)
+    sub = D.Plan(ph, bh, w.sampling, mode="bf16", subset=sel).result()
+    assert sub.shape == (len(sel), w.sampling.top_k)
+    assert np.array_equal(sub, full[sel])
+    with pytest.raises(N.LigateError):
+        D.Plan(ph, bh, w.sampling, mode="bf16", subset=np.array([64], np.int32))
