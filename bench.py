@@ -38,16 +38,18 @@ WORKLOAD = ("batched: 10000 ligands (N~U{15..60}, R~U{0..12}), 8x64^3 maps @0.37
             "256 orient x 32 anchors x S=16, top-16")
 # FP32 operations (FMA = 2) per unit of executed work, see the design doc:
 #   atom interpolation: 9 FMA rotation + 3 fraction subs + 7 lerps (sub + FMA) + 1 add = 43
-#   clash candidate test (once per bond): distance, axial/radial split, P, Q, bound = 40
-#   surviving clash pair, per torsion step: 2 FMA (d^2 in closed form) + 1 FMA (t^2) = 6
+#   clash candidate test (once per bond): 2 subs + mul + FMA against the circle bound = 5
+#   surviving pair set-up (once per bond): P, Q, D0 and the scaled coefficients = 33
+#   surviving pair, per torsion step: 2 FMA (d^2 in closed form) + 1 FMA (t^2) = 6
 FLOP_PER_ATOM_EVAL = 43.0
-FLOP_PER_PAIR_TEST = 40.0
+FLOP_PER_PAIR_TEST = 5.0
+FLOP_PER_PAIR_SETUP = 33.0
 FLOP_PER_PAIR_STEP = 6.0
 
 
 def executed_flops(work, S):
     return (work.done_atom_evals * FLOP_PER_ATOM_EVAL + work.done_pair_tests * FLOP_PER_PAIR_TEST
-            + work.done_pair_survivors * S * FLOP_PER_PAIR_STEP)
+            + work.done_pair_survivors * (FLOP_PER_PAIR_SETUP + S * FLOP_PER_PAIR_STEP))
 
 
 def fp32_peak_tflops(sms=152, lanes=128, mhz=2070.0):

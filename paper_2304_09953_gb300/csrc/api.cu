@@ -523,6 +523,7 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   p.n_anchor = s->n_anchor;
   p.n_starts = s->n_orient * s->n_anchor;
   p.S = s->torsion_steps;
+  fill_step_table(p.S, p.cs_tab);
   p.L = pow2ceil(s->torsion_steps);
   p.G = 32 / p.L;
   p.K = s->top_k;

@@ -153,9 +153,9 @@ struct WarpSmem {
 };
 
 // Surviving clash pairs buffered per warp before they are evaluated for
-// every torsion step: 128 entries, 128 / G = 4 L per start group (the
+// every torsion step: 256 entries, 256 / G = 8 L per start group (the
 // buffer is flushed whenever a group may overflow).
-constexpr int PAIR_WARP = 128;
+constexpr int PAIR_WARP = 256;
 
 __host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int wmax, int G) {
   return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
@@ -239,11 +239,10 @@ __device__ __forceinline__ void start_frame(const DockParams &p, int sid, float 
   for (int q = 0; q < 3; ++q) T[q] = __ldg(p.anc + 3 * a + q);
 }
 
-// cos/sin of 2 pi k / S (computed in FP64 once, rounded to FP32).
-__device__ __forceinline__ void step_cs(int k, int S, float &c, float &s) {
-  double sd, cd;
-  sincospi(2.0 * (double)k / (double)S, &sd, &cd);
-  c = (float)cd; s = (float)sd;
+// cos/sin of 2 pi k / S from the run's table (FP64 on the host, rounded).
+__device__ __forceinline__ void step_cs(const DockParams &p, int k, float &c, float &s) {
+  c = p.cs_tab[2 * k];
+  s = p.cs_tab[2 * k + 1];
 }
 
 // Full FP32 score of pose (sid, tors) of the loaded ligand, warp-cooperative,
@@ -272,7 +271,7 @@ __device__ float full_score(const DockParams &p, const void *maps, const WarpSme
     const float4 pv = buf[br.v];
     bond_axis(buf[br.u], pv, nx, ny, nz);
     float c, s;
-    step_cs(kb % p.S, p.S, c, s);
+    step_cs(p, kb % p.S, c, s);
     Rot rot;
     rot.make(c, s, nx, ny, nz, pv.x, pv.y, pv.z);
     __syncwarp();
@@ -321,7 +320,7 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
   const int glead = g * L;
   float4 *pose = w.pose + (size_t)g * (p.nmax + 1);
   float ck = 1.f, sk = 0.f;
-  if (k < S) step_cs(k, S, ck, sk);
+  if (k < S) step_cs(p, k, ck, sk);
   const int ts = type_stride(MODE, p.g);
   const float INF = __int_as_float(0x7f800000);
 
@@ -404,7 +403,7 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
         // pair whose minimum is beyond d_c contributes exactly zero at every
         // step and is dropped; the others are evaluated in closed form.
         {
-          const int cap = PAIR_WARP / G;  // = 4 L
+          const int cap = PAIR_WARP / G;  // = 8 L
           float4 *list = w.list + g * cap;
           float2 *cab = w.cab + g * p.nmax;  // (axial a, radial distance b) of each atom
           float4 *cw = w.cw + g * p.nmax;    // radial vector w of each atom
@@ -423,6 +422,23 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
           __syncwarp();
           auto flush = [&]() {
             __syncwarp();
+            // the group's lanes turn buffered pair indices into closed-form
+            // coefficients, one pair per lane
+            for (int q = k; q < cnt; q += L) {
+              const unsigned pr = __float_as_uint(list[q].w);
+              const int i = pr & 0xffu, j = pr >> 8;
+              const float2 hi = cab[i], hj = cab[j];
+              const float4 ui = cw[i], wj = cw[j];
+              const float da = hi.x - hj.x;
+              const float P = fmaf(ui.x, wj.x, fmaf(ui.y, wj.y, ui.z * wj.z));
+              const float cx = ui.y * wj.z - ui.z * wj.y, cy = ui.z * wj.x - ui.x * wj.z,
+                          cz = ui.x * wj.y - ui.y * wj.x;
+              const float Q = fmaf(nx, cx, fmaf(ny, cy, nz * cz));  // (n x u).w
+              const float D0 = fmaf(da, da, fmaf(hi.y, hi.y, fmaf(hj.y, hj.y, -2.f * P)));
+              list[q] = make_float4(fmaf(-D0, p.inv_dc2_grid, 1.f), -2.f * P * p.inv_dc2_grid,
+                                    2.f * Q * p.inv_dc2_grid, 0.f);
+            }
+            __syncwarp();
             const int top = __reduce_max_sync(FULL, (unsigned)cnt);
             for (int q = 0; q < top; ++q) {
               if (q < cnt) {
@@ -440,32 +456,30 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
           // sqrt(da^2 + (b_j - b_i)^2)
           const uint16_t *cand = p.cand + d.cand_base + br.cand_off;
           n_test += br.n_cand;
-          unsigned pr_next = k < br.n_cand ? __ldg(cand + k) : 0u;  // one pass ahead
-          for (int c0 = 0; c0 < br.n_cand; c0 += L) {
-            bool surv = false;
-            float4 e;
-            const unsigned pr = pr_next;
-            if (c0 + L + k < br.n_cand) pr_next = __ldg(cand + c0 + L + k);
-            if (c0 + k < br.n_cand) {
-              const int i = pr & 0xffu, j = pr >> 8;
-              const float2 hi = cab[i], hj = cab[j];
-              const float da = hi.x - hj.x, db = hj.y - hi.y;
-              surv = fmaf(da, da, db * db) < p.dc2_grid_margin;
-              if (surv) {
-                const float4 ui = cw[i], wj = cw[j];
-                const float P = fmaf(ui.x, wj.x, fmaf(ui.y, wj.y, ui.z * wj.z));
-                const float cx = ui.y * wj.z - ui.z * wj.y, cy = ui.z * wj.x - ui.x * wj.z,
-                            cz = ui.x * wj.y - ui.y * wj.x;
-                const float Q = fmaf(nx, cx, fmaf(ny, cy, nz * cz));  // (n x u).w
-                const float D0 = fmaf(da, da, fmaf(hi.y, hi.y, fmaf(hj.y, hj.y, -2.f * P)));
-                e = make_float4(fmaf(-D0, p.inv_dc2_grid, 1.f), -2.f * P * p.inv_dc2_grid,
-                                2.f * Q * p.inv_dc2_grid, 0.f);
-              }
+          // PASSES independent passes of L candidates per iteration: their
+          // loads and tests overlap, then the survivors are appended in order
+          constexpr int PASSES = 4;
+          for (int c0 = 0; c0 < br.n_cand; c0 += PASSES * L) {
+            unsigned pr[PASSES];
+            bool surv[PASSES];
+#pragma unroll
+            for (int u = 0; u < PASSES; ++u) {
+              const int c = c0 + u * L + k;
+              pr[u] = c < br.n_cand ? __ldg(cand + c) : 0u;
             }
-            const unsigned gm = (__ballot_sync(FULL, surv) >> (g * L)) & lmask;
-            if (surv) list[cnt + __popc(gm & below)] = e;
-            cnt += __popc(gm);
-            if (__any_sync(FULL, cnt > cap - L)) flush();
+#pragma unroll
+            for (int u = 0; u < PASSES; ++u) {
+              const float2 hi = cab[pr[u] & 0xffu], hj = cab[pr[u] >> 8];
+              const float da = hi.x - hj.x, db = hj.y - hi.y;
+              surv[u] = (c0 + u * L + k < br.n_cand) && fmaf(da, da, db * db) < p.dc2_grid_margin;
+            }
+#pragma unroll
+            for (int u = 0; u < PASSES; ++u) {
+              const unsigned gm = (__ballot_sync(FULL, surv[u]) >> (g * L)) & lmask;
+              if (surv[u]) list[cnt + __popc(gm & below)].w = __uint_as_float(pr[u]);
+              cnt += __popc(gm);
+            }
+            if (__any_sync(FULL, cnt > cap - PASSES * L)) flush();
           }
           flush();
         }

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -121,6 +122,7 @@ struct DockParams {
   // sampling
   int S, L, G;             // torsion steps, lanes per start (pow2 >= S), groups per warp
   int K;
+  float cs_tab[2 * LIGATE_MAX_STEPS];  // cos, sin of 2 pi k / S (host FP64, rounded)
   float clash_w;
   float inv_dc2_grid;      // h^2 / d_c^2
   float inv_dc2_ang;       // 1 / d_c^2
@@ -140,6 +142,16 @@ struct DockParams {
   int nmax;                // atoms capacity per warp slot (multiple of 32)
   int wmax;                // words per clash-mask row
 };
+
+// cos/sin of the S torsion steps 2 pi k / S (k = 0 exactly (1, 0)), FP64
+// rounded to FP32, into tab[2k], tab[2k + 1].
+inline void fill_step_table(int S, float *tab) {
+  for (int k = 0; k < LIGATE_MAX_STEPS; ++k) {
+    const double a = 6.283185307179586476925286766559 * (double)k / (double)S;
+    tab[2 * k] = k < S ? (float)(k == 0 ? 1.0 : std::cos(a)) : 1.f;
+    tab[2 * k + 1] = k < S ? (float)(k == 0 ? 0.0 : std::sin(a)) : 0.f;
+  }
+}
 
 // Host launch wrappers (dock.cu).
 size_t dock_smem_per_warp(int nmax, int G);

@@ -178,6 +178,7 @@ extern "C" ligate_status ligate_dock_noalloc(const ligate_pocket *P, const ligat
   p.n_anchor = s->n_anchor;
   p.n_starts = n_starts;
   p.S = s->torsion_steps; p.L = L; p.G = G; p.K = K;
+  fill_step_table(p.S, p.cs_tab);
   p.clash_w = s->clash_weight;
   const double dc2 = (double)s->clash_cutoff * s->clash_cutoff, h2 = pk.spacing * pk.spacing;
   p.inv_dc2_ang = (float)(1.0 / dc2);
