@@ -52,6 +52,19 @@ def executed_flops(work, S):
             + work.done_pair_survivors * (FLOP_PER_PAIR_SETUP + S * FLOP_PER_PAIR_STEP))
 
 
+# DRAM bytes (read + write) of one full-size launch of the chosen-form kernel,
+# from ncu (profiles/dock_kernel_bf16_batched10k.md), valid only for the
+# kernel source it was captured on (sha1 prefix of csrc/dock.cu).
+TRAFFIC_BYTES = {"c28d3039e287": 73548800 + 10424064}
+
+
+def kernel_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2304_09953_gb300", "csrc", "dock.cu")
+    sha = hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+    return TRAFFIC_BYTES.get(sha)
+
+
 def fp32_peak_tflops(sms=152, lanes=128, mhz=2070.0):
     return sms * lanes * 2 * mhz * 1e6 / 1e12
 
@@ -360,7 +373,8 @@ def main():
                   "form": "fp32 plain maps, default tile, no rescore",
                   "roofline_frac": plain_flops / (plain_ms / 1000) / 1e12 / peak},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": kernel_traffic(),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz",
                      "kernel": "dock_kernel<BF16_CORNER>",
                      "work_per_launch": {"atom_evals": work.done_atom_evals,
