@@ -36,6 +36,9 @@ sys.path.insert(0, ROOT)
 METRIC = "ligands docked/s & poses scored/s on 1 GB300, chosen vs plain form at stated error"
 WORKLOAD = ("batched: 10000 ligands (N~U{15..60}, R~U{0..12}), 8x64^3 maps @0.375 A, "
             "256 orient x 32 anchors x S=16, top-16")
+WORKLOADS = {"batched": WORKLOAD,
+             "combined": ("combined: 1000000 ligands (N log-uniform {10..80}, R~U{0..15}), "
+                          "8x96^3 maps @0.375 A, 256 orient x 32 anchors x S=16, top-16")}
 # FP32 operations (FMA = 2) per unit of executed work, see the design doc:
 #   atom interpolation: 9 FMA rotation + 3 fraction subs + 7 lerps (sub + FMA) + 1 add = 43
 #   clash candidate test (once per bond): 2 subs + mul + FMA against the circle bound = 5
@@ -55,14 +58,14 @@ def executed_flops(work, S):
 # DRAM bytes (read + write) of one full-size launch of the chosen-form kernel,
 # from ncu (profiles/dock_kernel_bf16_batched10k.md), valid only for the
 # kernel source it was captured on (sha1 prefix of csrc/dock.cu).
-TRAFFIC_BYTES = {"c28d3039e287": 73548800 + 10424064}
+TRAFFIC_BYTES = {("c28d3039e287", "batched", 10000): 73548800 + 10424064}
 
 
-def kernel_traffic():
+def kernel_traffic(workload, n_ligands):
     import hashlib
     path = os.path.join(ROOT, "paper_2304_09953_gb300", "csrc", "dock.cu")
     sha = hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
-    return TRAFFIC_BYTES.get(sha)
+    return TRAFFIC_BYTES.get((sha, workload, n_ligands))
 
 
 def fp32_peak_tflops(sms=152, lanes=128, mhz=2070.0):
@@ -75,7 +78,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n-ligands", type=int, default=10000)
+    ap.add_argument("--n-ligands", type=int, default=None,
+                    help="library size (default 10,000 batched, 1,000,000 combined)")
+    ap.add_argument("--workload", choices=["batched", "combined"], default="batched",
+                    help="batched: the 10k-ligand library of the reported line; combined: "
+                         "1M ligands, 96^3 maps, log-uniform sizes (a one-off record)")
     ap.add_argument("--tune-budget-ms", type=float, default=20000.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -84,7 +91,10 @@ def parse():
     ap.add_argument("--no-triage", action="store_true")
     ap.add_argument("--train-ligands", type=int, default=200000)
     ap.add_argument("--keep-frac", type=float, default=0.05)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.n_ligands is None:
+        a.n_ligands = 10000 if a.workload == "batched" else 1_000_000
+    return a
 
 
 def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
@@ -98,7 +108,8 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     from paper_2304_09953_gb300.workload import make_workload
 
     t0 = time.perf_counter()
-    tw = make_workload("learned_train", n_ligands=args.train_ligands, pocket=w.pocket)
+    train_cfg = "learned_train" if args.workload == "batched" else "combined_train"
+    tw = make_workload(train_cfg, n_ligands=args.train_ligands, pocket=w.pocket)
     tb = D.BatchHandle(tw.ligands)
     tp = D.Plan(ph, tb, tw.sampling, mode="fp32c")
     labels = tp.result()["score"][:, 0].copy()
@@ -271,7 +282,7 @@ def main():
     from paper_2304_09953_gb300 import native as N
     from paper_2304_09953_gb300.workload import make_workload
 
-    w = make_workload("batched", n_ligands=args.n_ligands, first_index=rank * args.n_ligands)
+    w = make_workload(args.workload, n_ligands=args.n_ligands, first_index=rank * args.n_ligands)
     tune_path = os.path.join(tempfile.gettempdir(), f"ligate_tune_{os.getpid()}.txt")
     os.environ["LIGATE_TUNE_CACHE"] = tune_path
     ph = D.PocketHandle(w.pocket)
@@ -362,7 +373,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "ligands/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "chosen: bf16 corner maps + autotuned tile + fp32 top-16 rescore",
+        "config": {"workload": WORKLOADS[args.workload],
+                   "form": "chosen: bf16 corner maps + autotuned tile + fp32 top-16 rescore",
                    "l2": "flushed (256 MB write) between timed steps",
                    "tile": {"warps_per_cta": t_.warps_per_cta, "ctas_per_sm": t_.ctas_per_sm,
                             "starts_per_item": list(t_.starts_per_item), "reg_cap": t_.reg_cap},
@@ -373,7 +385,7 @@ def main():
                   "form": "fp32 plain maps, default tile, no rescore",
                   "roofline_frac": plain_flops / (plain_ms / 1000) / 1e12 / peak},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": kernel_traffic(),
+                     "frac": achieved / peak, "traffic": kernel_traffic(args.workload, n_lig),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz",
                      "kernel": "dock_kernel<BF16_CORNER>",

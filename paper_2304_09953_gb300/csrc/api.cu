@@ -633,6 +633,19 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   t.reg_cap = t.reg_cap ? 1 : 0;
   for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
     t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
+  {  // keep the partial top-K lists (items x K poses) within 1 GiB: larger chunks for large batches
+    const double budget = 1024.0 * 1024.0 * 1024.0;
+    const int smallest = *std::min_element(t.starts_per_item, t.starts_per_item + LIGATE_N_BUCKETS);
+    const double bytes = (double)pl->n_ligands * std::ceil((double)p.n_starts / smallest) * p.K *
+                         sizeof(PoseOut);
+    if (bytes > budget) {
+      const double f = bytes / budget;
+      for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
+        const double c = std::ceil(t.starts_per_item[b] * f / p.G) * p.G;
+        t.starts_per_item[b] = (int)std::min<double>(c, std::max(p.n_starts, p.G));
+      }
+    }
+  }
   {  // fewer warps per CTA when large ligands or many start groups need more shared memory
     const size_t per_warp = dock_smem_per_warp(p.nmax, p.G);
     const int fit = (int)std::max<size_t>(1, (size_t)(227 * 1024) / per_warp);

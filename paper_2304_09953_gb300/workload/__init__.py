@@ -274,6 +274,9 @@ CONFIGS = {
     "combined": dict(seed=1004, n_ligands=1_000_000, kind=1, nmin=10, nmax=80, rmin=0, rmax=15,
                      n_types=8, grid=96, spacing=0.375, n_receptor=8000, n_orient=256, n_anchor=32,
                      steps=16, top_k=16),
+    "combined_train": dict(seed=1005, pocket_seed=1004, n_ligands=200_000, kind=1, nmin=10, nmax=80,
+                           rmin=0, rmax=15, n_types=8, grid=96, spacing=0.375, n_receptor=8000,
+                           n_orient=256, n_anchor=32, steps=16, top_k=16),
 }
 
 
