@@ -179,10 +179,10 @@ typedef struct {
  * warp's start group, 32 / pow2ceil(S)).  A zeroed field means "default". */
 #define LIGATE_N_BUCKETS 8
 typedef struct {
-  int warps_per_cta;   /* 1..8 */
+  int warps_per_cta;   /* 1..4 */
   int ctas_per_sm;
   int starts_per_item[LIGATE_N_BUCKETS];
-  int reg_cap;         /* 0: up to 255 registers per thread; 1: at most 85 (3 CTAs of 256) */
+  int reg_cap;         /* 0: at most 102 registers per thread (5 CTAs of 128 per SM); 1: at most 85 (6 CTAs) */
 } ligate_tile;
 
 /* ------------------------------------------------------------------------

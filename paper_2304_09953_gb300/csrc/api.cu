@@ -590,7 +590,7 @@ static void free_plan(ligate_plan *pl) {
 static bool read_tune_cache(int S, int mode, ligate_tile *t);
 
 static void default_tile(const DockParams &p, int n_ligands, int sms, ligate_tile *t) {
-  if (t->warps_per_cta <= 0) t->warps_per_cta = 8;
+  if (t->warps_per_cta <= 0) t->warps_per_cta = 4;
   const int total_warps = sms * std::max(1, t->ctas_per_sm > 0 ? t->ctas_per_sm : 4) * t->warps_per_cta;
   const double starts = (double)n_ligands * p.n_starts;
   int chunk = (int)std::min(2048.0, std::max(4.0 * p.G, starts / (4.0 * total_warps)));
@@ -629,7 +629,7 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   else read_tune_cache(p.S, mode, &pl->tile);
   default_tile(p, pl->n_ligands, sms, &pl->tile);
   ligate_tile &t = pl->tile;
-  t.warps_per_cta = std::max(1, std::min(8, t.warps_per_cta));
+  t.warps_per_cta = std::max(1, std::min(4, t.warps_per_cta));
   t.reg_cap = t.reg_cap ? 1 : 0;
   for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
     t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
@@ -1058,7 +1058,7 @@ extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_ba
   for (int shape = 0; shape < 4; ++shape) {
     ligate_tile t;
     memset(&t, 0, sizeof(t));
-    t.warps_per_cta = (shape & 1) ? 8 : 4;
+    t.warps_per_cta = (shape & 1) ? 4 : 2;
     t.reg_cap = shape >> 1;
     for (int b = 0; b < LIGATE_N_BUCKETS; ++b) t.starts_per_item[b] = mid;
     const double ms = time_tile(P, SB, s, t, 3);

@@ -146,20 +146,19 @@ struct WarpSmem {
   float4 *ref;     // [nmax]  (x - c, y - c, z - c) Angstrom, .w = atom type (int bits)
   float4 *pose;    // [G][nmax + 1] current pose, grid units, .w = map offset (int bits)
   float4 *list;    // [PAIR_WARP] clash pairs that survive the circle bound of a bond
-  float4 *cw;      // [G][nmax] radial vector of each atom about the current bond axis
-  float2 *cab;     // [G][nmax] (axial coordinate, radial distance) about that axis
+  float2 *cab;     // [G][nmax] (axial coordinate, radial distance) about the bond axis
   BondRec *bonds;  // [LIGATE_MAX_ROT]
-  uint32_t *elig;  // [nmax * wmax]
 };
 
 // Surviving clash pairs buffered per warp before they are evaluated for
-// every torsion step: 256 entries, 256 / G = 8 L per start group (the
+// every torsion step: 192 entries, 192 / G = 6 L per start group (the
 // buffer is flushed whenever a group may overflow).
-constexpr int PAIR_WARP = 256;
+constexpr int PAIR_WARP = 192;
 
 __host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int wmax, int G) {
+  (void)wmax;
   return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
-         (size_t)G * nmax * (16 + 8) + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)nmax * wmax * 4;
+         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT;
 }
 
 size_t dock_smem_per_warp(int nmax, int G) {
@@ -171,10 +170,8 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int
   w.ref = reinterpret_cast<float4 *>(base);
   w.pose = w.ref + nmax;
   w.list = w.pose + (size_t)G * (nmax + 1);
-  w.cw = w.list + PAIR_WARP;
-  w.cab = reinterpret_cast<float2 *>(w.cw + (size_t)G * nmax);
+  w.cab = reinterpret_cast<float2 *>(w.list + PAIR_WARP);
   w.bonds = reinterpret_cast<BondRec *>(w.cab + (size_t)G * nmax);
-  w.elig = reinterpret_cast<uint32_t *>(w.bonds + LIGATE_MAX_ROT);
   return w;
 }
 
@@ -207,13 +204,12 @@ __device__ float load_ligand(const DockParams &p, const WarpSmem &w, int li, Lig
     w.ref[i] = a;
   }
   for (int b = lane; b < d.n_rot; b += 32) w.bonds[b] = p.bonds[d.bond_base + b];
-  for (int q = lane; q < d.n_atoms * d.n_words; q += 32) w.elig[q] = __ldg(p.elig + d.elig_base + q);
   __syncwarp();
   float cl = 0.f;
   for (int i = lane; i < d.n_atoms; i += 32) {
     const float4 xi = w.ref[i];
     for (int wd = 0; wd < d.n_words; ++wd) {
-      uint32_t m = w.elig[i * d.n_words + wd];
+      uint32_t m = __ldg(p.elig + d.elig_base + i * d.n_words + wd);
       const int lo = i + 1 - 32 * wd;  // keep only j > i
       if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
       while (m) {
@@ -287,7 +283,7 @@ __device__ float full_score(const DockParams &p, const void *maps, const WarpSme
     const float4 xi = buf[i];
     e += grid_eval<MODE>(maps, __float_as_int(xi.w), xi.x, xi.y, xi.z, p.g);
     for (int wd = 0; wd < d.n_words; ++wd) {
-      uint32_t m = w.elig[i * d.n_words + wd];
+      uint32_t m = __ldg(p.elig + d.elig_base + i * d.n_words + wd);
       const int lo = i + 1 - 32 * wd;
       if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
       while (m) {
@@ -307,10 +303,12 @@ __device__ float full_score(const DockParams &p, const void *maps, const WarpSme
 }
 
 // ---------------------------------------------------------------------------
-// MINB = CTAs of 256 threads that must fit on one SM: 1 leaves the compiler up
-// to 255 registers, 3 caps them at 85 (more resident warps, a few spills).
+// CTAs of at most 128 threads; MINB of them must fit on one SM: 5 caps the
+// registers at 102 (20 resident warps), 6 at 85 (24 warps, a few spills).
+// Latency of the map gathers is covered by resident warps, so occupancy
+// matters more than per-thread registers here.
 template <int MODE, int MINB>
-__global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
+__global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.wmax, p.G),
@@ -403,10 +401,9 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
         // pair whose minimum is beyond d_c contributes exactly zero at every
         // step and is dropped; the others are evaluated in closed form.
         {
-          const int cap = PAIR_WARP / G;  // = 8 L
+          const int cap = PAIR_WARP / G;  // = 6 L
           float4 *list = w.list + g * cap;
           float2 *cab = w.cab + g * p.nmax;  // (axial a, radial distance b) of each atom
-          float4 *cw = w.cw + g * p.nmax;    // radial vector w of each atom
           const unsigned lmask = L == 32 ? FULL : ((1u << L) - 1u);
           const unsigned below = (1u << k) - 1u;
           const float omc = 1.f - ck;
@@ -417,7 +414,6 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
             const float a = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
             const float wx = fmaf(-a, nx, fx), wy = fmaf(-a, ny, fy), wz = fmaf(-a, nz, fz);
             cab[j] = make_float2(a, sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz))));
-            cw[j] = make_float4(wx, wy, wz, 0.f);
           }
           __syncwarp();
           auto flush = [&]() {
@@ -428,7 +424,12 @@ __global__ void __launch_bounds__(256, MINB) dock_kernel(const DockParams p) {
               const unsigned pr = __float_as_uint(list[q].w);
               const int i = pr & 0xffu, j = pr >> 8;
               const float2 hi = cab[i], hj = cab[j];
-              const float4 ui = cw[i], wj = cw[j];
+              const float4 xi = pose[i], xj = pose[j];
+              // radial vectors about the axis: w = (x - p) - a n
+              const float4 ui = make_float4(fmaf(-hi.x, nx, xi.x - pv.x), fmaf(-hi.x, ny, xi.y - pv.y),
+                                            fmaf(-hi.x, nz, xi.z - pv.z), 0.f);
+              const float4 wj = make_float4(fmaf(-hj.x, nx, xj.x - pv.x), fmaf(-hj.x, ny, xj.y - pv.y),
+                                            fmaf(-hj.x, nz, xj.z - pv.z), 0.f);
               const float da = hi.x - hj.x;
               const float P = fmaf(ui.x, wj.x, fmaf(ui.y, wj.y, ui.z * wj.z));
               const float cx = ui.y * wj.z - ui.z * wj.y, cy = ui.z * wj.x - ui.x * wj.z,
@@ -669,14 +670,14 @@ __global__ void start_frames_kernel(const float4 *__restrict__ quat, int n_orien
 // ---------------------------------------------------------------------------
 static const void *dock_fn(int mode, int reg_cap) {
   switch (mode * 2 + (reg_cap ? 1 : 0)) {
-    case 0: return (const void *)dock_kernel<MODE_F32_PLAIN, 1>;
-    case 1: return (const void *)dock_kernel<MODE_F32_PLAIN, 3>;
-    case 2: return (const void *)dock_kernel<MODE_F32_CORNER, 1>;
-    case 3: return (const void *)dock_kernel<MODE_F32_CORNER, 3>;
-    case 4: return (const void *)dock_kernel<MODE_BF16_CORNER, 1>;
-    case 5: return (const void *)dock_kernel<MODE_BF16_CORNER, 3>;
-    case 6: return (const void *)dock_kernel<MODE_F16_CORNER, 1>;
-    default: return (const void *)dock_kernel<MODE_F16_CORNER, 3>;
+    case 0: return (const void *)dock_kernel<MODE_F32_PLAIN, 5>;
+    case 1: return (const void *)dock_kernel<MODE_F32_PLAIN, 6>;
+    case 2: return (const void *)dock_kernel<MODE_F32_CORNER, 5>;
+    case 3: return (const void *)dock_kernel<MODE_F32_CORNER, 6>;
+    case 4: return (const void *)dock_kernel<MODE_BF16_CORNER, 5>;
+    case 5: return (const void *)dock_kernel<MODE_BF16_CORNER, 6>;
+    case 6: return (const void *)dock_kernel<MODE_F16_CORNER, 5>;
+    default: return (const void *)dock_kernel<MODE_F16_CORNER, 6>;
   }
 }
 
