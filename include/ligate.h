@@ -334,6 +334,14 @@ ligate_status ligate_surrogate_grad(const ligate_surrogate *s, const float *x, c
                                     int b, float *grad, float *loss_out, void *stream);
 /* Copy the FP32 master weights (host [LIGATE_SURROGATE_PARAMS]). */
 ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s, float *out);
+/* Contraction engine chosen at creation: 1 when the forward layers and the
+ * data gradients run on tcgen05 (TMA-fed, TMEM accumulators), 0 when they
+ * run on the mma.sync kernels (environment LIGATE_MLP_GEMM=mma at creation
+ * selects these; both use the same operands and rounding points), -1 for
+ * a NULL handle.  Weight gradients always use mma.sync.  A tcgen05 wait
+ * that runs out makes train/grad/predict/rank return LIGATE_ERR_TIMEOUT;
+ * predict then returns only after its kernels have finished. */
+int ligate_surrogate_engine(const ligate_surrogate *s);
 
 #if defined(__GNUC__)
 #pragma GCC visibility pop

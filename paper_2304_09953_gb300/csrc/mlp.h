@@ -41,5 +41,16 @@ cudaError_t unstd(float *y, int n, float mu, float sd, cudaStream_t s);
 cudaError_t sort_select(const float *pred, int n, int k, unsigned long long *keys, int n2,
                         int32_t *idx, cudaStream_t s);
 
+// tcgen05 path (mlp_tc05.cu) for K-major A [M][K] and B [N][K]:
+// C[M][N] = epi(A B^T), epi EPI_BIAS_RELU or EPI_RELU_MASK; needs N % 256 == 0,
+// K % 64 == 0, 16-byte aligned pointers.  *err is set to 1 when a bounded
+// wait ran out (results then undefined).
+bool tc05_supported(int M, int N, int K);
+cudaError_t gemm_tc05(int epi, const __nv_bfloat16 *a, int M, int K, const __nv_bfloat16 *b, int N,
+                      const float *bias, const __nv_bfloat16 *mask, __nv_bfloat16 *out, int *err,
+                      cudaStream_t s);
+// wt[n][k] = bf16(w[k][n]) for row-major FP32 w [K][N].
+cudaError_t transpose_bf16(const float *w, int K, int N, __nv_bfloat16 *wt, cudaStream_t s);
+
 }  // namespace mlp
 }  // namespace ligate

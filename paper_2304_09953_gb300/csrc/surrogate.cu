@@ -5,6 +5,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "ligate_internal.h"
@@ -113,6 +115,12 @@ struct ligate_surrogate {
   float *t = nullptr, *y = nullptr, *dy = nullptr;
   int *idx = nullptr;
   int idx_cap = 0;
+  // tcgen05 path: transposed BF16 hidden weights W1^T [512][256], W2^T,
+  // W3^T [512][512] (K-major B operands of the forward layers) and the
+  // timeout flag of its bounded waits
+  bool tc05 = false;
+  __nv_bfloat16 *wt = nullptr;
+  int *err = nullptr;
 };
 
 namespace {
@@ -143,6 +151,34 @@ cudaError_t ensure_work(ligate_surrogate *s, int rows) {
   return cudaSuccess;
 }
 
+constexpr int TW1 = 0, TW2 = TW1 + F0 * F1, TW3 = TW2 + F1 * F1, NTW = TW3 + F1 * F1;
+
+// Re-derive the transposed BF16 forward weights from the FP32 masters.
+cudaError_t refresh_wt(ligate_surrogate *s, cudaStream_t st) {
+  if (!s->tc05) return cudaSuccess;
+  cudaError_t e;
+  if ((e = mlp::transpose_bf16(s->w + OW1, F0, F1, s->wt + TW1, st))) return e;
+  if ((e = mlp::transpose_bf16(s->w + OW2, F1, F1, s->wt + TW2, st))) return e;
+  return mlp::transpose_bf16(s->w + OW3, F1, F1, s->wt + TW3, st);
+}
+
+// LIGATE_OK, or LIGATE_ERR_TIMEOUT once a tcgen05 wait ran out (flag
+// cleared); synchronises st.
+ligate_status check_err(ligate_surrogate *s, cudaStream_t st, const char *what) {
+  if (!s->tc05) return LIGATE_OK;
+  int h = 0;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(&h, s->err, 4, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+    return cuda_fail(e, what);
+  if (h) {
+    cudaMemsetAsync(s->err, 0, 4, st);
+    cudaStreamSynchronize(st);
+    set_error("%s: a tensor-core pipeline wait ran out", what);
+    return LIGATE_ERR_TIMEOUT;
+  }
+  return LIGATE_OK;
+}
+
 mlp::GemmArgs fwd_args(const __nv_bfloat16 *in, int fan_in, const __nv_bfloat16 *W, const float *b,
                        __nv_bfloat16 *out, int rows) {
   mlp::GemmArgs a{};
@@ -155,6 +191,15 @@ mlp::GemmArgs fwd_args(const __nv_bfloat16 *in, int fan_in, const __nv_bfloat16 
 // Forward of the hidden layers on x (standardised BF16 rows).
 cudaError_t forward_hidden(ligate_surrogate *s, int rows, cudaStream_t st) {
   cudaError_t e;
+  if (s->tc05) {
+    if ((e = mlp::gemm_tc05(mlp::EPI_BIAS_RELU, s->x, rows, F0, s->wt + TW1, F1, s->w + OB1, nullptr, s->h1,
+                            s->err, st)) ||
+        (e = mlp::gemm_tc05(mlp::EPI_BIAS_RELU, s->h1, rows, F1, s->wt + TW2, F1, s->w + OB2, nullptr, s->h2,
+                            s->err, st)))
+      return e;
+    return mlp::gemm_tc05(mlp::EPI_BIAS_RELU, s->h2, rows, F1, s->wt + TW3, F1, s->w + OB3, nullptr, s->h3,
+                          s->err, st);
+  }
   if ((e = mlp::gemm(mlp::GEMM_FWD, fwd_args(s->x, F0, s->wb + OW1, s->w + OB1, s->h1, rows), st))) return e;
   if ((e = mlp::gemm(mlp::GEMM_FWD, fwd_args(s->h1, F1, s->wb + OW2, s->w + OB2, s->h2, rows), st))) return e;
   return mlp::gemm(mlp::GEMM_FWD, fwd_args(s->h2, F1, s->wb + OW3, s->w + OB3, s->h3, rows), st);
@@ -180,7 +225,12 @@ cudaError_t backward(ligate_surrogate *s, int rows, cudaStream_t st) {
       dg.A = l.dz; dg.B = s->wb + l.ow; dg.M = rows; dg.N = l.fan_in; dg.K = F1;
       dg.sAm = F1; dg.sAk = 1; dg.sBk = 1; dg.sBn = F1;
       dg.mask = l.hin; dg.Cb = l.dz_prev; dg.ldc = l.fan_in;
-      if ((e = mlp::gemm(mlp::GEMM_DGRAD, dg, st))) return e;
+      if (s->tc05)  // B[n][k] = W[n][k]: the row-major weights are already K-major here
+        e = mlp::gemm_tc05(mlp::EPI_RELU_MASK, l.dz, rows, F1, s->wb + l.ow, l.fan_in, nullptr, l.hin,
+                           l.dz_prev, s->err, st);
+      else
+        e = mlp::gemm(mlp::GEMM_DGRAD, dg, st);
+      if (e) return e;
     }
   }
   return cudaSuccess;
@@ -226,6 +276,16 @@ extern "C" ligate_status ligate_surrogate_create(const float *init, uint64_t see
     ligate_surrogate_destroy(s);
     return cuda_fail(e, "surrogate_create");
   }
+  // K-major contractions on tcgen05 unless LIGATE_MLP_GEMM=mma selects the
+  // mma.sync kernels (same operands and rounding points; used to compare)
+  const char *sel = getenv("LIGATE_MLP_GEMM");
+  s->tc05 = !(sel && strcmp(sel, "mma") == 0) && mlp::tc05_supported(1, F1, F0);
+  if (s->tc05 &&
+      ((e = cudaMalloc(&s->wt, (size_t)NTW * 2)) || (e = cudaMalloc(&s->err, 4)) ||
+       (e = cudaMemset(s->err, 0, 4)) || (e = refresh_wt(s, 0)) || (e = cudaDeviceSynchronize()))) {
+    ligate_surrogate_destroy(s);
+    return cuda_fail(e, "surrogate_create");
+  }
   std::vector<float> mu(F0, 0.f), one(F0, 1.f);
   cudaMemcpy(s->mu, mu.data(), F0 * 4, cudaMemcpyHostToDevice);
   cudaMemcpy(s->inv_sd, one.data(), F0 * 4, cudaMemcpyHostToDevice);
@@ -238,6 +298,7 @@ extern "C" void ligate_surrogate_destroy(ligate_surrogate *s) {
   free_work(s);
   cudaFree(s->w); cudaFree(s->m); cudaFree(s->v); cudaFree(s->g); cudaFree(s->wb);
   cudaFree(s->mu); cudaFree(s->inv_sd); cudaFree(s->lstat); cudaFree(s->sse); cudaFree(s->idx);
+  cudaFree(s->wt); cudaFree(s->err);
   delete s;
 }
 
@@ -294,12 +355,14 @@ extern "C" ligate_status ligate_surrogate_train(ligate_surrogate *s, const float
                          s->sse, s->dz3, st)) ||
           (e = backward(s, batch, st)) ||
           (e = mlp::adam(s->w, s->g, s->m, s->v, s->wb, NPAR, lr, 0.9f, 0.999f, 1e-8f, (float)c1,
-                         (float)c2, st)))
+                         (float)c2, st)) ||
+          (e = refresh_wt(s, st)))
         return cuda_fail(e, "surrogate step");
     }
     double sse = 0.0;
     if ((e = cudaMemcpyAsync(&sse, s->sse, 8, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
       return cuda_fail(e, "surrogate epoch");
+    if (ligate_status r = check_err(s, st, "surrogate epoch")) return r;
     last = steps > 0 ? sse / ((double)steps * batch) : 0.0;
   }
   if (loss_out) *loss_out = (float)last;
@@ -323,6 +386,7 @@ extern "C" ligate_status ligate_surrogate_grad(const ligate_surrogate *cs, const
       (e = cudaMemcpyAsync(grad, s->g, NPAR * 4, cudaMemcpyDeviceToDevice, st)) ||
       (e = cudaMemcpyAsync(&sse, s->sse, 8, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
     return cuda_fail(e, "surrogate_grad");
+  if (ligate_status r = check_err(s, st, "surrogate_grad")) return r;
   if (loss_out) *loss_out = (float)(sse / b);
   return LIGATE_OK;
 }
@@ -344,7 +408,7 @@ extern "C" ligate_status ligate_surrogate_predict(const ligate_surrogate *cs, co
         (e = mlp::unstd(pred + r0, rows, (float)s->label_mu, (float)s->label_sd, st)))
       return cuda_fail(e, "surrogate_predict");
   }
-  return LIGATE_OK;
+  return check_err(s, st, "surrogate_predict");
 }
 
 extern "C" ligate_status ligate_surrogate_rank(const ligate_surrogate *s, const float *desc, int n,
@@ -384,3 +448,5 @@ extern "C" ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s,
   if (e != cudaSuccess) return cuda_fail(e, "surrogate_get_weights");
   return LIGATE_OK;
 }
+
+extern "C" int ligate_surrogate_engine(const ligate_surrogate *s) { return s ? (s->tc05 ? 1 : 0) : -1; }

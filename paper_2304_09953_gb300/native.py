@@ -101,6 +101,7 @@ _SIGS = {
     "ligate_surrogate_rank": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_double, P, P, P]),
     "ligate_surrogate_grad": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P]),
     "ligate_surrogate_get_weights": (ctypes.c_int, [P, P]),
+    "ligate_surrogate_engine": (ctypes.c_int, [P]),
 }
 
 _lib = None
@@ -332,3 +333,8 @@ def ligate_surrogate_get_weights(h):
     out = np.zeros(LIGATE_SURROGATE_PARAMS, np.float32)
     check(load().ligate_surrogate_get_weights(h, out.ctypes.data), "ligate_surrogate_get_weights")
     return out
+
+
+def ligate_surrogate_engine(h):
+    """1: tcgen05 contractions, 0: mma.sync (LIGATE_MLP_GEMM=mma at creation)."""
+    return int(load().ligate_surrogate_engine(h))

@@ -169,3 +169,36 @@ def test_subset_plan_equals_rows_of_full_run(batched_small):
     assert np.array_equal(sub, full[sel])
     with pytest.raises(N.LigateError):
         D.Plan(ph, bh, w.sampling, mode="bf16", subset=np.array([64], np.int32))
+
+
+def test_host_array_call_equals_plan_path(batched_small):
+    """ligate_dock_batch (pack, upload, dock, download in one call) returns
+    the plan path's poses."""
+    w = batched_small
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    want = D.Plan(ph, bh, w.sampling, mode="fp16").result()
+    s = N.make_sampling(w.sampling, N.LIGATE_FP16, N.LIGATE_LAYOUT_CORNER, rescore=True)
+    got = np.zeros_like(want)
+    N.ligate_dock_batch(ph.h, w.ligands, s, got)
+    assert np.array_equal(got, want)
+
+
+def test_autotune_cache_round_trip(batched_small, tmp_path, monkeypatch):
+    """The tuned shape is written to LIGATE_TUNE_CACHE and picked up by a
+    plan created without an explicit tile; results do not depend on it."""
+    w = batched_small
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("LIGATE_TUNE_CACHE", str(path))
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    s = N.make_sampling(w.sampling, N.LIGATE_BF16, N.LIGATE_LAYOUT_CORNER, rescore=True)
+    best = N.ligate_autotune(ph.h, bh.h, s, 5000.0)
+    assert path.exists() and len(path.read_text().split()) == 12
+    pl = D.Plan(ph, bh, w.sampling, mode="bf16")
+    t, launches = pl.tile()
+    assert launches == 1
+    assert t.warps_per_cta == best.warps_per_cta and t.reg_cap == best.reg_cap
+    assert list(t.starts_per_item) == list(best.starts_per_item)
+    ref = D.Plan(ph, bh, w.sampling, mode="bf16", tile=N.ligate_tile()).result()
+    assert np.array_equal(pl.result(), ref)

@@ -56,14 +56,17 @@ def test_descriptors_match_oracle(batched_small):
         np.testing.assert_array_equal(np.round(np.expm1(got[i])), np.round(np.expm1(want)))
 
 
-def test_forward_and_gradients_match_oracle():
+@pytest.mark.parametrize("engine,B", [("tc05", 256), ("tc05", 200), ("mma", 256), ("mma", 200)])
+def test_forward_and_gradients_match_oracle(engine, B, monkeypatch):
+    """Both contraction engines; B = 200 leaves a ragged 72-row tile."""
+    monkeypatch.setenv("LIGATE_MLP_GEMM", engine)
     rng = np.random.default_rng(3)
     wf = omlp.bf16_round(he_weights(5))
-    B = 256
     x = omlp.bf16_round(rng.normal(size=(B, 256)).astype(np.float32))
     t = rng.normal(size=B).astype(np.float32)
     s = N.ligate_surrogate_create(wf, 0)
     try:
+        assert N.ligate_surrogate_engine(s) == (1 if engine == "tc05" else 0)
         xd = torch.from_numpy(x).cuda()
         td = torch.from_numpy(t).cuda()
         g = torch.zeros(N.LIGATE_SURROGATE_PARAMS, dtype=torch.float32, device="cuda")
@@ -91,6 +94,37 @@ def test_forward_and_gradients_match_oracle():
         assert np.linalg.norm(yp - y) / np.linalg.norm(y) <= 1e-3
     finally:
         N.ligate_surrogate_destroy(s)
+
+
+def test_tcgen05_and_mma_engines_agree(monkeypatch):
+    """Same weights, two engines: predictions over 70,001 rows (three
+    32,768-row chunks, ragged last tile) and the weights after two epochs of
+    training.  Only FP32 summation order differs, so BF16 activations may
+    differ by one unit in rare elements."""
+    rng = np.random.default_rng(12)
+    wf = he_weights(13)
+    n = 70001
+    desc = torch.from_numpy(rng.normal(size=(n, 256)).astype(np.float32)).cuda()
+    lab = torch.from_numpy(rng.normal(size=n).astype(np.float32)).cuda()
+    preds, weights = [], []
+    for engine in ("tc05", "mma"):
+        monkeypatch.setenv("LIGATE_MLP_GEMM", engine)
+        s = N.ligate_surrogate_create(wf, 0)
+        try:
+            assert N.ligate_surrogate_engine(s) == (1 if engine == "tc05" else 0)
+            pred = torch.zeros(n, dtype=torch.float32, device="cuda")
+            N.ligate_surrogate_predict(s, desc, n, pred)
+            preds.append(pred.cpu().numpy().astype(np.float64))
+            N.ligate_surrogate_train(s, desc[:8192], lab[:8192], 8192, 2, 1024, 1e-3, 5)
+            weights.append(N.ligate_surrogate_get_weights(s).astype(np.float64))
+        finally:
+            N.ligate_surrogate_destroy(s)
+    a, b = preds
+    assert np.all(np.isfinite(a))
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 2e-3
+    assert np.max(np.abs(a - b)) <= 2e-2 * np.max(np.abs(b))
+    d0 = weights[1] - wf.astype(np.float64)
+    assert np.linalg.norm(weights[0] - weights[1]) <= 5e-2 * np.linalg.norm(d0)
 
 
 def test_first_adam_step_follows_gradient_sign():
