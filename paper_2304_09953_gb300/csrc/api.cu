@@ -647,12 +647,12 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
     }
   }
   {  // fewer warps per CTA when large ligands or many start groups need more shared memory
-    const size_t per_warp = dock_smem_per_warp(p.nmax, p.G);
+    const size_t per_warp = dock_smem_per_warp(p.nmax, p.S, p.G);
     const int fit = (int)std::max<size_t>(1, (size_t)(227 * 1024) / per_warp);
     t.warps_per_cta = std::min(t.warps_per_cta, fit);
   }
   pl->block = 32 * t.warps_per_cta;
-  pl->smem = dock_smem_per_warp(p.nmax, p.G) * t.warps_per_cta;
+  pl->smem = dock_smem_per_warp(p.nmax, p.S, p.G) * t.warps_per_cta;
   if (pl->smem > 227 * 1024) {
     free_plan(pl);
     set_error("plan_create: %zu B shared memory per CTA exceeds 227 KB; use fewer warps", pl->smem);

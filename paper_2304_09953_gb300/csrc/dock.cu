@@ -45,7 +45,7 @@ __device__ __forceinline__ float grid_eval(const void *__restrict__ maps, int to
     v0 = __ldg(m); v1 = __ldg(m + 1); v2 = __ldg(m + sy); v3 = __ldg(m + sy + 1);
     v4 = __ldg(m + sz); v5 = __ldg(m + sz + 1); v6 = __ldg(m + sz + sy); v7 = __ldg(m + sz + sy + 1);
   } else {
-    const size_t cell = (size_t)toff + ((size_t)iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+    const int cell = toff + (iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;  // < 2^28: host limit
     if (MODE == MODE_F32_CORNER) {
       const float4 *m = (const float4 *)maps + 2 * cell;
       const float4 a = __ldg(m), b = __ldg(m + 1);
@@ -148,6 +148,7 @@ struct WarpSmem {
   float4 *list;    // [PAIR_WARP] clash pairs that survive the circle bound of a bond
   float2 *cab;     // [G][nmax] (axial coordinate, radial distance) about the bond axis
   BondRec *bonds;  // [LIGATE_MAX_ROT]
+  float *memo;     // [memo_floats(S)] clash sums of the first bonds' sweeps
 };
 
 // Surviving clash pairs buffered per warp before they are evaluated for
@@ -155,23 +156,32 @@ struct WarpSmem {
 // buffer is flushed whenever a group may overflow).
 constexpr int PAIR_WARP = 192;
 
-__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int wmax, int G) {
-  (void)wmax;
+// The clash term of a bond's sweep depends only on the ligand's internal
+// conformation, which before bond b is set by the steps chosen at bonds
+// 0 .. b-1.  Bond 0 therefore sweeps the same conformation for every start
+// and bond 1 one of S conformations: their clash sums are computed once per
+// ligand (S values for bond 0, S x S for bond 1 when S <= 16) and looked up
+// by every start.
+__host__ __device__ inline int memo_bonds(int S) { return S <= 16 ? 2 : 1; }
+__host__ __device__ inline int memo_floats(int S) {
+  return S <= 0 ? 0 : (S + (memo_bonds(S) == 2 ? S * S : 0) + 3) / 4 * 4;
+}
+
+__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int S, int G) {
   return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
-         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT;
+         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)memo_floats(S) * 4;
 }
 
-size_t dock_smem_per_warp(int nmax, int G) {
-  return smem_bytes_per_warp(nmax, (nmax + 31) / 32, G);
-}
+size_t dock_smem_per_warp(int nmax, int S, int G) { return smem_bytes_per_warp(nmax, S, G); }
 
-__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int wmax, int G) {
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int G) {
   WarpSmem w;
   w.ref = reinterpret_cast<float4 *>(base);
   w.pose = w.ref + nmax;
   w.list = w.pose + (size_t)G * (nmax + 1);
   w.cab = reinterpret_cast<float2 *>(w.list + PAIR_WARP);
   w.bonds = reinterpret_cast<BondRec *>(w.cab + (size_t)G * nmax);
+  w.memo = reinterpret_cast<float *>(w.bonds + LIGATE_MAX_ROT);
   return w;
 }
 
@@ -302,6 +312,157 @@ __device__ float full_score(const DockParams &p, const void *maps, const WarpSme
   return fmaf(p.clash_w, cl, e);
 }
 
+// Clash part of the sweep of bond br at this lane's torsion step (ck, sk):
+// the sum over the bond's crossing candidate pairs of max(0, 1 - d^2/d_c^2)^2
+// on the group's conformation `pose` (grid units; axis n through pv).
+// Moved atom i travels on a circle about the axis; with
+// u = radial vector of i, m = n x u, w = radial vector of fixed atom
+// j, P = u.w, Q = m.w and D0 = |x_i - x_j|^2 at the current pose,
+//   d^2(theta) = D0 + 2P (1 - cos theta) - 2Q sin theta,
+// whose minimum over the circle is D0 + 2P - 2 sqrt(P^2 + Q^2).  A
+// pair whose minimum is beyond d_c contributes exactly zero at every
+// step and is dropped; the others are evaluated in closed form.
+// Warp-collective: every lane calls it, each with its own group's data.
+__device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem &w, const float4 *pose,
+                                             const LigDesc &d, const BondRec &br, float nx, float ny,
+                                             float nz, const float4 &pv, float ck, float sk, int g,
+                                             int k, int L, int G, unsigned &n_test, unsigned &n_pair) {
+  float ac = 0.f;
+  const int cap = PAIR_WARP / G;  // = 6 L
+  float4 *list = w.list + g * cap;
+  float2 *cab = w.cab + g * p.nmax;  // (axial a, radial distance b) of each atom
+  const unsigned lmask = L == 32 ? FULL : ((1u << L) - 1u);
+  const unsigned below = (1u << k) - 1u;
+  const float omc = 1.f - ck;
+  int cnt = 0;
+  for (int j = k; j < d.n_atoms; j += L) {
+    const float4 xj = pose[j];
+    const float fx = xj.x - pv.x, fy = xj.y - pv.y, fz = xj.z - pv.z;
+    const float a = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
+    const float wx = fmaf(-a, nx, fx), wy = fmaf(-a, ny, fy), wz = fmaf(-a, nz, fz);
+    cab[j] = make_float2(a, sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz))));
+  }
+  __syncwarp();
+  auto flush = [&]() {
+    __syncwarp();
+    // the group's lanes turn buffered pair indices into closed-form
+    // coefficients, one pair per lane
+    for (int q = k; q < cnt; q += L) {
+      const unsigned pr = __float_as_uint(list[q].w);
+      const int i = pr & 0xffu, j = pr >> 8;
+      const float2 hi = cab[i], hj = cab[j];
+      const float4 xi = pose[i], xj = pose[j];
+      // radial vectors about the axis: w = (x - p) - a n
+      const float4 ui = make_float4(fmaf(-hi.x, nx, xi.x - pv.x), fmaf(-hi.x, ny, xi.y - pv.y),
+                                    fmaf(-hi.x, nz, xi.z - pv.z), 0.f);
+      const float4 wj = make_float4(fmaf(-hj.x, nx, xj.x - pv.x), fmaf(-hj.x, ny, xj.y - pv.y),
+                                    fmaf(-hj.x, nz, xj.z - pv.z), 0.f);
+      const float da = hi.x - hj.x;
+      const float P = fmaf(ui.x, wj.x, fmaf(ui.y, wj.y, ui.z * wj.z));
+      const float cx = ui.y * wj.z - ui.z * wj.y, cy = ui.z * wj.x - ui.x * wj.z,
+                  cz = ui.x * wj.y - ui.y * wj.x;
+      const float Q = fmaf(nx, cx, fmaf(ny, cy, nz * cz));  // (n x u).w
+      const float D0 = fmaf(da, da, fmaf(hi.y, hi.y, fmaf(hj.y, hj.y, -2.f * P)));
+      list[q] = make_float4(fmaf(-D0, p.inv_dc2_grid, 1.f), -2.f * P * p.inv_dc2_grid,
+                            2.f * Q * p.inv_dc2_grid, 0.f);
+    }
+    __syncwarp();
+    const int top = __reduce_max_sync(FULL, (unsigned)cnt);
+    for (int q = 0; q < top; ++q) {
+      if (q < cnt) {
+        const float4 e = list[q];
+        const float t = fmaxf(0.f, fmaf(e.z, sk, fmaf(e.y, omc, e.x)));
+        ac = fmaf(t, t, ac);
+      }
+    }
+    n_pair += cnt;
+    cnt = 0;
+    __syncwarp();
+  };
+  // candidates of this bond, L per pass; with u = radial vector of the
+  // moved atom, the minimum distance over its circle is
+  // sqrt(da^2 + (b_j - b_i)^2)
+  const uint16_t *cand = p.cand + d.cand_base + br.cand_off;
+  n_test += br.n_cand;
+  // PASSES independent passes of L candidates per iteration: their
+  // loads and tests overlap, then the survivors are appended in order
+  constexpr int PASSES = 4;
+  for (int c0 = 0; c0 < br.n_cand; c0 += PASSES * L) {
+    unsigned pr[PASSES];
+    bool surv[PASSES];
+#pragma unroll
+    for (int u = 0; u < PASSES; ++u) {
+      const int c = c0 + u * L + k;
+      pr[u] = c < br.n_cand ? __ldg(cand + c) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < PASSES; ++u) {
+      const float2 hi = cab[pr[u] & 0xffu], hj = cab[pr[u] >> 8];
+      const float da = hi.x - hj.x, db = hj.y - hi.y;
+      surv[u] = (c0 + u * L + k < br.n_cand) && fmaf(da, da, db * db) < p.dc2_grid_margin;
+    }
+#pragma unroll
+    for (int u = 0; u < PASSES; ++u) {
+      const unsigned gm = (__ballot_sync(FULL, surv[u]) >> (g * L)) & lmask;
+      if (surv[u]) list[cnt + __popc(gm & below)].w = __uint_as_float(pr[u]);
+      cnt += __popc(gm);
+    }
+    if (__any_sync(FULL, cnt > cap - PASSES * L)) flush();
+  }
+  flush();
+  return ac;
+}
+
+// Clash sums of the first n_memo bonds' sweeps into w.memo: memo[k] for
+// bond 0 on the input conformation, memo[S + k0 S + k] for bond 1 after
+// bond 0 turned by step k0.  Conformations are posed by start 0's frame
+// (the clash term is invariant under the rigid move); group g takes
+// k0 = g, g + G, ...  Warp-collective.
+__device__ void build_memo(const DockParams &p, const WarpSmem &w, float4 *pose, const LigDesc &d,
+                           int n_memo, float ck, float sk, int g, int k, int L, int G, int S) {
+  unsigned n_test = 0, n_pair = 0;  // not counted: once per ligand
+  float R[9], T[3];
+  start_frame(p, 0, R, T);
+  const int rounds = n_memo == 2 ? (S + G - 1) / G : 0;
+  for (int r = -1; r < rounds; ++r) {  // r = -1: bond 0 on the input conformation
+    for (int i = k; i < d.n_atoms; i += L) {
+      const float4 a = w.ref[i];
+      pose[i] = make_float4(fmaf(R[0], a.x, fmaf(R[1], a.y, fmaf(R[2], a.z, T[0]))),
+                            fmaf(R[3], a.x, fmaf(R[4], a.y, fmaf(R[5], a.z, T[1]))),
+                            fmaf(R[6], a.x, fmaf(R[7], a.y, fmaf(R[8], a.z, T[2]))), 0.f);
+    }
+    __syncwarp();
+    const BondRec b0 = w.bonds[0];
+    float nx, ny, nz;
+    float4 pv = pose[b0.v];
+    bond_axis(pose[b0.u], pv, nx, ny, nz);
+    if (r < 0) {
+      const float ac = clash_sweep(p, w, pose, d, b0, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
+      if (g == 0 && k < S) w.memo[k] = ac;
+      __syncwarp();
+      continue;
+    }
+    const int k0 = min(r * G + g, S - 1);  // groups past S repeat the last step
+    float c0, s0;
+    step_cs(p, k0, c0, s0);
+    Rot rb;
+    rb.make(c0, s0, nx, ny, nz, pv.x, pv.y, pv.z);
+    __syncwarp();
+    for (int i = b0.v + 1 + k; i < b0.end; i += L) {
+      float4 q = pose[i];
+      rb.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+      pose[i] = q;
+    }
+    __syncwarp();
+    const BondRec b1 = w.bonds[1];
+    pv = pose[b1.v];
+    bond_axis(pose[b1.u], pv, nx, ny, nz);
+    const float ac = clash_sweep(p, w, pose, d, b1, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
+    if (r * G + g < S && k < S) w.memo[S + k0 * S + k] = ac;
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // CTAs of at most 128 threads; MINB of them must fit on one SM: 5 caps the
 // registers at 102 (20 resident warps), 6 at 85 (24 warps, a few spills).
@@ -311,8 +472,8 @@ template <int MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.wmax, p.G),
-                               p.nmax, p.wmax, p.G);
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.S, p.G),
+                               p.nmax, p.G);
   const int L = p.L, G = p.G, S = p.S, K = p.K;
   const int g = lane / L, k = lane - g * L;
   const int glead = g * L;
@@ -322,7 +483,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
   const int ts = type_stride(MODE, p.g);
   const float INF = __int_as_float(0x7f800000);
 
-  int cur = -1;
+  int cur = -1, n_memo = 0;
   LigDesc d;
   float clash_ref = 0.f;
   TopK top;
@@ -337,6 +498,8 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
       __syncwarp();
       clash_ref = load_ligand(p, w, item.ligand, d, lane);
       cur = item.ligand;
+      n_memo = min(d.n_rot, memo_bonds(S));
+      if (n_memo > 0) build_memo(p, w, pose, d, n_memo, ck, sk, g, k, L, G, S);
     }
     top.clear();
     unsigned n_atom = 0, n_test = 0, n_pair = 0;  // work counters of this lane's group
@@ -375,7 +538,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         rot.make(ck, sk, nx, ny, nz, pv.x, pv.y, pv.z);
         // grid part: every moved atom at this lane's torsion step, two atoms
         // per iteration so two map gathers are in flight per lane
-        float ag = 0.f, ag2 = 0.f, ac = 0.f;
+        float ag = 0.f, ag2 = 0.f;
         int i = br.v + 1;
         for (; i + 1 < br.end; i += 2) {
           const float4 q = pose[i], q2 = pose[i + 1];
@@ -393,96 +556,11 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         }
         ag += ag2;
         n_atom += (unsigned)(br.end - br.v - 1) * (unsigned)S;
-        // clash part.  Moved atom i travels on a circle about the axis; with
-        // u = radial vector of i, m = n x u, w = radial vector of fixed atom
-        // j, P = u.w, Q = m.w and D0 = |x_i - x_j|^2 at the current pose,
-        //   d^2(theta) = D0 + 2P (1 - cos theta) - 2Q sin theta,
-        // whose minimum over the circle is D0 + 2P - 2 sqrt(P^2 + Q^2).  A
-        // pair whose minimum is beyond d_c contributes exactly zero at every
-        // step and is dropped; the others are evaluated in closed form.
-        {
-          const int cap = PAIR_WARP / G;  // = 6 L
-          float4 *list = w.list + g * cap;
-          float2 *cab = w.cab + g * p.nmax;  // (axial a, radial distance b) of each atom
-          const unsigned lmask = L == 32 ? FULL : ((1u << L) - 1u);
-          const unsigned below = (1u << k) - 1u;
-          const float omc = 1.f - ck;
-          int cnt = 0;
-          for (int j = k; j < d.n_atoms; j += L) {
-            const float4 xj = pose[j];
-            const float fx = xj.x - pv.x, fy = xj.y - pv.y, fz = xj.z - pv.z;
-            const float a = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
-            const float wx = fmaf(-a, nx, fx), wy = fmaf(-a, ny, fy), wz = fmaf(-a, nz, fz);
-            cab[j] = make_float2(a, sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz))));
-          }
-          __syncwarp();
-          auto flush = [&]() {
-            __syncwarp();
-            // the group's lanes turn buffered pair indices into closed-form
-            // coefficients, one pair per lane
-            for (int q = k; q < cnt; q += L) {
-              const unsigned pr = __float_as_uint(list[q].w);
-              const int i = pr & 0xffu, j = pr >> 8;
-              const float2 hi = cab[i], hj = cab[j];
-              const float4 xi = pose[i], xj = pose[j];
-              // radial vectors about the axis: w = (x - p) - a n
-              const float4 ui = make_float4(fmaf(-hi.x, nx, xi.x - pv.x), fmaf(-hi.x, ny, xi.y - pv.y),
-                                            fmaf(-hi.x, nz, xi.z - pv.z), 0.f);
-              const float4 wj = make_float4(fmaf(-hj.x, nx, xj.x - pv.x), fmaf(-hj.x, ny, xj.y - pv.y),
-                                            fmaf(-hj.x, nz, xj.z - pv.z), 0.f);
-              const float da = hi.x - hj.x;
-              const float P = fmaf(ui.x, wj.x, fmaf(ui.y, wj.y, ui.z * wj.z));
-              const float cx = ui.y * wj.z - ui.z * wj.y, cy = ui.z * wj.x - ui.x * wj.z,
-                          cz = ui.x * wj.y - ui.y * wj.x;
-              const float Q = fmaf(nx, cx, fmaf(ny, cy, nz * cz));  // (n x u).w
-              const float D0 = fmaf(da, da, fmaf(hi.y, hi.y, fmaf(hj.y, hj.y, -2.f * P)));
-              list[q] = make_float4(fmaf(-D0, p.inv_dc2_grid, 1.f), -2.f * P * p.inv_dc2_grid,
-                                    2.f * Q * p.inv_dc2_grid, 0.f);
-            }
-            __syncwarp();
-            const int top = __reduce_max_sync(FULL, (unsigned)cnt);
-            for (int q = 0; q < top; ++q) {
-              if (q < cnt) {
-                const float4 e = list[q];
-                const float t = fmaxf(0.f, fmaf(e.z, sk, fmaf(e.y, omc, e.x)));
-                ac = fmaf(t, t, ac);
-              }
-            }
-            n_pair += cnt;
-            cnt = 0;
-            __syncwarp();
-          };
-          // candidates of this bond, L per pass; with u = radial vector of the
-          // moved atom, the minimum distance over its circle is
-          // sqrt(da^2 + (b_j - b_i)^2)
-          const uint16_t *cand = p.cand + d.cand_base + br.cand_off;
-          n_test += br.n_cand;
-          // PASSES independent passes of L candidates per iteration: their
-          // loads and tests overlap, then the survivors are appended in order
-          constexpr int PASSES = 4;
-          for (int c0 = 0; c0 < br.n_cand; c0 += PASSES * L) {
-            unsigned pr[PASSES];
-            bool surv[PASSES];
-#pragma unroll
-            for (int u = 0; u < PASSES; ++u) {
-              const int c = c0 + u * L + k;
-              pr[u] = c < br.n_cand ? __ldg(cand + c) : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < PASSES; ++u) {
-              const float2 hi = cab[pr[u] & 0xffu], hj = cab[pr[u] >> 8];
-              const float da = hi.x - hj.x, db = hj.y - hi.y;
-              surv[u] = (c0 + u * L + k < br.n_cand) && fmaf(da, da, db * db) < p.dc2_grid_margin;
-            }
-#pragma unroll
-            for (int u = 0; u < PASSES; ++u) {
-              const unsigned gm = (__ballot_sync(FULL, surv[u]) >> (g * L)) & lmask;
-              if (surv[u]) list[cnt + __popc(gm & below)].w = __uint_as_float(pr[u]);
-              cnt += __popc(gm);
-            }
-            if (__any_sync(FULL, cnt > cap - PASSES * L)) flush();
-          }
-          flush();
+        float ac;
+        if (b < n_memo) {  // looked up: bond 0, or bond 1 after bond 0's step
+          ac = k < S ? w.memo[b == 0 ? k : S + (int)(t0 & 0xffu) * S + k] : 0.f;
+        } else {
+          ac = clash_sweep(p, w, pose, d, br, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
         }
         const float V = (k < S) ? fmaf(p.clash_w, ac, ag) : INF;
         float best = V;
@@ -611,8 +689,7 @@ __global__ void __launch_bounds__(256) score_poses_kernel(const DockParams p, in
                                                           float *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.wmax, 1),
-                               p.nmax, p.wmax, 1);
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1), p.nmax, 1);
   const int pi = blockIdx.x * (blockDim.x >> 5) + warp;
   if (pi >= n_poses) return;
   const int li = lig_idx[pi], sid = start_id[pi];
@@ -711,7 +788,7 @@ static cudaError_t launch_score_t(const DockParams &p, int n_poses, const int32_
                                   const int32_t *start_id, const uint8_t *tors, float *out,
                                   cudaStream_t s) {
   const int warps = 4;
-  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, p.wmax, 1);
+  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1);
   cudaError_t e = cudaFuncSetAttribute(score_poses_kernel<MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;

@@ -154,7 +154,7 @@ inline void fill_step_table(int S, float *tab) {
 }
 
 // Host launch wrappers (dock.cu).
-size_t dock_smem_per_warp(int nmax, int G);
+size_t dock_smem_per_warp(int nmax, int S, int G);
 cudaError_t launch_dock(int mode, int reg_cap, const DockParams &p, int grid, int block, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_start_frames(const double *quat_unused, const float *quat_f32_dev,
