@@ -58,7 +58,7 @@ def executed_flops(work, S):
 # DRAM bytes (read + write) of one full-size launch of the chosen-form kernel,
 # from ncu (profiles/dock_kernel_bf16_batched10k.md), valid only for the
 # kernel source it was captured on (sha1 prefix of csrc/dock.cu).
-TRAFFIC_BYTES = {("1047d1fddd32", "batched", 10000): 73302528 + 10253568}
+TRAFFIC_BYTES = {("30881babca3d", "batched", 10000): 73092352 + 10049792}
 
 
 def kernel_traffic(workload, n_ligands):
