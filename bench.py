@@ -99,12 +99,16 @@ def parse():
 
 def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     """Surrogate triage (paper Sec. 3.5): train the MLP on the plain-method
-    best scores of a separate seeded training library (same pocket), then
-    per step: descriptors of the batch, rank, dock the kept fraction with the
-    chosen form.  Recall of the plain FP32 top 1% among the kept ligands."""
+    best scores of a separate seeded training library (same pocket), holding
+    out 10% to calibrate the keep fraction that reaches 0.99 recall of the
+    held-out top 1%; then per step: descriptors of the batch, rank, dock the
+    kept fraction with the chosen form.  Timed at the fixed --keep-frac and at
+    the calibrated fraction; recall of the plain FP32 top 1% of the library
+    among the kept ligands."""
     import torch
     from paper_2304_09953_gb300 import docking as D
     from paper_2304_09953_gb300 import native as N
+    from paper_2304_09953_gb300 import triage as T
     from paper_2304_09953_gb300.workload import make_workload
 
     t0 = time.perf_counter()
@@ -116,53 +120,81 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     tp.close()
     t_label = time.perf_counter() - t0
     n_tr = tw.ligands.n
+    n_cal = n_tr // 10
+    n_fit = n_tr - n_cal
     desc_tr = torch.empty((n_tr, 256), dtype=torch.float32, device="cuda")
     N.ligate_descriptors(tb.h, desc_tr, sh)
     lab = torch.from_numpy(labels).cuda()
     sur = N.ligate_surrogate_create(None, 1003)
     t1 = time.perf_counter()
-    loss = N.ligate_surrogate_train(sur, desc_tr, lab, n_tr, 20, 1024, 1e-3, 1003, sh)
+    loss = N.ligate_surrogate_train(sur, desc_tr[:n_fit], lab[:n_fit], n_fit, 20, 1024, 1e-3, 1003, sh)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    del desc_tr, lab
+    pred_cal = torch.empty(n_cal, dtype=torch.float32, device="cuda")
+    N.ligate_surrogate_predict(sur, desc_tr[n_fit:], n_cal, pred_cal, sh)
+    torch.cuda.synchronize()
+    keep_cal = T.keep_for_recall(pred_cal.cpu().numpy(), labels[n_fit:], 0.99)
+    del desc_tr, lab, pred_cal
     tb.close()
 
     n = w.ligands.n
-    k = int(np.ceil(n * args.keep_frac))
     desc = torch.empty((n, 256), dtype=torch.float32, device="cuda")
-    idx_dev = torch.empty(k, dtype=torch.int32, device="cuda")
+    pred_all = torch.empty(n, dtype=torch.float32, device="cuda")
 
-    def step():
-        N.ligate_descriptors(bh.h, desc, sh)
-        N.ligate_surrogate_rank(sur, desc, n, args.keep_frac, idx_dev, None, sh)
-        sel = idx_dev.cpu().numpy()
-        pl = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile, subset=sel)
-        res = pl.result(sh)
-        pl.close()
-        return sel, res
+    def timed(keep):
+        k = int(np.ceil(n * keep - 1e-9))
+        idx_dev = torch.empty(max(k, 1), dtype=torch.int32, device="cuda")
 
-    for _ in range(2):
-        step()
-    times = []
-    for _ in range(max(1, args.steps)):
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        sel, res = step()
-        times.append(time.perf_counter() - a)
-    N.ligate_surrogate_destroy(sur)
+        def step():
+            N.ligate_descriptors(bh.h, desc, sh)
+            N.ligate_surrogate_rank(sur, desc, n, keep, idx_dev, None, sh)
+            sel = idx_dev[:k].cpu().numpy()
+            pl = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile, subset=sel)
+            pl.result(sh)
+            pl.close()
+            return sel
+
+        for _ in range(2):
+            step()
+        times = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            sel = step()
+            times.append(time.perf_counter() - a)
+        return k, sel, statistics.mean(times)
+
+    k, sel, t = timed(args.keep_frac)
     truth_scores = plain.result(sh)["score"][:, 0]
-    top = int(np.ceil(0.01 * n))
-    truth = set(np.lexsort((np.arange(n), truth_scores))[:top].tolist())
-    recall = len(truth & set(sel.tolist())) / top
-    flex = set(np.argsort(-w.ligands.n_rot, kind="stable")[:k].tolist())
-    t = statistics.mean(times)
-    return {"value": n / t, "unit": "ligands/s", "ms_per_step": 1000 * t, "keep_frac": args.keep_frac,
-            "docked_per_step": k, "recall_top1pct": recall,
-            "recall_top1pct_most_rotatable_bonds_5pct": len(truth & flex) / top,
-            "recall_target": 0.99, "meets_target": recall >= 0.99,
-            "train_ligands": n_tr, "train_epochs": 20, "final_train_loss": loss,
-            "label_docking_s": round(t_label, 2), "train_s": round(t_train, 2),
-            "form": "descriptors + MLP rank (bf16 tensor cores) + dock kept 5% (bf16 maps, fp32 rescore)"}
+    N.ligate_surrogate_rank(sur, desc, n, args.keep_frac, torch.empty(max(k, 1), dtype=torch.int32,
+                            device="cuda"), pred_all, sh)
+    pred = pred_all.cpu().numpy()
+    rec = T.recall(truth_scores, sel)
+    flex = np.argsort(-w.ligands.n_rot, kind="stable")[:k]
+    out = {"value": n / t, "unit": "ligands/s", "ms_per_step": 1000 * t, "keep_frac": args.keep_frac,
+           "docked_per_step": k, "recall_top1pct": rec,
+           "recall_top1pct_most_rotatable_bonds_first": T.recall(truth_scores, flex),
+           "recall_curve": {str(f): round(r, 4) for f, r in
+                            T.recall_curve(pred, truth_scores, [0.05, 0.1, 0.2, 0.3, 0.5, 0.7]).items()},
+           "keep_needed_on_library_for_0.99": round(T.keep_for_recall(pred, truth_scores, 0.99), 4),
+           "recall_target": 0.99, "meets_target": rec >= 0.99,
+           "train_ligands": n_fit, "calibration_ligands": n_cal, "train_epochs": 20,
+           "final_train_loss": loss, "label_docking_s": round(t_label, 2), "train_s": round(t_train, 2),
+           "form": "descriptors + MLP rank (bf16 tensor cores) + dock kept fraction (bf16 maps, fp32 rescore)"}
+    if keep_cal < 1.0:
+        kc, selc, tc = timed(keep_cal)
+        recc = T.recall(truth_scores, selc)
+        out["at_calibrated_keep"] = {
+            "value": n / tc, "unit": "ligands/s", "ms_per_step": 1000 * tc,
+            "keep_frac": round(keep_cal, 4), "docked_per_step": kc, "recall_top1pct": recc,
+            "meets_target": recc >= 0.99,
+            "note": "keep fraction reaching 0.99 recall of the top 1% on the held-out 10% of the "
+                    "training library"}
+    else:
+        out["at_calibrated_keep"] = {"keep_frac": 1.0, "note": "calibration needs the whole library: "
+                                     "triage gives no speed-up at 0.99 recall"}
+    N.ligate_surrogate_destroy(sur)
+    return out
 
 
 class Clocks:
