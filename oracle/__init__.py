@@ -73,6 +73,8 @@ def _load():
         lib.or_greedy.argtypes = [P, P, P, I, P, P, P, I, P]
         lib.or_exhaustive.argtypes = [P, P, P, I, P, P]
         lib.or_descriptor.argtypes = [P, I, P]
+        lib.or_pose_grad.argtypes = [P, P, P, I, P, P, P, P, P, P]
+        lib.or_refine.argtypes = [P, P, P, I, P, I, D, P, D, P, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -278,3 +280,68 @@ def descriptor(lig, n_types: int = 8) -> np.ndarray:
     if lib.or_descriptor(_ref(L), n_types, out.ctypes.data):
         raise ValueError("descriptor needs 8 atom types")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Pose refinement (see the refinement section of ligate_oracle.c).  A state
+# is a row [R (9, row-major), t (3, Angstrom), phi (nrot, radians)].
+
+def docked_state(sampling, anchors, start, tors) -> np.ndarray:
+    """State of docked pose (start, tors): R of the start's orientation
+    quaternion, t = its anchor, phi_b = 2 pi tors[b] / S."""
+    o, a = divmod(int(start), int(sampling.n_anchor))
+    R = quat_to_matrix(np.asarray(sampling.quats)[o])
+    t = np.asarray(anchors, np.float64)[a]
+    phi = 2.0 * np.pi * np.asarray(tors, np.float64) / sampling.torsion_steps
+    return np.concatenate([R.reshape(-1), t, phi])
+
+
+def pose_grad(lig, pocket, sampling, states):
+    """E, generalised gradient (F, tau, psi), error scales (of E, then of
+    each gradient component), moments (I_R, I_b) and the smallest cell-face
+    distance of any atom, for each state row."""
+    lib = _load()
+    k = _Keep()
+    L = _lig(k, *lig)
+    P = _pock(k, pocket)
+    S = _samp(k, sampling, pocket.anchors)
+    st = _c(np.atleast_2d(states), np.float64)
+    n, w = st.shape
+    nr = w - 12
+    e = np.zeros(n)
+    g = np.zeros((n, 6 + nr))
+    sc = np.zeros((n, 7 + nr))
+    inert = np.zeros((n, 1 + nr))
+    face = np.zeros(n)
+    if lib.or_pose_grad(_ref(L), _ref(P), _ref(S), n, st.ctypes.data, e.ctypes.data, g.ctypes.data,
+                        sc.ctypes.data, inert.ctypes.data, face.ctypes.data):
+        raise ValueError("ligand bonds do not form a tree")
+    return e, g, sc, inert, face
+
+
+def refine(lig, pocket, sampling, states, iters, eta0, follow=None, tie_rel=1e-4):
+    """Gradient-descent refinement of each state row for `iters` iterations.
+    With `follow` (accept masks, one per row) the oracle takes those
+    decisions and counts the ones that contradict its own beyond a near-tie.
+    Returns dict(states, e_in, e_out, own_mask, n_disagree, scale)."""
+    lib = _load()
+    k = _Keep()
+    L = _lig(k, *lig)
+    P = _pock(k, pocket)
+    S = _samp(k, sampling, pocket.anchors)
+    st = _c(np.atleast_2d(states), np.float64)
+    n = st.shape[0]
+    out = np.zeros_like(st)
+    e_in, e_out, scale = np.zeros(n), np.zeros(n), np.zeros(n)
+    mask = np.zeros(n, np.uint32)
+    dis = np.zeros(n, np.int32)
+    fol = None if follow is None else _c(follow, np.uint32)
+    rc = lib.or_refine(_ref(L), _ref(P), _ref(S), n, st.ctypes.data, int(iters), float(eta0),
+                       None if fol is None else fol.ctypes.data, float(tie_rel), out.ctypes.data,
+                       e_in.ctypes.data, e_out.ctypes.data, mask.ctypes.data, dis.ctypes.data,
+                       scale.ctypes.data)
+    if rc:
+        raise ValueError("bad refinement arguments")
+    return {"states": out, "e_in": e_in, "e_out": e_out, "own_mask": mask, "n_disagree": dis,
+            "scale": scale}
+

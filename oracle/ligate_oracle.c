@@ -507,6 +507,320 @@ OR_EXPORT int or_exhaustive(const or_ligand_in *li, const or_pocket_in *pi, cons
 }
 
 /* ------------------------------------------------------------------------ */
+/* Pose refinement by gradient descent (paper Sec. 2: the docking search is  */
+/* a gradient descent from multiple restarts; here the greedy sweep supplies */
+/* the restarts and a local descent refines the best poses).  Readings:      */
+/*                                                                           */
+/*   state q = (R, t, phi): x_i = R (y_i - c) + t, with y the input          */
+/*       conformation after torsion angle phi_b (radians) is applied to each */
+/*       rotatable bond b in sweep order about its current axis u->v (as in  */
+/*       pose(s, tors), with continuous angles; phi_b = 0 leaves the bond),  */
+/*       c the input centroid, R a rotation matrix, t in Angstrom.           */
+/*   E(q)    : the docking score of x (grid terms, penalty, clash term).     */
+/*   g_i     : dE/dx_i.  Grid: derivative of the trilinear interpolant in    */
+/*       the atom's cell (the cell the value uses), divided by h; zero for   */
+/*       an atom scoring the penalty.  Clash: -4 w t (x_i - x_j) / d_c^2     */
+/*       for every pair with t = 1 - d_ij^2/d_c^2 > 0.                       */
+/*   generalised gradient: the derivatives of E along a translation, a       */
+/*       rotation exp([w]x) R about t, and a turn of bond b:                 */
+/*         F = sum_i g_i,   tau = sum_i (x_i - t) x g_i,                     */
+/*         psi_b = n_b . sum_{i moved by b} (x_i - x_v) x g_i,               */
+/*       n_b the unit axis u->v of bond b at the pose.                       */
+/*   descent : scaled steepest descent with step control.  The trial from q  */
+/*       is t' = t - eta F / N, R' = GS(Rot(-eta tau / I_R) R) and           */
+/*       phi'_b = phi_b - eta psi_b / I_b, with I_R = 1 + sum_i |x_i - t|^2  */
+/*       and I_b = 1 + sum_{i moved by b} |(x_i - x_v) minus its component   */
+/*       along n_b|^2 (A^2, the moments that turn a unit angle into atom     */
+/*       displacement); GS re-orthonormalises the rows (r0 normalised, r1    */
+/*       made orthogonal to r0 and normalised, r2 = r0 x r1).  The trial is  */
+/*       accepted if E(trial) < E(q), and eta grows by 1.25; otherwise it is */
+/*       rejected and eta halves.  A fixed number of iterations.             */
+
+typedef struct {
+  double R[9], t[3], phi[64];
+} or_state;
+
+static void state_coords(const or_lig *L, const or_state *q, double (*x)[3]) {
+  for (int a = 0; a < L->n; ++a)
+    for (int d = 0; d < 3; ++d) x[a][d] = L->ref[a][d];
+  for (int b = 0; b < L->nrot; ++b)
+    if (q->phi[b] != 0.0) apply_torsion(L, b, q->phi[b], x);
+  for (int a = 0; a < L->n; ++a) {
+    double v[3] = {x[a][0] - L->centroid[0], x[a][1] - L->centroid[1], x[a][2] - L->centroid[2]};
+    for (int d = 0; d < 3; ++d)
+      x[a][d] = q->R[3 * d] * v[0] + q->R[3 * d + 1] * v[1] + q->R[3 * d + 2] * v[2] + q->t[d];
+  }
+}
+
+/* Trilinear value of map t at x (same arithmetic as trilinear()) and its
+ * gradient with respect to x; *face = distance (grid units) of u to the
+ * nearest face of its cell, or a large value for a penalty atom. */
+static double trilinear_grad(const or_pocket *P, int t, const double x[3], double g[3],
+                             double *face) {
+  int dims[3] = {P->nx, P->ny, P->nz};
+  double u[3];
+  int c[3];
+  g[0] = g[1] = g[2] = 0.0;
+  *face = 1e30;
+  for (int d = 0; d < 3; ++d) {
+    u[d] = (x[d] - P->origin[d]) / P->h;
+    if (!(u[d] >= 0.0 && u[d] <= (double)(dims[d] - 1))) return P->penalty;
+    int f = (int)floor(u[d]);
+    c[d] = f < dims[d] - 2 ? f : dims[d] - 2;
+  }
+  double fx = u[0] - c[0], fy = u[1] - c[1], fz = u[2] - c[2];
+  for (int d = 0; d < 3; ++d) {
+    double fr = u[d] - floor(u[d]);
+    double dd = fr < 1.0 - fr ? fr : 1.0 - fr;
+    if (dd < *face) *face = dd;
+  }
+  const float *m = P->maps + (size_t)t * P->nx * P->ny * P->nz;
+#define V(i, j, k) ((double)m[((size_t)(c[2] + (k)) * P->ny + (c[1] + (j))) * P->nx + (c[0] + (i))])
+  double v000 = V(0, 0, 0), v100 = V(1, 0, 0), v010 = V(0, 1, 0), v110 = V(1, 1, 0);
+  double v001 = V(0, 0, 1), v101 = V(1, 0, 1), v011 = V(0, 1, 1), v111 = V(1, 1, 1);
+#undef V
+  double y0z0 = lerp(v000, v100, fx), y1z0 = lerp(v010, v110, fx);
+  double y0z1 = lerp(v001, v101, fx), y1z1 = lerp(v011, v111, fx);
+  double z0 = lerp(y0z0, y1z0, fy), z1 = lerp(y0z1, y1z1, fy);
+  /* d/dfx, d/dfy, d/dfz of the interpolant */
+  double dx = lerp(lerp(v100 - v000, v110 - v010, fy), lerp(v101 - v001, v111 - v011, fy), fz);
+  double dy = lerp(y1z0 - y0z0, y1z1 - y0z1, fz);
+  double dz = z1 - z0;
+  g[0] = dx / P->h; g[1] = dy / P->h; g[2] = dz / P->h;
+  return lerp(z0, z1, fz);
+}
+
+static void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* E and generalised gradient G[6 + nrot] = (F, tau, psi) at state q;
+ * scale[1 + 6 + nrot]: sum of absolute term values of E, then for each
+ * gradient component the sum of the absolute values of its contributions
+ * (the scale of its rounding error); inert[1 + nrot] = (I_R, I_b);
+ * *face = smallest cell-face distance of any in-grid atom. */
+static double energy_grad(const or_lig *L, const or_pocket *P, const or_clash *C, const or_state *q,
+                          double (*x)[3], double (*g)[3], double *a_abs, double *G, double *scale,
+                          double *inert, double *face) {
+  const int n = L->n, nr = L->nrot;
+  state_coords(L, q, x);
+  double e = 0.0, mag = 0.0, inv = 1.0 / (C->dc * C->dc);
+  *face = 1e30;
+  for (int i = 0; i < n; ++i) {
+    double fc;
+    double v = trilinear_grad(P, L->type[i], x[i], g[i], &fc);
+    if (fc < *face) *face = fc;
+    e += v;
+    mag += fabs(v);
+    a_abs[i] = fabs(g[i][0]) + fabs(g[i][1]) + fabs(g[i][2]);
+  }
+  double cl = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      if (L->topo[(size_t)i * n + j] < C->min_sep) continue;
+      double d[3] = {x[i][0] - x[j][0], x[i][1] - x[j][1], x[i][2] - x[j][2]};
+      double tt = 1.0 - (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * inv;
+      if (!(tt > 0.0)) continue;
+      cl += tt * tt;
+      double f = -4.0 * C->w * tt * inv;
+      for (int k = 0; k < 3; ++k) {
+        g[i][k] += f * d[k];
+        g[j][k] -= f * d[k];
+      }
+      double fa = fabs(f) * (fabs(d[0]) + fabs(d[1]) + fabs(d[2]));
+      a_abs[i] += fa;
+      a_abs[j] += fa;
+    }
+  e += C->w * cl;
+  scale[0] = mag + fabs(C->w) * cl;
+  for (int k = 0; k < 6 + nr; ++k) { G[k] = 0.0; scale[1 + k] = 0.0; }
+  inert[0] = 1.0;
+  for (int i = 0; i < n; ++i) {
+    double r[3] = {x[i][0] - q->t[0], x[i][1] - q->t[1], x[i][2] - q->t[2]}, c[3];
+    cross3(r, g[i], c);
+    double rl = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int k = 0; k < 3; ++k) {
+      G[k] += g[i][k];
+      G[3 + k] += c[k];
+      scale[1 + k] += a_abs[i];
+      scale[4 + k] += rl * a_abs[i];
+    }
+    inert[0] += r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  }
+  for (int b = 0; b < nr; ++b) {
+    int u = L->rot_u[b], v = L->rot_v[b];
+    double nb[3] = {x[v][0] - x[u][0], x[v][1] - x[u][1], x[v][2] - x[u][2]};
+    double len = sqrt(nb[0] * nb[0] + nb[1] * nb[1] + nb[2] * nb[2]);
+    for (int d = 0; d < 3; ++d) nb[d] /= len;
+    double psi = 0.0, sc = 0.0, in = 1.0;
+    for (int i = 0; i < n; ++i) {
+      if (!L->moved[b * n + i] || i == v) continue;
+      double r[3] = {x[i][0] - x[v][0], x[i][1] - x[v][1], x[i][2] - x[v][2]}, c[3];
+      cross3(r, g[i], c);
+      psi += nb[0] * c[0] + nb[1] * c[1] + nb[2] * c[2];
+      double rl = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      sc += rl * a_abs[i];
+      double ra = r[0] * nb[0] + r[1] * nb[1] + r[2] * nb[2];
+      in += rl * rl - ra * ra;
+    }
+    G[6 + b] = psi;
+    scale[7 + b] = sc;
+    inert[1 + b] = in;
+  }
+  return e;
+}
+
+/* Rotation matrix exp([w]x) (Rodrigues; identity for w = 0). */
+static void rot_exp(const double w[3], double M[9]) {
+  double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  if (th == 0.0) {
+    for (int k = 0; k < 9; ++k) M[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    return;
+  }
+  double n[3] = {w[0] / th, w[1] / th, w[2] / th}, c = cos(th), s = sin(th), o = 1.0 - c;
+  M[0] = c + o * n[0] * n[0];        M[1] = o * n[0] * n[1] - s * n[2]; M[2] = o * n[0] * n[2] + s * n[1];
+  M[3] = o * n[1] * n[0] + s * n[2]; M[4] = c + o * n[1] * n[1];        M[5] = o * n[1] * n[2] - s * n[0];
+  M[6] = o * n[2] * n[0] - s * n[1]; M[7] = o * n[2] * n[1] + s * n[0]; M[8] = c + o * n[2] * n[2];
+}
+
+/* Rows re-orthonormalised by Gram-Schmidt, r2 = r0 x r1. */
+static void gram_schmidt(double R[9]) {
+  double *r0 = R, *r1 = R + 3;
+  double l0 = sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+  for (int k = 0; k < 3; ++k) r0[k] /= l0;
+  double dp = r0[0] * r1[0] + r0[1] * r1[1] + r0[2] * r1[2];
+  for (int k = 0; k < 3; ++k) r1[k] -= dp * r0[k];
+  double l1 = sqrt(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+  for (int k = 0; k < 3; ++k) r1[k] /= l1;
+  cross3(r0, r1, R + 6);
+}
+
+static void trial_state(const or_lig *L, const or_state *q, const double *G, const double *inert,
+                        double eta, or_state *out) {
+  double w[3], M[9];
+  for (int k = 0; k < 3; ++k) {
+    out->t[k] = q->t[k] - eta * G[k] / L->n;
+    w[k] = -eta * G[3 + k] / inert[0];
+  }
+  rot_exp(w, M);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      out->R[3 * r + c] = M[3 * r] * q->R[c] + M[3 * r + 1] * q->R[3 + c] + M[3 * r + 2] * q->R[6 + c];
+  gram_schmidt(out->R);
+  for (int b = 0; b < L->nrot; ++b) out->phi[b] = q->phi[b] - eta * G[6 + b] / inert[1 + b];
+}
+
+static void state_in(const or_lig *L, const double *s, or_state *q) {
+  memcpy(q->R, s, 9 * sizeof(double));
+  memcpy(q->t, s + 9, 3 * sizeof(double));
+  for (int b = 0; b < L->nrot; ++b) q->phi[b] = s[12 + b];
+}
+
+static void state_out(const or_lig *L, const or_state *q, double *s) {
+  memcpy(s, q->R, 9 * sizeof(double));
+  memcpy(s + 9, q->t, 3 * sizeof(double));
+  for (int b = 0; b < L->nrot; ++b) s[12 + b] = q->phi[b];
+}
+
+/* E, generalised gradient and scales at n states.  states: [n][12 + nrot]
+ * (R row-major, t, phi); g_out [n][6 + nrot]; scale_out [n][7 + nrot];
+ * inert_out [n][1 + nrot]; face_out [n]. */
+OR_EXPORT int or_pose_grad(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                           int n_states, const double *states, double *e_out, double *g_out,
+                           double *scale_out, double *inert_out, double *face_out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_pocket P;
+  make_pocket(pi, sp->penalty, &P);
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+  const int nr = L.nrot;
+#pragma omp parallel
+  {
+    double (*x)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+    double (*g)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+    double *aa = (double *)malloc(sizeof(double) * (size_t)L.n);
+#pragma omp for schedule(dynamic, 4)
+    for (int p = 0; p < n_states; ++p) {
+      or_state q;
+      state_in(&L, states + (size_t)p * (12 + nr), &q);
+      e_out[p] = energy_grad(&L, &P, &C, &q, x, g, aa, g_out + (size_t)p * (6 + nr),
+                             scale_out + (size_t)p * (7 + nr), inert_out + (size_t)p * (1 + nr),
+                             face_out + p);
+    }
+    free(x); free(g); free(aa);
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* Descent from n states for `iters` iterations (see above).  follow
+ * (optional, [n]): bit it = the decision to take at iteration it instead of
+ * the oracle's own; a decision that differs from the oracle's own by more
+ * than a near-tie (|E(trial) - E| > tie_rel * max(scale, 1)) is counted in
+ * n_disagree[p].  Outputs: final states [n][12 + nrot], e_in/e_out [n],
+ * own_mask [n] (the oracle's own decisions along the path it took),
+ * n_disagree [n] (optional), scale_out [n] (sum of |terms| of the final E). */
+OR_EXPORT int or_refine(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                        int n_states, const double *states, int iters, double eta0,
+                        const uint32_t *follow, double tie_rel, double *states_out, double *e_in,
+                        double *e_out, uint32_t *own_mask, int *n_disagree, double *scale_out) {
+  if (iters < 0 || iters > 32) return -2;
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_pocket P;
+  make_pocket(pi, sp->penalty, &P);
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+  const int nr = L.nrot;
+#pragma omp parallel
+  {
+    double (*x)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+    double (*g)[3] = (double(*)[3])malloc(sizeof(double) * 3 * (size_t)L.n);
+    double *aa = (double *)malloc(sizeof(double) * (size_t)L.n);
+    double G[70], G2[70], sc[71], sc2[71], in[65], in2[65], face;
+#pragma omp for schedule(dynamic, 2)
+    for (int p = 0; p < n_states; ++p) {
+      or_state q, tq;
+      state_in(&L, states + (size_t)p * (12 + nr), &q);
+      double e = energy_grad(&L, &P, &C, &q, x, g, aa, G, sc, in, &face);
+      e_in[p] = e;
+      double eta = eta0;
+      uint32_t mask = 0;
+      int dis = 0;
+      for (int it = 0; it < iters; ++it) {
+        trial_state(&L, &q, G, in, eta, &tq);
+        double et = energy_grad(&L, &P, &C, &tq, x, g, aa, G2, sc2, in2, &face);
+        int own = et < e;
+        int take = follow ? (int)((follow[p] >> it) & 1u) : own;
+        if (take != own) {
+          double s = sc[0] > sc2[0] ? sc[0] : sc2[0];
+          if (fabs(et - e) > tie_rel * (s > 1.0 ? s : 1.0)) ++dis;
+        }
+        if (own) mask |= 1u << it;
+        if (take) {
+          q = tq; e = et;
+          memcpy(G, G2, sizeof(double) * (6 + nr));
+          memcpy(sc, sc2, sizeof(double) * (7 + nr));
+          memcpy(in, in2, sizeof(double) * (1 + nr));
+          eta *= 1.25;
+        } else {
+          eta *= 0.5;
+        }
+      }
+      state_out(&L, &q, states_out + (size_t)p * (12 + nr));
+      e_out[p] = e;
+      own_mask[p] = mask;
+      if (n_disagree) n_disagree[p] = dis;
+      if (scale_out) scale_out[p] = sc[0];
+    }
+    free(x); free(g); free(aa);
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Descriptor (256 entries, 233 used).                                       */
 OR_EXPORT int or_descriptor(const or_ligand_in *li, int n_types, double *out) {
   if (n_types != 8) return -1;
