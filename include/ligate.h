@@ -275,6 +275,63 @@ ligate_status ligate_score_poses(const ligate_pocket *pocket, const ligate_batch
                                  const uint8_t *tors, float *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Pose refinement by gradient descent (paper Sec. 2: the docking search is a
+ * gradient descent from multiple restarts; here the best poses of the
+ * greedy sweep are the restarts and a local descent refines each one).
+ *
+ * A pose state is (R, t, phi): atom i sits at x_i = R (y_i - c) + t, with y
+ * the input conformation after torsion angle phi_b (radians) is applied to
+ * each rotatable bond b in sweep order about its current axis u -> v, c the
+ * input centroid, R a rotation matrix (row-major) and t in Angstrom.  The
+ * docked pose (start s, steps k) is R = R_o, t = anchor a, phi_b =
+ * 2 pi k_b / S.  The energy is the docking score on the FP32 maps.  The
+ * generalised gradient is (F, tau, psi): F = sum_i g_i, tau = sum_i
+ * (x_i - t) x g_i and psi_b = n_b . sum_{i moved by b} (x_i - x_v) x g_i
+ * with g_i = dE/dx_i and n_b the unit axis of bond b (the derivatives of E
+ * along a translation, a rotation about t and a turn of bond b; the
+ * trilinear derivative is the one of the atom's cell, zero for atoms
+ * outside the maps).  Each descent iteration forms the trial
+ * t - eta F / N, GS(exp([-eta tau / I_R]x) R), phi - eta psi / I_b with
+ * I_R = 1 + sum_i |x_i - t|^2 and I_b = 1 + sum_{moved} |r_perp|^2 (A^2;
+ * GS = Gram-Schmidt on the rows) and accepts it when it lowers E (eta
+ * grows by 1.25) or rejects it (eta halves). */
+typedef struct {
+  float rot[9];                /* R, row-major */
+  float trans[3];              /* t (Angstrom) */
+  float tors[LIGATE_MAX_ROT];  /* phi_b (radians), bonds in sweep order; unused entries 0 */
+} ligate_pose_state;
+typedef struct {
+  ligate_pose_state state;     /* refined state */
+  float score_in;              /* energy at the starting state */
+  float score;                 /* energy at the refined state (<= score_in) */
+  uint32_t accepted;           /* bit i: the trial of iteration i was accepted */
+  int32_t ligand;              /* batch index of the ligand */
+} ligate_refined;
+#define LIGATE_REFINE_MAX_ITERS 32
+#define LIGATE_GRAD_DIM (6 + LIGATE_MAX_ROT) /* F (3), tau (3), psi (LIGATE_MAX_ROT) */
+
+/* Energy and generalised gradient of n explicit states: pose p is ligand
+ * lig_idx[p] of the batch in state states[p].  All arrays DEVICE memory;
+ * energy [n], grad [n][LIGATE_GRAD_DIM] (entries of missing bonds 0).  A
+ * ligand index outside the batch gives a NaN energy.  Synchronises stream. */
+ligate_status ligate_pose_gradient(const ligate_pocket *pocket, const ligate_batch *batch,
+                                   const ligate_sampling *sampling, int n, const int32_t *lig_idx,
+                                   const ligate_pose_state *states, float *energy, float *grad,
+                                   void *stream);
+/* Refine n explicit states (DEVICE arrays; out DEVICE [n]) for
+ * `iterations` (0..LIGATE_REFINE_MAX_ITERS) descent iterations with
+ * initial step eta0 > 0 (A^2 per score unit).  Synchronises stream. */
+ligate_status ligate_refine_states(const ligate_pocket *pocket, const ligate_batch *batch,
+                                   const ligate_sampling *sampling, int n, const int32_t *lig_idx,
+                                   const ligate_pose_state *init, int iterations, float eta0,
+                                   ligate_refined *out, void *stream);
+/* Refine every pose of the plan's last run (its ligate_pose[n_ligands]
+ * [top_k] device output) into DEVICE out[n_ligands][top_k], same order;
+ * empty slots are copied with accepted = 0.  Enqueues on stream. */
+ligate_status ligate_plan_refine(const ligate_plan *plan, int iterations, float eta0,
+                                 ligate_refined *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Autotuner (paper Sec. 3.3: per-size batch tuning).  Times candidate
  * shapes on a sample of the batch's ligands per size bucket and writes the
  * best to *best (and to the cache file named by LIGATE_TUNE_CACHE, when

@@ -567,6 +567,8 @@ struct ligate_plan {
   Item *items = nullptr;
   int *lig_items = nullptr, *lig_slot0 = nullptr, *counters = nullptr;
   PoseOut *partial = nullptr, *out = nullptr;
+  int32_t *row_lig = nullptr;  // [n_ligands] batch index of each output row
+  double origin[3] = {0, 0, 0}, h = 1.0;
   size_t counter_bytes = 0;
   unsigned long long *stats = nullptr;  // [3] executed-work counters of the last run
   cudaStream_t cap_stream = nullptr;
@@ -583,6 +585,7 @@ static void free_plan(ligate_plan *pl) {
   cudaFree(pl->rot); cudaFree(pl->anc); cudaFree(pl->quat);
   cudaFree(pl->items); cudaFree(pl->lig_items); cudaFree(pl->lig_slot0);
   cudaFree(pl->counters); cudaFree(pl->partial); cudaFree(pl->out); cudaFree(pl->stats);
+  cudaFree(pl->row_lig);
   delete pl;
 }
 
@@ -620,6 +623,18 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   ligate_plan *pl = new ligate_plan();
   pl->mode = mode;
   pl->n_ligands = sel ? n_sel : B->d.n_ligands;
+  for (int d = 0; d < 3; ++d) pl->origin[d] = P->d.origin[d];
+  pl->h = P->d.spacing;
+  {
+    std::vector<int32_t> rl(pl->n_ligands);
+    for (int r = 0; r < pl->n_ligands; ++r) rl[r] = sel ? sel[r] : r;
+    cudaError_t e0;
+    if (!rl.empty() && ((e0 = dmalloc(&pl->row_lig, rl.size())) != cudaSuccess ||
+                        (e0 = cudaMemcpy(pl->row_lig, rl.data(), 4 * rl.size(), cudaMemcpyHostToDevice)) != cudaSuccess)) {
+      free_plan(pl);
+      return cuda_fail(e0, "plan allocation");
+    }
+  }
   st = base_params(P, B, s, mode, pl->p, &pl->rot, &pl->anc, &pl->quat);
   if (st != LIGATE_OK) { free_plan(pl); return st; }
   DockParams &p = pl->p;
@@ -867,6 +882,80 @@ extern "C" ligate_status ligate_score_poses(const ligate_pocket *P, const ligate
   cudaFree(rot); cudaFree(anc); cudaFree(quat);
   if (st != LIGATE_OK) return st;
   if (e != cudaSuccess) return cuda_fail(e, "score_poses");
+  return LIGATE_OK;
+}
+
+// ===========================================================================
+// Pose refinement (refine.cu).
+static ligate_status refine_explicit(int mode, const ligate_pocket *P, const ligate_batch *B,
+                                     const ligate_sampling *s, int n, const int32_t *lig_idx,
+                                     const ligate_pose_state *states, int iters, float eta0,
+                                     ligate_refined *out, float *energy, float *grad, void *stream,
+                                     const char *what) {
+  int m = 0;
+  ligate_status st = check_sampling(P, B, s, &m);
+  if (st != LIGATE_OK) return st;
+  if (n < 0 || (n > 0 && (!lig_idx || !states || (mode == 0 ? (!energy || !grad) : !out)))) {
+    set_error("%s: bad arrays", what);
+    return LIGATE_ERR_INVALID;
+  }
+  if (mode == 1 && (iters < 0 || iters > LIGATE_REFINE_MAX_ITERS || !(eta0 > 0.f) || !std::isfinite(eta0))) {
+    set_error("%s: iterations must be 0..%d and eta0 finite and > 0", what, LIGATE_REFINE_MAX_ITERS);
+    return LIGATE_ERR_INVALID;
+  }
+  if (n == 0) return LIGATE_OK;
+  DockParams p;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  st = base_params(P, B, s, m, p, &rot, &anc, &quat);
+  cudaError_t e = cudaSuccess;
+  if (st == LIGATE_OK && refine_smem_bytes(p.nmax) * 4 > 227 * 1024) {
+    set_error("%s: ligands too large for the refinement kernel's shared memory", what);
+    st = LIGATE_ERR_UNSUPPORTED;
+  }
+  if (st == LIGATE_OK) {
+    e = launch_refine(mode, p, P->d.origin, P->d.spacing, n, lig_idx, states, nullptr, nullptr, iters,
+                      eta0, out, energy, grad, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  cudaFree(rot); cudaFree(anc); cudaFree(quat);
+  if (st != LIGATE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_pose_gradient(const ligate_pocket *P, const ligate_batch *B,
+                                              const ligate_sampling *s, int n, const int32_t *lig_idx,
+                                              const ligate_pose_state *states, float *energy, float *grad,
+                                              void *stream) {
+  return refine_explicit(0, P, B, s, n, lig_idx, states, 0, 1.f, nullptr, energy, grad, stream,
+                         "pose_gradient");
+}
+
+extern "C" ligate_status ligate_refine_states(const ligate_pocket *P, const ligate_batch *B,
+                                              const ligate_sampling *s, int n, const int32_t *lig_idx,
+                                              const ligate_pose_state *init, int iterations, float eta0,
+                                              ligate_refined *out, void *stream) {
+  return refine_explicit(1, P, B, s, n, lig_idx, init, iterations, eta0, out, nullptr, nullptr, stream,
+                         "refine_states");
+}
+
+extern "C" ligate_status ligate_plan_refine(const ligate_plan *pl, int iterations, float eta0,
+                                            ligate_refined *out, void *stream) {
+  if (!pl || !out) { set_error("plan_refine: NULL argument"); return LIGATE_ERR_INVALID; }
+  if (iterations < 0 || iterations > LIGATE_REFINE_MAX_ITERS || !(eta0 > 0.f) || !std::isfinite(eta0)) {
+    set_error("plan_refine: iterations must be 0..%d and eta0 finite and > 0", LIGATE_REFINE_MAX_ITERS);
+    return LIGATE_ERR_INVALID;
+  }
+  const int n = pl->n_ligands * pl->p.K;
+  if (n == 0) return LIGATE_OK;
+  if (refine_smem_bytes(pl->p.nmax) * 4 > 227 * 1024) {
+    set_error("plan_refine: ligands too large for the refinement kernel's shared memory");
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  cudaError_t e = launch_refine(2, pl->p, pl->origin, pl->h, n, nullptr, nullptr,
+                                reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, iterations,
+                                eta0, out, nullptr, nullptr, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plan_refine");
   return LIGATE_OK;
 }
 

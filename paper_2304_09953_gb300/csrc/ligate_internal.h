@@ -153,6 +153,14 @@ inline void fill_step_table(int S, float *tab) {
   }
 }
 
+// Pose refinement (refine.cu): mode 0 energy + gradient of explicit
+// states, 1 refine explicit states, 2 refine a plan's poses.
+size_t refine_smem_bytes(int nmax);
+cudaError_t launch_refine(int mode, const DockParams &p, const double origin[3], double h, int n,
+                          const int32_t *lig_idx, const ligate_pose_state *init, const ligate_pose *poses,
+                          const int32_t *row_lig, int iters, float eta0, ligate_refined *out,
+                          float *energy, float *grad, cudaStream_t s);
+
 // Host launch wrappers (dock.cu).
 size_t dock_smem_per_warp(int nmax, int S, int G);
 cudaError_t launch_dock(int mode, int reg_cap, const DockParams &p, int grid, int block, size_t smem,

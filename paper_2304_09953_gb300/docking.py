@@ -13,7 +13,7 @@ class PocketHandle:
         self.h = N.ligate_pocket_create(pocket.maps, pocket.origin, pocket.spacing, pocket.anchors, mask)
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             N.ligate_pocket_destroy(self.h)
             self.h = None
 
@@ -26,7 +26,7 @@ class BatchHandle:
         self.h = N.ligate_batch_create(ligands)
 
     def close(self):
-        if self.h:
+        if getattr(self, "h", None):
             N.ligate_batch_destroy(self.h)
             self.h = None
 
@@ -64,6 +64,15 @@ class Plan:
         out = np.zeros((self.n, self.k), N.POSE_DTYPE)
         N.ligate_plan_run(self.h, out, stream)
         return out
+
+    def refine(self, iterations=32, eta0=0.1, stream=None) -> np.ndarray:
+        """Gradient-descent refinement of every pose of the last run
+        (ligate_plan_refine); returns REFINED_DTYPE [n, K] on the host."""
+        import torch
+        buf = torch.empty(self.n * self.k * N.REFINED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        N.ligate_plan_refine(self.h, iterations, eta0, buf, stream)
+        torch.cuda.synchronize()
+        return buf.cpu().numpy().view(N.REFINED_DTYPE).reshape(self.n, self.k)
 
     def device_output(self) -> int:
         """Device address of the last run's ligate_pose[n][K] result."""

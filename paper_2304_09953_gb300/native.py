@@ -56,6 +56,13 @@ class ligate_pose(ctypes.Structure):
 
 POSE_DTYPE = np.dtype([("score", np.float32), ("start_id", np.int32), ("tors", np.uint8, (16,))])
 assert POSE_DTYPE.itemsize == ctypes.sizeof(ligate_pose) == 24
+LIGATE_REFINE_MAX_ITERS = 32
+LIGATE_GRAD_DIM = 6 + 16
+# ligate_pose_state and ligate_refined (include/ligate.h)
+STATE_DTYPE = np.dtype([("rot", np.float32, (9,)), ("trans", np.float32, (3,)), ("tors", np.float32, (16,))])
+REFINED_DTYPE = np.dtype([("state", STATE_DTYPE), ("score_in", np.float32), ("score", np.float32),
+                          ("accepted", np.uint32), ("ligand", np.int32)])
+assert STATE_DTYPE.itemsize == 112 and REFINED_DTYPE.itemsize == 128
 
 
 class ligate_tile(ctypes.Structure):
@@ -102,6 +109,9 @@ _SIGS = {
     "ligate_surrogate_grad": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P]),
     "ligate_surrogate_get_weights": (ctypes.c_int, [P, P]),
     "ligate_surrogate_engine": (ctypes.c_int, [P]),
+    "ligate_pose_gradient": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
+    "ligate_refine_states": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_float, P, P]),
+    "ligate_plan_refine": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_float, P, P]),
 }
 
 _lib = None
@@ -280,6 +290,24 @@ def ligate_dock_noalloc(pocket, batch, sampling_struct, out, stream=None):
 def ligate_score_poses(pocket, batch, sampling_struct, n, lig_idx, start_id, tors, out, stream=None):
     check(load().ligate_score_poses(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
                                     _ptr(start_id), _ptr(tors), _ptr(out), stream), "ligate_score_poses")
+
+
+def ligate_pose_gradient(pocket, batch, sampling_struct, n, lig_idx, states, energy, grad, stream=None):
+    """states: DEVICE ligate_pose_state[n] (e.g. a uint8 tensor of n * 112 bytes)."""
+    check(load().ligate_pose_gradient(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
+                                      _ptr(states), _ptr(energy), _ptr(grad), stream), "ligate_pose_gradient")
+
+
+def ligate_refine_states(pocket, batch, sampling_struct, n, lig_idx, init, iterations, eta0, out,
+                         stream=None):
+    check(load().ligate_refine_states(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
+                                      _ptr(init), int(iterations), float(eta0), _ptr(out), stream),
+          "ligate_refine_states")
+
+
+def ligate_plan_refine(plan, iterations, eta0, out, stream=None):
+    check(load().ligate_plan_refine(plan, int(iterations), float(eta0), _ptr(out), stream),
+          "ligate_plan_refine")
 
 
 def ligate_autotune(pocket, batch, sampling_struct, budget_ms=20000.0):
