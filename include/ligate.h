@@ -182,7 +182,9 @@ typedef struct {
   int warps_per_cta;   /* 1..4 */
   int ctas_per_sm;
   int starts_per_item[LIGATE_N_BUCKETS];
-  int reg_cap;         /* 0: at most 102 registers per thread (5 CTAs of 128 per SM); 1: at most 85 (6 CTAs) */
+  int reg_cap;         /* registers per thread: 1: at most 85 (6 CTAs of 128 threads per SM), 2: at most
+                          102 (5 CTAs), 3: at most 128 (4 CTAs), 0: default (128 for the plain FP32
+                          layout, 102 for the corner layouts) */
 } ligate_tile;
 
 /* ------------------------------------------------------------------------

@@ -645,7 +645,7 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   default_tile(p, pl->n_ligands, sms, &pl->tile);
   ligate_tile &t = pl->tile;
   t.warps_per_cta = std::max(1, std::min(4, t.warps_per_cta));
-  t.reg_cap = t.reg_cap ? 1 : 0;
+  if (t.reg_cap < 0 || t.reg_cap > 3) t.reg_cap = 0;
   for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
     t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
   {  // keep the partial top-K lists (items x K poses) within 1 GiB: larger chunks for large batches
@@ -1133,22 +1133,29 @@ extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_ba
   memset(&cur, 0, sizeof(cur));
   const int G = 32 / pow2ceil(s->torsion_steps);
   if (sample.empty()) {
-    cur.warps_per_cta = 8;
+    cur.warps_per_cta = 4;
     for (int b = 0; b < LIGATE_N_BUCKETS; ++b) cur.starts_per_item[b] = std::max(G, 512 / G * G);
     *best = cur;
     return LIGATE_OK;
   }
+  // 1) CTA shape and register cap on up to 2048 ligands spread over the
+  //    batch (long enough a run for the steady state the full run sees),
+  //    with a mid chunk
+  std::vector<int> shape_sample;
+  {
+    const int n = B->d.n_ligands, m = std::min(n, 2048);
+    for (int j = 0; j < m; ++j) shape_sample.push_back((int)((long long)j * n / m));
+  }
   ligate_batch *SB = nullptr;
-  if ((st = sub_batch(B, sample, &SB)) != LIGATE_OK) return st;
-  // 1) CTA shape on the whole sample with a mid chunk
+  if ((st = sub_batch(B, shape_sample, &SB)) != LIGATE_OK) return st;
   const int mid = std::max(G, 512 / G * G);
   double best_ms = -1;
   ligate_tile best_t = cur;
-  for (int shape = 0; shape < 4; ++shape) {
+  for (int shape = 0; shape < 6; ++shape) {  // 2 or 4 warps x register caps 85 / 102 / 128
     ligate_tile t;
     memset(&t, 0, sizeof(t));
     t.warps_per_cta = (shape & 1) ? 4 : 2;
-    t.reg_cap = shape >> 1;
+    t.reg_cap = 1 + (shape >> 1);
     for (int b = 0; b < LIGATE_N_BUCKETS; ++b) t.starts_per_item[b] = mid;
     const double ms = time_tile(P, SB, s, t, 3);
     if (ms > 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; best_t = t; }

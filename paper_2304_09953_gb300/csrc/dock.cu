@@ -464,8 +464,9 @@ __device__ void build_memo(const DockParams &p, const WarpSmem &w, float4 *pose,
 }
 
 // ---------------------------------------------------------------------------
-// CTAs of at most 128 threads; MINB of them must fit on one SM: 5 caps the
-// registers at 102 (20 resident warps), 6 at 85 (24 warps, a few spills).
+// CTAs of at most 128 threads; MINB of them must fit on one SM: 4 caps the
+// registers at 128 (16 resident warps), 5 at 102 (20 warps), 6 at 85 (24
+// warps, a few spills).
 // Latency of the map gathers is covered by resident warps, so occupancy
 // matters more than per-thread registers here.
 template <int MODE, int MINB>
@@ -745,15 +746,25 @@ __global__ void start_frames_kernel(const float4 *__restrict__ quat, int n_orien
 }
 
 // ---------------------------------------------------------------------------
+// Kernel instance of a mode and register cap: reg_cap 1 = at most 85
+// registers (6 CTAs of 128 threads per SM), 2 = at most 102 (5 CTAs), 3 = at
+// most 128 (4 CTAs), 0 = the mode's default: 128 for the plain FP32 layout
+// (eight scalar gathers per interpolation want registers for loads in
+// flight), 102 for the corner layouts (one vector gather; occupancy wins).
 static const void *dock_fn(int mode, int reg_cap) {
-  switch (mode * 2 + (reg_cap ? 1 : 0)) {
-    case 0: return (const void *)dock_kernel<MODE_F32_PLAIN, 5>;
-    case 1: return (const void *)dock_kernel<MODE_F32_PLAIN, 6>;
-    case 2: return (const void *)dock_kernel<MODE_F32_CORNER, 5>;
-    case 3: return (const void *)dock_kernel<MODE_F32_CORNER, 6>;
-    case 4: return (const void *)dock_kernel<MODE_BF16_CORNER, 5>;
-    case 5: return (const void *)dock_kernel<MODE_BF16_CORNER, 6>;
-    case 6: return (const void *)dock_kernel<MODE_F16_CORNER, 5>;
+  const int minb = reg_cap == 1 ? 6 : reg_cap == 2 ? 5 : reg_cap == 3 ? 4 : (mode == MODE_F32_PLAIN ? 4 : 5);
+  switch (mode * 3 + (minb - 4)) {
+    case 0: return (const void *)dock_kernel<MODE_F32_PLAIN, 4>;
+    case 1: return (const void *)dock_kernel<MODE_F32_PLAIN, 5>;
+    case 2: return (const void *)dock_kernel<MODE_F32_PLAIN, 6>;
+    case 3: return (const void *)dock_kernel<MODE_F32_CORNER, 4>;
+    case 4: return (const void *)dock_kernel<MODE_F32_CORNER, 5>;
+    case 5: return (const void *)dock_kernel<MODE_F32_CORNER, 6>;
+    case 6: return (const void *)dock_kernel<MODE_BF16_CORNER, 4>;
+    case 7: return (const void *)dock_kernel<MODE_BF16_CORNER, 5>;
+    case 8: return (const void *)dock_kernel<MODE_BF16_CORNER, 6>;
+    case 9: return (const void *)dock_kernel<MODE_F16_CORNER, 4>;
+    case 10: return (const void *)dock_kernel<MODE_F16_CORNER, 5>;
     default: return (const void *)dock_kernel<MODE_F16_CORNER, 6>;
   }
 }
