@@ -49,6 +49,12 @@ class _Samp(ctypes.Structure):
                 ("clash_min_sep", ctypes.c_int), ("penalty", ctypes.c_double)]
 
 
+class _Rec(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("xyz", ctypes.c_void_p), ("type", ctypes.c_void_p),
+                ("n_types", ctypes.c_int), ("radius", ctypes.c_void_p), ("eps", ctypes.c_void_p),
+                ("cutoff", ctypes.c_double), ("cap", ctypes.c_double), ("rmin", ctypes.c_double)]
+
+
 class _Pock(ctypes.Structure):
     _fields_ = [("maps", ctypes.c_void_p), ("n_types", ctypes.c_int), ("nx", ctypes.c_int),
                 ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("origin", ctypes.c_double * 3),
@@ -75,6 +81,7 @@ def _load():
         lib.or_descriptor.argtypes = [P, I, P]
         lib.or_pose_grad.argtypes = [P, P, P, I, P, P, P, P, P, P]
         lib.or_refine.argtypes = [P, P, P, I, P, I, D, P, D, P, P, P, P, P, P]
+        lib.or_rescore_coords.argtypes = [P, P, P, P, I, P, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -344,4 +351,32 @@ def refine(lig, pocket, sampling, states, iters, eta0, follow=None, tie_rel=1e-4
         raise ValueError("bad refinement arguments")
     return {"states": out, "e_in": e_in, "e_out": e_out, "own_mask": mask, "n_disagree": dis,
             "scale": scale}
+
+
+# ---------------------------------------------------------------------------
+# Exact rescoring and pose filter (see the rescoring section of ligate_oracle.c).
+
+def rescore_coords(lig, pocket, sampling, receptor, coords):
+    """receptor: dict(xyz [m,3] float32, type [m], radius [T], eps [T],
+    cutoff, cap, rmin).  coords [n_poses, n_atoms, 3].  Returns dict(e_inter,
+    e_clash, n_outside, n_capped, scale)."""
+    lib = _load()
+    k = _Keep()
+    L = _lig(k, *lig)
+    P = _pock(k, pocket)
+    S = _samp(k, sampling, pocket.anchors)
+    rx = _c(receptor["xyz"], np.float32)
+    rt = _c(receptor["type"], np.int32)
+    rr = _c(receptor["radius"], np.float64)
+    re = _c(receptor["eps"], np.float64)
+    R = _Rec(len(rx), k.ptr(rx), k.ptr(rt), len(rr), k.ptr(rr), k.ptr(re), float(receptor["cutoff"]),
+             float(receptor["cap"]), float(receptor["rmin"]))
+    x = _c(coords, np.float64)
+    n = x.shape[0]
+    ei, ec, sc = np.zeros(n), np.zeros(n), np.zeros(n)
+    no, nc = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    if lib.or_rescore_coords(_ref(L), _ref(P), _ref(S), _ref(R), n, x.ctypes.data, ei.ctypes.data,
+                             ec.ctypes.data, no.ctypes.data, nc.ctypes.data, sc.ctypes.data):
+        raise ValueError("ligand bonds do not form a tree")
+    return {"e_inter": ei, "e_clash": ec, "n_outside": no, "n_capped": nc, "scale": sc}
 

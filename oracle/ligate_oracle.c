@@ -821,6 +821,92 @@ OR_EXPORT int or_refine(const or_ligand_in *li, const or_pocket_in *pi, const or
 }
 
 /* ------------------------------------------------------------------------ */
+/* Exact rescoring and pose filter (paper Sec. 2: a more accurate scoring of */
+/* the generated poses, then a filter).  Readings:                           */
+/*   e_inter : sum over ligand atoms i of min(cap, sum_j eps_ij [(r0/r)^12   */
+/*       - 2 (r0/r)^6]) over receptor atoms j within `cutoff` of x_i, r      */
+/*       clamped below at rmin, r0 = r_t + r_tau, eps_ij = sqrt(eps_t eps_tau)*/
+/*       -- the function the grid maps tabulate, evaluated at the atom       */
+/*       itself instead of interpolated, everywhere (no box penalty).        */
+/*   e_clash : the docking score's intramolecular clash term.                */
+/*   filter  : a pose passes when no atom lies outside the map box           */
+/*       ([0, n-1] in grid units on every axis) and no atom's receptor sum   */
+/*       reaches the cap.                                                    */
+typedef struct {
+  int n;
+  const float *xyz;     /* [n][3] */
+  const int *type;      /* [n] */
+  int n_types;
+  const double *radius; /* [n_types] */
+  const double *eps;    /* [n_types] */
+  double cutoff, cap, rmin;
+} or_receptor_in;
+
+/* For n_poses coordinate sets [n_poses][n][3]: e_inter, e_clash, n_outside,
+ * n_capped and scale (sum of absolute values of the per-atom and clash terms,
+ * each per-atom term itself counted by the sum of its pair magnitudes when
+ * it is not capped). */
+OR_EXPORT int or_rescore_coords(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                                const or_receptor_in *rc, int n_poses, const double *coords,
+                                double *e_inter, double *e_clash, int *n_out, int *n_capped,
+                                double *scale) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+  const int n = L.n;
+  const int dims[3] = {pi->nx, pi->ny, pi->nz};
+  const double c2 = rc->cutoff * rc->cutoff;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int p = 0; p < n_poses; ++p) {
+    const double (*x)[3] = (const double(*)[3])(coords + (size_t)p * n * 3);
+    double ei = 0.0, mag = 0.0;
+    int nout = 0, ncap = 0;
+    for (int i = 0; i < n; ++i) {
+      int outside = 0;
+      for (int d = 0; d < 3; ++d) {
+        double u = (x[i][d] - pi->origin[d]) / pi->h;
+        if (!(u >= 0.0 && u <= (double)(dims[d] - 1))) outside = 1;
+      }
+      nout += outside;
+      const int t = L.type[i];
+      double acc = 0.0, am = 0.0;
+      for (int j = 0; j < rc->n; ++j) {
+        double dx = (double)rc->xyz[3 * j] - x[i][0], dy = (double)rc->xyz[3 * j + 1] - x[i][1],
+               dz = (double)rc->xyz[3 * j + 2] - x[i][2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 > c2) continue;
+        double r = sqrt(d2);
+        if (r < rc->rmin) r = rc->rmin;
+        int tau = rc->type[j];
+        double q = (rc->radius[t] + rc->radius[tau]) / r;
+        double q2 = q * q, q6 = q2 * q2 * q2;
+        double v = sqrt(rc->eps[t] * rc->eps[tau]) * (q6 * q6 - 2.0 * q6);
+        acc += v;
+        am += fabs(v);
+      }
+      if (acc >= rc->cap) { acc = rc->cap; am = rc->cap; ++ncap; }
+      ei += acc;
+      mag += am;
+    }
+    double cl = 0.0, inv = 1.0 / (C.dc * C.dc);
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        if (L.topo[(size_t)i * n + j] < C.min_sep) continue;
+        double dx = x[i][0] - x[j][0], dy = x[i][1] - x[j][1], dz = x[i][2] - x[j][2];
+        double t = 1.0 - (dx * dx + dy * dy + dz * dz) * inv;
+        if (t > 0.0) cl += t * t;
+      }
+    e_inter[p] = ei;
+    e_clash[p] = C.w * cl;
+    n_out[p] = nout;
+    n_capped[p] = ncap;
+    if (scale) scale[p] = mag + fabs(C.w) * cl;
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Descriptor (256 entries, 233 used).                                       */
 OR_EXPORT int or_descriptor(const or_ligand_in *li, int n_types, double *out) {
   if (n_types != 8) return -1;

@@ -113,6 +113,22 @@ class Pocket:
     anchors: np.ndarray   # float32 [n_anchors, 3]
     receptor_xyz: Optional[np.ndarray] = None
     receptor_type: Optional[np.ndarray] = None
+    # parameters the maps were computed with (per-type LJ radius and depth,
+    # cutoff, cap, radius floor)
+    type_radius: Optional[np.ndarray] = None
+    type_eps: Optional[np.ndarray] = None
+    cutoff: float = 8.0
+    cap: float = 10.0
+    rmin: float = 0.5
+
+    def receptor(self) -> dict:
+        """Receptor atoms (FP32 coordinates) and the parameters of the maps'
+        potential, as the rescoring stage takes them."""
+        return {"xyz": np.ascontiguousarray(self.receptor_xyz, np.float32),
+                "type": np.ascontiguousarray(self.receptor_type, np.int32),
+                "radius": np.asarray(self.type_radius, np.float64),
+                "eps": np.asarray(self.type_eps, np.float64),
+                "cutoff": self.cutoff, "cap": self.cap, "rmin": self.rmin}
 
     @property
     def n_types(self) -> int:
@@ -211,7 +227,7 @@ def make_pocket(seed: int, n_types: int, n: int, spacing: float, n_receptor: int
         raise MemoryError("grid map generation failed")
     anchors = np.zeros((n_anchors, 3), np.float32)
     lib.lw_anchors(seed, n_anchors, _p(center), 0.2 * L, _p(anchors))
-    return Pocket(maps, origin, float(spacing), anchors, rxyz, rtyp)
+    return Pocket(maps, origin, float(spacing), anchors, rxyz, rtyp, radius, eps, cutoff, cap, rmin)
 
 
 def type_params(seed: int, n_types: int):
