@@ -334,6 +334,46 @@ ligate_status ligate_plan_refine(const ligate_plan *plan, int iterations, float 
                                  ligate_refined *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Exact rescoring and pose filter (paper Sec. 2: a more accurate scoring
+ * of the generated poses, then a filter keeps the plausible ones).
+ *
+ * The receptor term of a pose is sum_i min(cap, sum_j eps_ij ((r0/r)^12 -
+ * 2 (r0/r)^6)) over the receptor atoms j within `cutoff` of ligand atom i,
+ * r floored at rmin, r0 = radius[t_i] + radius[t_j], eps_ij =
+ * sqrt(eps[t_i] eps[t_j]): the pair potential the grid maps tabulate,
+ * evaluated at the atom instead of interpolated, everywhere (no box
+ * penalty).  The clash term is the docking score's.  A pose passes the
+ * filter when no atom lies outside the map box and no atom's receptor sum
+ * reaches the cap.
+ *
+ * Attach the receptor to a pocket (HOST arrays, copied): xyz [n][3] A,
+ * type [n] in [0, n_types), radius/eps [n_types] (A, well depth); cutoff,
+ * cap, rmin > 0.  Replaces a previous receptor.  n_types must cover every
+ * ligand atom type of the batches rescored. */
+ligate_status ligate_pocket_set_receptor(ligate_pocket *pocket, const float *xyz, const int32_t *type,
+                                         int n_atoms, const float *radius, const float *eps,
+                                         int n_types, float cutoff, float cap, float rmin);
+typedef struct {
+  float energy;       /* e_inter + e_clash; +inf for an empty slot */
+  float e_inter;      /* exact receptor term */
+  float e_clash;      /* clash term (weight included) */
+  int32_t n_outside;  /* ligand atoms outside the map box (-1: empty slot) */
+  int32_t n_capped;   /* ligand atoms whose receptor sum reached the cap */
+  int32_t pass;       /* 1: n_outside == 0 and n_capped == 0 */
+} ligate_rescored;
+/* Explicit poses (DEVICE lig_idx, start_id, tors[n][LIGATE_MAX_ROT]; out
+ * DEVICE [n]).  Errors: INVALID without a receptor or with ligand types
+ * beyond it; UNSUPPORTED when the receptor (16 B per atom) does not fit in
+ * shared memory (about 12,000 atoms).  Synchronises stream. */
+ligate_status ligate_rescore_poses(const ligate_pocket *pocket, const ligate_batch *batch,
+                                   const ligate_sampling *sampling, int n, const int32_t *lig_idx,
+                                   const int32_t *start_id, const uint8_t *tors, ligate_rescored *out,
+                                   void *stream);
+/* Every pose of the plan's last run into DEVICE out[n_ligands][top_k]
+ * (same order).  Enqueues on stream. */
+ligate_status ligate_plan_rescore(const ligate_plan *plan, ligate_rescored *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Autotuner (paper Sec. 3.3: per-size batch tuning).  Times candidate
  * shapes on a sample of the batch's ligands per size bucket and writes the
  * best to *best (and to the cache file named by LIGATE_TUNE_CACHE, when

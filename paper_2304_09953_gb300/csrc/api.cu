@@ -146,7 +146,67 @@ extern "C" void ligate_pocket_destroy(ligate_pocket *p) {
   cudaFree(p->d.map_bf16c);
   cudaFree(p->d.map_f16c);
   cudaFree(p->d.anchors);
+  cudaFree(p->d.rec);
+  cudaFree(p->d.rec_pair);
   delete p;
+}
+
+extern "C" ligate_status ligate_pocket_set_receptor(ligate_pocket *P, const float *xyz, const int32_t *type,
+                                                    int n, const float *radius, const float *eps,
+                                                    int n_types, float cutoff, float cap, float rmin) {
+  if (!P || n < 0 || (n > 0 && (!xyz || !type)) || n_types < 1 || n_types > 64 || !radius || !eps) {
+    set_error("pocket_set_receptor: bad arguments");
+    return LIGATE_ERR_INVALID;
+  }
+  if (!(cutoff > 0.f) || !std::isfinite(cutoff) || !std::isfinite(cap) || !(rmin > 0.f) || !std::isfinite(rmin)) {
+    set_error("pocket_set_receptor: cutoff and rmin must be finite and > 0, cap finite");
+    return LIGATE_ERR_INVALID;
+  }
+  for (int t = 0; t < n_types; ++t)
+    if (!(radius[t] > 0.f) || !std::isfinite(radius[t]) || !(eps[t] >= 0.f) || !std::isfinite(eps[t])) {
+      set_error("pocket_set_receptor: bad radius or eps of type %d", t);
+      return LIGATE_ERR_INVALID;
+    }
+  const double h = P->d.spacing;
+  std::vector<float4> rec((size_t)n);
+  for (int j = 0; j < n; ++j) {
+    if (type[j] < 0 || type[j] >= n_types || !std::isfinite(xyz[3 * j]) || !std::isfinite(xyz[3 * j + 1]) ||
+        !std::isfinite(xyz[3 * j + 2])) {
+      set_error("pocket_set_receptor: bad atom %d", j);
+      return LIGATE_ERR_INVALID;
+    }
+    float tb;
+    memcpy(&tb, &type[j], 4);  // type index as the int bits of .w
+    rec[j] = make_float4((float)(((double)xyz[3 * j] - P->d.origin[0]) / h),
+                         (float)(((double)xyz[3 * j + 1] - P->d.origin[1]) / h),
+                         (float)(((double)xyz[3 * j + 2] - P->d.origin[2]) / h), tb);
+  }
+  std::vector<float2> pair((size_t)n_types * n_types);
+  for (int t = 0; t < n_types; ++t)
+    for (int u = 0; u < n_types; ++u) {
+      const double r0 = ((double)radius[t] + (double)radius[u]) / h;
+      pair[(size_t)t * n_types + u] = make_float2((float)(r0 * r0), (float)std::sqrt((double)eps[t] * eps[u]));
+    }
+  cudaFree(P->d.rec);
+  cudaFree(P->d.rec_pair);
+  P->d.rec = nullptr;
+  P->d.rec_pair = nullptr;
+  P->d.n_rec = 0;
+  cudaError_t e;
+  if ((n && ((e = dmalloc(&P->d.rec, (size_t)n)) != cudaSuccess ||
+             (e = cudaMemcpy(P->d.rec, rec.data(), 16 * (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess)) ||
+      (e = dmalloc(&P->d.rec_pair, pair.size())) != cudaSuccess ||
+      (e = cudaMemcpy(P->d.rec_pair, pair.data(), 8 * pair.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(P->d.rec); cudaFree(P->d.rec_pair);
+    P->d.rec = nullptr; P->d.rec_pair = nullptr;
+    return cuda_fail(e, "pocket_set_receptor");
+  }
+  P->d.n_rec = n;
+  P->d.rec_types = n_types;
+  P->d.rec_cut2 = (float)((double)cutoff * cutoff / (h * h));
+  P->d.rec_cap = cap;
+  P->d.rec_rmin2 = (float)((double)rmin * rmin / (h * h));
+  return LIGATE_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -568,6 +628,8 @@ struct ligate_plan {
   int *lig_items = nullptr, *lig_slot0 = nullptr, *counters = nullptr;
   PoseOut *partial = nullptr, *out = nullptr;
   int32_t *row_lig = nullptr;  // [n_ligands] batch index of each output row
+  const ligate_pocket *pocket = nullptr;
+  const ligate_batch *batch = nullptr;
   double origin[3] = {0, 0, 0}, h = 1.0;
   size_t counter_bytes = 0;
   unsigned long long *stats = nullptr;  // [3] executed-work counters of the last run
@@ -625,6 +687,8 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   pl->n_ligands = sel ? n_sel : B->d.n_ligands;
   for (int d = 0; d < 3; ++d) pl->origin[d] = P->d.origin[d];
   pl->h = P->d.spacing;
+  pl->pocket = P;
+  pl->batch = B;
   {
     std::vector<int32_t> rl(pl->n_ligands);
     for (int r = 0; r < pl->n_ligands; ++r) rl[r] = sel ? sel[r] : r;
@@ -956,6 +1020,69 @@ extern "C" ligate_status ligate_plan_refine(const ligate_plan *pl, int iteration
                                 reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, iterations,
                                 eta0, out, nullptr, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "plan_refine");
+  return LIGATE_OK;
+}
+
+// ===========================================================================
+// Exact rescoring (dock.cu).
+static ligate_status rec_params(const ligate_pocket *P, const ligate_batch *B, RecParams &r, const char *what) {
+  if (!P->d.rec_pair) { set_error("%s: the pocket has no receptor (ligate_pocket_set_receptor)", what); return LIGATE_ERR_INVALID; }
+  if (B->max_type >= P->d.rec_types) {
+    set_error("%s: ligand atom type %d beyond the receptor's %d types", what, B->max_type, P->d.rec_types);
+    return LIGATE_ERR_INVALID;
+  }
+  r.rec = P->d.rec; r.pair = P->d.rec_pair; r.n_rec = P->d.n_rec; r.n_types = P->d.rec_types;
+  r.cut2 = P->d.rec_cut2; r.cap = P->d.rec_cap; r.rmin2 = P->d.rec_rmin2;
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_rescore_poses(const ligate_pocket *P, const ligate_batch *B,
+                                              const ligate_sampling *s, int n, const int32_t *lig_idx,
+                                              const int32_t *start_id, const uint8_t *tors,
+                                              ligate_rescored *out, void *stream) {
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  if (n < 0 || (n > 0 && (!lig_idx || !start_id || !tors || !out))) {
+    set_error("rescore_poses: bad pose arrays");
+    return LIGATE_ERR_INVALID;
+  }
+  RecParams r;
+  if ((st = rec_params(P, B, r, "rescore_poses")) != LIGATE_OK) return st;
+  if (n == 0) return LIGATE_OK;
+  DockParams p;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  st = base_params(P, B, s, mode, p, &rot, &anc, &quat);
+  cudaError_t e = cudaSuccess;
+  if (st == LIGATE_OK && rescore_smem_bytes(p, r, 1) > 227 * 1024) {
+    set_error("rescore_poses: %d receptor atoms do not fit in shared memory", r.n_rec);
+    st = LIGATE_ERR_UNSUPPORTED;
+  }
+  if (st == LIGATE_OK) {
+    e = launch_rescore(p, r, n, lig_idx, start_id, tors, nullptr, nullptr, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  cudaFree(rot); cudaFree(anc); cudaFree(quat);
+  if (st != LIGATE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "rescore_poses");
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_rescore(const ligate_plan *pl, ligate_rescored *out, void *stream) {
+  if (!pl || !out) { set_error("plan_rescore: NULL argument"); return LIGATE_ERR_INVALID; }
+  RecParams r;
+  ligate_status st = rec_params(pl->pocket, pl->batch, r, "plan_rescore");
+  if (st != LIGATE_OK) return st;
+  const int n = pl->n_ligands * pl->p.K;
+  if (n == 0) return LIGATE_OK;
+  if (rescore_smem_bytes(pl->p, r, 1) > 227 * 1024) {
+    set_error("plan_rescore: %d receptor atoms do not fit in shared memory", r.n_rec);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  cudaError_t e = launch_rescore(pl->p, r, n, nullptr, nullptr, nullptr,
+                                 reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, out,
+                                 (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plan_rescore");
   return LIGATE_OK;
 }
 

@@ -18,6 +18,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "ligate_internal.h"
 
 namespace ligate {
@@ -251,11 +253,13 @@ __device__ __forceinline__ void step_cs(const DockParams &p, int k, float &c, fl
   s = p.cs_tab[2 * k + 1];
 }
 
-// Full FP32 score of pose (sid, tors) of the loaded ligand, warp-cooperative,
-// using the map `maps` read in mode MODE (scratch: pose slot `buf`).
+// Coordinates (grid units, .w = map offset of the atom's type for map
+// layout MODE) of pose (sid, tors) of the loaded ligand into buf:
+// rigid start frame, then each bond's step about its current axis.
+// Warp-cooperative.
 template <int MODE>
-__device__ float full_score(const DockParams &p, const void *maps, const WarpSmem &w, float4 *buf,
-                            const LigDesc &d, int sid, const uint32_t (&tors)[4], int lane) {
+__device__ void build_pose(const DockParams &p, const WarpSmem &w, float4 *buf, const LigDesc &d, int sid,
+                           const uint32_t (&tors)[4], int lane) {
   float R[9], T[3];
   start_frame(p, sid, R, T);
   const int ts = type_stride(MODE, p.g);
@@ -288,6 +292,14 @@ __device__ float full_score(const DockParams &p, const void *maps, const WarpSme
     }
     __syncwarp();
   }
+}
+
+// Full FP32 score of pose (sid, tors) of the loaded ligand, warp-cooperative,
+// using the map `maps` read in mode MODE (scratch: pose slot `buf`).
+template <int MODE>
+__device__ float full_score(const DockParams &p, const void *maps, const WarpSmem &w, float4 *buf,
+                            const LigDesc &d, int sid, const uint32_t (&tors)[4], int lane) {
+  build_pose<MODE>(p, w, buf, d, sid, tors, lane);
   float e = 0.f, cl = 0.f;
   for (int i = lane; i < d.n_atoms; i += 32) {
     const float4 xi = buf[i];
@@ -707,6 +719,145 @@ __global__ void __launch_bounds__(256) score_poses_kernel(const DockParams p, in
   }
   const float e = full_score<MODE>(p, p.maps, w, w.pose, d, sid, tt, lane);
   if (lane == 0) out[pi] = e;
+}
+
+// ---------------------------------------------------------------------------
+// Exact rescoring and filter of explicit or planned poses (paper Sec. 2: a
+// more accurate scoring of the generated poses, then a filter).  The
+// receptor term is the maps' pair potential evaluated at each atom:
+// min(cap, sum_j eps_tj ((r0/r)^12 - 2 (r0/r)^6)) over receptor atoms within
+// the cutoff, r floored at rmin (grid units throughout); the clash term is
+// the docking score's.  The CTA stages all receptor atoms in shared memory;
+// each warp takes poses, builds the pose, and for every ligand atom its
+// lanes split the receptor atoms (conflict-free consecutive reads).
+__global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const RecParams r, int n_poses,
+                                                     const int32_t *__restrict__ lig_idx,
+                                                     const int32_t *__restrict__ start_id,
+                                                     const uint8_t *__restrict__ tors,
+                                                     const PoseOut *__restrict__ poses,
+                                                     const int32_t *__restrict__ row_lig,
+                                                     ligate_rescored *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *rec = reinterpret_cast<float4 *>(smem_raw);
+  float2 *pair = reinterpret_cast<float2 *>(rec + r.n_rec);
+  unsigned char *slots = reinterpret_cast<unsigned char *>(pair + ((r.n_types * r.n_types + 1) & ~1));
+  for (int j = threadIdx.x; j < r.n_rec; j += blockDim.x) rec[j] = r.rec[j];
+  for (int j = threadIdx.x; j < r.n_types * r.n_types; j += blockDim.x) pair[j] = r.pair[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const WarpSmem w = warp_smem(slots + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1), p.nmax, 1);
+  int cur = -1;
+  LigDesc d;
+  for (int pi = blockIdx.x * W + warp; pi < n_poses; pi += gridDim.x * W) {
+    int li, sid;
+    uint32_t tt[4] = {0u, 0u, 0u, 0u};
+    if (poses) {
+      const PoseOut po = poses[pi];
+      li = row_lig[pi / p.K];
+      sid = po.start_id;
+      for (int q = 0; q < 4; ++q) tt[q] = po.tors[q];
+    } else {
+      li = lig_idx[pi];
+      sid = start_id[pi];
+      for (int q = 0; q < 16; ++q) tt[q >> 2] |= (uint32_t)tors[(size_t)pi * 16 + q] << (8 * (q & 3));
+    }
+    if (li < 0 || li >= p.n_ligands || sid < 0 || sid >= p.n_starts) {  // empty slot or bad index
+      if (lane == 0) {
+        ligate_rescored o;
+        o.energy = o.e_inter = o.e_clash = __int_as_float(0x7f800000);
+        o.n_outside = o.n_capped = -1;
+        o.pass = 0;
+        out[pi] = o;
+      }
+      continue;
+    }
+    if (li != cur) {
+      __syncwarp();
+      (void)load_ligand(p, w, li, d, lane);
+      cur = li;
+    }
+    build_pose<MODE_F32_PLAIN>(p, w, w.pose, d, sid, tt, lane);
+    float e_inter = 0.f;
+    int ncap = 0, nout = 0;
+    for (int i = 0; i < d.n_atoms; ++i) {
+      const float4 u = w.pose[i];
+      const int t = __float_as_int(w.ref[i].w);
+      const float2 *prow = pair + t * r.n_types;
+      float acc = 0.f;
+      for (int j = lane; j < r.n_rec; j += 32) {
+        const float4 a = rec[j];
+        const float dx = u.x - a.x, dy = u.y - a.y, dz = u.z - a.z;
+        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (d2 <= r.cut2) {
+          d2 = fmaxf(d2, r.rmin2);
+          const float2 pp = prow[__float_as_int(a.w)];
+          const float q2 = pp.x * __frcp_rn(d2);
+          const float q6 = q2 * q2 * q2;
+          acc = fmaf(pp.y, fmaf(q6, q6, -2.f * q6), acc);
+        }
+      }
+      acc = warp_sum(acc);
+      if (acc >= r.cap) { acc = r.cap; ++ncap; }
+      e_inter += acc;
+      nout += !((u.x >= 0.f) & (u.x <= p.g.fx1) & (u.y >= 0.f) & (u.y <= p.g.fy1) & (u.z >= 0.f) &
+                (u.z <= p.g.fz1));
+    }
+    float cl = 0.f;
+    for (int i = lane; i < d.n_atoms; i += 32) {
+      const float4 xi = w.pose[i];
+      for (int wd = 0; wd < d.n_words; ++wd) {
+        uint32_t m = __ldg(p.elig + d.elig_base + i * d.n_words + wd);
+        const int lo = i + 1 - 32 * wd;
+        if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
+        while (m) {
+          const int j = 32 * wd + __ffs(m) - 1;
+          m &= m - 1;
+          const float4 xj = w.pose[j];
+          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+          const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_grid, 1.f));
+          cl = fmaf(t, t, cl);
+        }
+      }
+    }
+    cl = p.clash_w * warp_sum(cl);
+    if (lane == 0) {
+      ligate_rescored o;
+      o.e_inter = e_inter;
+      o.e_clash = cl;
+      o.energy = e_inter + cl;
+      o.n_outside = nout;
+      o.n_capped = ncap;
+      o.pass = (nout == 0 && ncap == 0) ? 1 : 0;
+      out[pi] = o;
+    }
+    __syncwarp();
+  }
+}
+
+size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps) {
+  return (size_t)r.n_rec * 16 + (size_t)((r.n_types * r.n_types + 1) & ~1) * 8 +
+         (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1);
+}
+
+cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,
+                           const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
+                           const int32_t *row_lig, ligate_rescored *out, cudaStream_t s) {
+  if (n_poses <= 0) return cudaSuccess;
+  int warps = 4;
+  while (warps > 1 && rescore_smem_bytes(p, r, warps) > 227 * 1024) --warps;
+  const size_t smem = rescore_smem_bytes(p, r, warps);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rescore_kernel, 32 * warps, smem)))
+    return e;
+  const long long need = (n_poses + warps - 1) / warps;
+  const int grid = (int)std::min<long long>(need, (long long)sms * std::max(occ, 1));
+  rescore_kernel<<<grid, 32 * warps, smem, s>>>(p, r, n_poses, lig_idx, start_id, tors,
+                                                reinterpret_cast<const PoseOut *>(poses), row_lig, out);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

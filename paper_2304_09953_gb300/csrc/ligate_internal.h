@@ -72,6 +72,19 @@ struct PocketDev {
   uint16_t *map_f16c = nullptr;    // corner [T][cells][8]
   size_t n_nodes() const { return (size_t)nx * ny * nz; }
   size_t n_cells() const { return (size_t)(nx - 1) * (ny - 1) * (nz - 1); }
+  // receptor for exact rescoring (ligate_pocket_set_receptor), grid units
+  float4 *rec = nullptr;           // [n_rec] (u, type bits)
+  float2 *rec_pair = nullptr;      // [rec_types][rec_types] (r0^2 / h^2, eps)
+  int n_rec = 0, rec_types = 0;
+  float rec_cut2 = 0.f, rec_cap = 0.f, rec_rmin2 = 0.f;  // cutoff^2 / h^2, cap, rmin^2 / h^2
+};
+
+// Receptor term of the exact rescoring, device view.
+struct RecParams {
+  const float4 *rec;
+  const float2 *pair;
+  int n_rec, n_types;
+  float cut2, cap, rmin2;
 };
 
 // Map-read modes of the docking kernel.
@@ -152,6 +165,13 @@ inline void fill_step_table(int S, float *tab) {
     tab[2 * k + 1] = k < S ? (float)(k == 0 ? 0.0 : std::sin(a)) : 0.f;
   }
 }
+
+// Exact rescoring (dock.cu): explicit poses (lig_idx, start_id, tors) or,
+// with poses != NULL, a plan's output [n_poses / K][K] with row_lig.
+size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps);
+cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,
+                           const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
+                           const int32_t *row_lig, ligate_rescored *out, cudaStream_t s);
 
 // Pose refinement (refine.cu): mode 0 energy + gradient of explicit
 // states, 1 refine explicit states, 2 refine a plan's poses.

@@ -11,6 +11,10 @@ class PocketHandle:
     def __init__(self, pocket, mask=N.LIGATE_POCKET_FP32_CORNER | N.LIGATE_POCKET_BF16_CORNER
                  | N.LIGATE_POCKET_FP16_CORNER):
         self.h = N.ligate_pocket_create(pocket.maps, pocket.origin, pocket.spacing, pocket.anchors, mask)
+        if getattr(pocket, "receptor_xyz", None) is not None and getattr(pocket, "type_radius", None) is not None:
+            r = pocket.receptor()
+            N.ligate_pocket_set_receptor(self.h, r["xyz"], r["type"], r["radius"], r["eps"], r["cutoff"],
+                                         r["cap"], r["rmin"])
 
     def close(self):
         if getattr(self, "h", None):
@@ -74,6 +78,15 @@ class Plan:
         torch.cuda.synchronize()
         return buf.cpu().numpy().view(N.REFINED_DTYPE).reshape(self.n, self.k)
 
+    def rescore_exact(self, stream=None) -> np.ndarray:
+        """Exact receptor term + clash and the filter flags of every pose of
+        the last run (ligate_plan_rescore); RESCORED_DTYPE [n, K] on the host."""
+        import torch
+        buf = torch.empty(self.n * self.k * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        N.ligate_plan_rescore(self.h, buf, stream)
+        torch.cuda.synchronize()
+        return buf.cpu().numpy().view(N.RESCORED_DTYPE).reshape(self.n, self.k)
+
     def device_output(self) -> int:
         """Device address of the last run's ligate_pose[n][K] result."""
         return N.ligate_plan_output(self.h)
@@ -103,3 +116,13 @@ def dock(pocket, ligands, sampling, mode="fp32", rescore=None, tile=None, top_k=
         pl.close()
         bh.close()
         ph.close()
+
+
+def best_passing(rescored: np.ndarray):
+    """Per ligand (row) the index of the lowest-energy pose that passes the
+    filter, or -1 when none passes; and that energy (+inf when none)."""
+    e = np.where(rescored["pass"] == 1, rescored["energy"], np.inf)
+    idx = np.argmin(e, axis=1)
+    best = e[np.arange(len(e)), idx]
+    return np.where(np.isfinite(best), idx, -1), best
+

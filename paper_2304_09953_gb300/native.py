@@ -63,6 +63,8 @@ STATE_DTYPE = np.dtype([("rot", np.float32, (9,)), ("trans", np.float32, (3,)), 
 REFINED_DTYPE = np.dtype([("state", STATE_DTYPE), ("score_in", np.float32), ("score", np.float32),
                           ("accepted", np.uint32), ("ligand", np.int32)])
 assert STATE_DTYPE.itemsize == 112 and REFINED_DTYPE.itemsize == 128
+RESCORED_DTYPE = np.dtype([("energy", np.float32), ("e_inter", np.float32), ("e_clash", np.float32),
+                           ("n_outside", np.int32), ("n_capped", np.int32), ("pass", np.int32)])
 
 
 class ligate_tile(ctypes.Structure):
@@ -112,6 +114,10 @@ _SIGS = {
     "ligate_pose_gradient": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_refine_states": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_float, P, P]),
     "ligate_plan_refine": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_float, P, P]),
+    "ligate_pocket_set_receptor": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_float,
+                                                  ctypes.c_float, ctypes.c_float]),
+    "ligate_rescore_poses": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
+    "ligate_plan_rescore": (ctypes.c_int, [P, P, P]),
 }
 
 _lib = None
@@ -308,6 +314,25 @@ def ligate_refine_states(pocket, batch, sampling_struct, n, lig_idx, init, itera
 def ligate_plan_refine(plan, iterations, eta0, out, stream=None):
     check(load().ligate_plan_refine(plan, int(iterations), float(eta0), _ptr(out), stream),
           "ligate_plan_refine")
+
+
+def ligate_pocket_set_receptor(pocket, xyz, type_, radius, eps, cutoff, cap, rmin):
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    type_ = np.ascontiguousarray(type_, np.int32)
+    radius = np.ascontiguousarray(radius, np.float32)
+    eps = np.ascontiguousarray(eps, np.float32)
+    check(load().ligate_pocket_set_receptor(pocket, xyz.ctypes.data, type_.ctypes.data, len(type_),
+                                            radius.ctypes.data, eps.ctypes.data, len(radius), float(cutoff),
+                                            float(cap), float(rmin)), "ligate_pocket_set_receptor")
+
+
+def ligate_rescore_poses(pocket, batch, sampling_struct, n, lig_idx, start_id, tors, out, stream=None):
+    check(load().ligate_rescore_poses(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
+                                      _ptr(start_id), _ptr(tors), _ptr(out), stream), "ligate_rescore_poses")
+
+
+def ligate_plan_rescore(plan, out, stream=None):
+    check(load().ligate_plan_rescore(plan, _ptr(out), stream), "ligate_plan_rescore")
 
 
 def ligate_autotune(pocket, batch, sampling_struct, budget_ms=20000.0):
