@@ -393,6 +393,21 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes),
                "ms_per_step": 1000 * statistics.mean(et)}
 
+    # analytic launch model (no timing) against the autotuned shape
+    model = None
+    if not args.no_tune:
+        mt = N.ligate_model_tile(ph.h, bh.h, s_chosen)
+        mplan = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=mt)
+        for _ in range(2):
+            N.ligate_plan_run(mplan.h, None, sh)
+        mms = statistics.mean(timed(mplan, args.steps))
+        mt_, _ = mplan.tile()
+        model = {"value": ws * n_lig / (mms / 1000), "unit": "ligands/s", "ms_per_step": mms,
+                 "vs_autotuned": (ws * n_lig / (mms / 1000)) / value,
+                 "tile": {"warps_per_cta": mt_.warps_per_cta, "ctas_per_sm": mt_.ctas_per_sm,
+                          "starts_per_item": list(mt_.starts_per_item), "reg_cap": mt_.reg_cap}}
+        mplan.close()
+
     refine = None
     if not args.no_refine:
         # gradient-descent refinement of the chosen form's top-K poses (FP32 maps)
@@ -487,7 +502,7 @@ def main():
                                          "pair_tests": work.done_pair_tests,
                                          "pair_survivors": work.done_pair_survivors,
                                          "pair_candidates_x_S": work.pair_evals, "poses": work.poses}},
-        "triage": triage, "refine": refine, "rescore": rescore,
+        "triage": triage, "refine": refine, "rescore": rescore, "model_tile": model,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
         "gpu_launches": launches_per_run * args.steps,
     }

@@ -382,6 +382,21 @@ ligate_status ligate_autotune(const ligate_pocket *pocket, const ligate_batch *b
                               const ligate_sampling *sampling, double budget_ms,
                               ligate_tile *best);
 
+/* Analytic launch model (paper Sec. 3.3: a batch shape per ligand size),
+ * chosen without timing anything.  Shape: the CTA size and register cap
+ * that keep the most warps resident on one SM under the register file and
+ * shared-memory limits (for the plain FP32 layout only among the 128-register
+ * instances: its eight scalar gathers per interpolation need registers for
+ * loads in flight).  Chunk of size bucket b: starts_per_item[b] =
+ * W / (8 P c_b) clamped to [128, 2048] and rounded down to the start group,
+ * with W the run's total work (sum over ligands of starts x per-start cost
+ * atoms + 0.35 clash pairs + 40), P the resident warps of the whole GPU and
+ * c_b the bucket's mean per-start cost: the largest item stays under an
+ * eighth of a warp's share, small enough to balance the tail, large enough
+ * to amortise loading a ligand.  Writes *out; needs the current device. */
+ligate_status ligate_model_tile(const ligate_pocket *pocket, const ligate_batch *batch,
+                                const ligate_sampling *sampling, ligate_tile *out);
+
 /* ------------------------------------------------------------------------
  * Ligand descriptors for the triage surrogate (paper Sec. 3.5: ligand
  * features as input of an affinity predictor).  Per ligand 256 FP32:

@@ -1233,6 +1233,60 @@ static double time_tile(const ligate_pocket *P, const ligate_batch *B, const lig
   return best;
 }
 
+extern "C" ligate_status ligate_model_tile(const ligate_pocket *P, const ligate_batch *B,
+                                           const ligate_sampling *s, ligate_tile *out) {
+  if (!out) { set_error("model_tile: out is NULL"); return LIGATE_ERR_INVALID; }
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  int dev = 0, sms = 1, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int S = s->torsion_steps, G = 32 / pow2ceil(S);
+  const int nmax = std::max(32, (B->d.max_atoms + 31) / 32 * 32);
+  const size_t per_warp = dock_smem_per_warp(nmax, S, G);
+  ligate_tile t;
+  memset(&t, 0, sizeof(t));
+  int best_res = 0;
+  for (int cap = 1; cap <= 3; ++cap) {
+    if (mode == MODE_F32_PLAIN && cap != 3) continue;
+    const int minb = cap == 1 ? 6 : cap == 2 ? 5 : 4;  // CTAs of 128 threads the register cap allows
+    for (int warps : {2, 4}) {
+      const size_t cta_smem = per_warp * warps + 1024;  // + the per-CTA reserve
+      if (cta_smem > 227 * 1024) continue;
+      const int by_regs = minb * 4 / warps;
+      const int by_smem = (int)(smem_sm / cta_smem);
+      const int res = std::min(by_regs, by_smem) * warps;  // resident warps per SM
+      if (res > best_res) { best_res = res; t.warps_per_cta = warps; t.reg_cap = cap; }
+    }
+  }
+  if (best_res == 0) {
+    set_error("model_tile: ligands too large for any CTA shape");
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  const double P_w = (double)sms * best_res;
+  const int n_starts = s->n_orient * s->n_anchor;
+  double W = 0.0, cb[LIGATE_N_BUCKETS] = {0}, nb[LIGATE_N_BUCKETS] = {0};
+  for (int i = 0; i < B->d.n_ligands; ++i) {
+    double a, q;
+    start_work(B->d, i, S, a, q);
+    const double c = a + 0.35 * q + 40.0;
+    W += c * n_starts;
+    const int b = bucket_of(B->d.h_lig[i]);
+    cb[b] += c;
+    nb[b] += 1.0;
+  }
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
+    double chunk = 512.0;
+    if (nb[b] > 0) chunk = W / (8.0 * P_w * (cb[b] / nb[b]));
+    chunk = std::min(2048.0, std::max(128.0, chunk));
+    t.starts_per_item[b] = std::max(G, (int)chunk / G * G);
+  }
+  *out = t;
+  return LIGATE_OK;
+}
+
 extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_batch *B,
                                          const ligate_sampling *s, double budget_ms,
                                          ligate_tile *best) {

@@ -101,6 +101,7 @@ _SIGS = {
     "ligate_dock_noalloc": (ctypes.c_int, [P, P, P, P, P]),
     "ligate_score_poses": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_autotune": (ctypes.c_int, [P, P, P, ctypes.c_double, P]),
+    "ligate_model_tile": (ctypes.c_int, [P, P, P, P]),
     "ligate_descriptors": (ctypes.c_int, [P, P, P]),
     "ligate_surrogate_create": (ctypes.c_int, [P, ctypes.c_uint64, P]),
     "ligate_surrogate_destroy": (None, [P]),
@@ -339,6 +340,13 @@ def ligate_autotune(pocket, batch, sampling_struct, budget_ms=20000.0):
     t = ligate_tile()
     check(load().ligate_autotune(pocket, batch, ctypes.byref(sampling_struct), float(budget_ms),
                                  ctypes.byref(t)), "ligate_autotune")
+    return t
+
+
+def ligate_model_tile(pocket, batch, sampling_struct):
+    t = ligate_tile()
+    check(load().ligate_model_tile(pocket, batch, ctypes.byref(sampling_struct), ctypes.byref(t)),
+          "ligate_model_tile")
     return t
 
 

@@ -202,3 +202,25 @@ def test_autotune_cache_round_trip(batched_small, tmp_path, monkeypatch):
     assert list(t.starts_per_item) == list(best.starts_per_item)
     ref = D.Plan(ph, bh, w.sampling, mode="bf16", tile=N.ligate_tile()).result()
     assert np.array_equal(pl.result(), ref)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_model_tile_is_valid_and_changes_nothing(batched_small, mode):
+    """The analytic launch model gives a shape the plan accepts (plain layout:
+    the 128-register instance; chunks within [128, 2048], multiples of the
+    start group) and the same results as the default shape."""
+    w = batched_small
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    prec, layout = D.MODES[mode]
+    s = N.make_sampling(w.sampling, prec, layout, rescore=(mode != "fp32"))
+    t = N.ligate_model_tile(ph.h, bh.h, s)
+    assert t.warps_per_cta in (2, 4) and t.reg_cap in (1, 2, 3)
+    if mode == "fp32":
+        assert t.reg_cap == 3
+    G = 32 // (1 << (w.sampling.torsion_steps - 1).bit_length())
+    for c in t.starts_per_item:
+        assert c % G == 0 and G <= c <= 2048
+    pl = D.Plan(ph, bh, w.sampling, mode=mode, tile=t)
+    ref = D.Plan(ph, bh, w.sampling, mode=mode, tile=N.ligate_tile()).result()
+    assert np.array_equal(pl.result(), ref)
