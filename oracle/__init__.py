@@ -82,6 +82,7 @@ def _load():
         lib.or_pose_grad.argtypes = [P, P, P, I, P, P, P, P, P, P]
         lib.or_refine.argtypes = [P, P, P, I, P, I, D, P, D, P, P, P, P, P, P]
         lib.or_rescore_coords.argtypes = [P, P, P, P, I, P, P, P, P, P, P]
+        lib.or_pose_features.argtypes = [P, P, P, I, P, P]
         _lib = lib
     return _lib
 
@@ -379,4 +380,19 @@ def rescore_coords(lig, pocket, sampling, receptor, coords):
                              ec.ctypes.data, no.ctypes.data, nc.ctypes.data, sc.ctypes.data):
         raise ValueError("ligand bonds do not form a tree")
     return {"e_inter": ei, "e_clash": ec, "n_outside": no, "n_capped": nc, "scale": sc}
+
+
+def pose_features(lig, pocket, sampling, coords) -> np.ndarray:
+    """Per-pose selector features [n_poses, 256] of coordinate sets
+    [n_poses, n_atoms, 3] (see the pose-feature section of ligate_oracle.c)."""
+    lib = _load()
+    k = _Keep()
+    L = _lig(k, *lig)
+    P = _pock(k, pocket)
+    S = _samp(k, sampling, pocket.anchors)
+    x = _c(coords, np.float64)
+    out = np.zeros((x.shape[0], 256))
+    if lib.or_pose_features(_ref(L), _ref(P), _ref(S), x.shape[0], x.ctypes.data, out.ctypes.data):
+        raise ValueError("ligand bonds do not form a tree")
+    return out
 

@@ -907,6 +907,67 @@ OR_EXPORT int or_rescore_coords(const or_ligand_in *li, const or_pocket_in *pi, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Pose features for the learned pose selector (paper Sec. 3.5: a           */
+/* high-throughput pose selector trading a little accuracy for much         */
+/* throughput).  Per pose, 256 entries:                                      */
+/*   [0, 64)   log1p of the count of atoms whose grid value v (trilinear, or  */
+/*             the penalty) falls in bin min(63, max(0, floor(4 (v + 4))))   */
+/*             -- 0.25-wide bins over [-4, 12);                              */
+/*   [64, 72)  mean grid value of the atoms of each type 0..7 (0 if none);   */
+/*   [72]      the docking score divided by the atom count;                  */
+/*   [73]      the clash term (weight included);                             */
+/*   [74]      log1p(atom count);  [75] rotatable-bond count;                */
+/*   [76]      log1p of the count of atoms with v >= 9;                      */
+/*   [77, 256) zero.                                                         */
+/* The bin of v is decided in FP32: v is rounded to FP32 first (the GPU's    */
+/* precision), so both sides bin the same value unless their values differ */
+/* across an edge.                                                           */
+OR_EXPORT int or_pose_features(const or_ligand_in *li, const or_pocket_in *pi, const or_sampling *sp,
+                               int n_poses, const double *coords, double *out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  or_pocket P;
+  make_pocket(pi, sp->penalty, &P);
+  or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
+  const int n = L.n;
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int p = 0; p < n_poses; ++p) {
+    const double (*x)[3] = (const double(*)[3])(coords + (size_t)p * n * 3);
+    double *f = out + (size_t)p * 256;
+    for (int k = 0; k < 256; ++k) f[k] = 0.0;
+    double cnt[64] = {0}, tsum[8] = {0}, tn[8] = {0}, e = 0.0, high = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double v = trilinear(&P, L.type[i], x[i]);
+      e += v;
+      volatile float vf = (float)v;
+      volatile float sc = (vf + 4.0f) * 4.0f;
+      int b = (int)floorf(sc);
+      b = b < 0 ? 0 : (b > 63 ? 63 : b);
+      cnt[b] += 1.0;
+      if (L.type[i] < 8) { tsum[L.type[i]] += v; tn[L.type[i]] += 1.0; }
+      if (vf >= 9.0f) high += 1.0;
+    }
+    double cl = 0.0, inv = 1.0 / (C.dc * C.dc);
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        if (L.topo[(size_t)i * n + j] < C.min_sep) continue;
+        double dx = x[i][0] - x[j][0], dy = x[i][1] - x[j][1], dz = x[i][2] - x[j][2];
+        double t = 1.0 - (dx * dx + dy * dy + dz * dz) * inv;
+        if (t > 0.0) cl += t * t;
+      }
+    for (int b = 0; b < 64; ++b) f[b] = log1p(cnt[b]);
+    for (int t = 0; t < 8; ++t) f[64 + t] = tn[t] > 0.0 ? tsum[t] / tn[t] : 0.0;
+    f[72] = (e + C.w * cl) / n;
+    f[73] = C.w * cl;
+    f[74] = log1p((double)n);
+    f[75] = (double)L.nrot;
+    f[76] = log1p(high);
+  }
+  lig_free(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Descriptor (256 entries, 233 used).                                       */
 OR_EXPORT int or_descriptor(const or_ligand_in *li, int n_types, double *out) {
   if (n_types != 8) return -1;
