@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--no-triage", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-rescore", action="store_true")
+    ap.add_argument("--no-selector", action="store_true")
+    ap.add_argument("--selector-train-ligands", type=int, default=20000)
     ap.add_argument("--refine-iters", type=int, default=32)
     ap.add_argument("--train-ligands", type=int, default=200000)
     ap.add_argument("--keep-frac", type=float, default=0.05)
@@ -198,6 +200,93 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
                                      "triage gives no speed-up at 0.99 recall"}
     N.ligate_surrogate_destroy(sur)
     return out
+
+
+def run_pose_selector(args, w, ph, chosen, tile, stream, sh, fail_label=30.0):  # noqa: C901
+    """Learned per-pose selector (paper Sec. 3.5: a high-throughput pose
+    selector).  Train the triage network on per-pose features of the top-K
+    poses of a separate seeded training library, labelled by the exact
+    rescoring kernel (exact energy of passing poses, clipped to fail_label;
+    failing poses fail_label).  On the library: features + network pick one
+    pose per ligand; compared with the exact rescoring of all K poses (the
+    truth) and with taking the docking rank-0 pose."""
+    import torch
+    from paper_2304_09953_gb300 import docking as D
+    from paper_2304_09953_gb300 import native as N
+    from paper_2304_09953_gb300 import selector as SEL
+    from paper_2304_09953_gb300.workload import make_workload
+
+    K = w.sampling.top_k
+    tw = make_workload("learned_train", n_ligands=args.selector_train_ligands, pocket=w.pocket)
+    tb = D.BatchHandle(tw.ligands)
+    tp = D.Plan(ph, tb, tw.sampling, mode="bf16", rescore=True, tile=tile)
+    tp.run(sh)
+    nt = tw.ligands.n * K
+    feat = torch.empty((nt, 256), dtype=torch.float32, device="cuda")
+    N.ligate_plan_pose_features(tp.h, feat, sh)
+    rs = torch.empty(nt * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_plan_rescore(tp.h, rs, sh)
+    torch.cuda.synchronize()
+    r = rs.cpu().numpy().view(N.RESCORED_DTYPE)
+    lab = SEL.labels(r, fail_label)
+    live = np.isfinite(r["energy"])
+    idx = torch.from_numpy(np.nonzero(live)[0]).cuda()
+    x_tr = feat[idx].contiguous()
+    y_tr = torch.from_numpy(lab[live]).cuda()
+    sel_net = N.ligate_surrogate_create(None, 77)
+    t0 = time.perf_counter()
+    N.ligate_surrogate_train(sel_net, x_tr, y_tr, len(idx), 10, 1024, 1e-3, 77, sh)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del feat, rs, x_tr, y_tr
+    tp.close()
+    tb.close()
+
+    n = w.ligands.n
+    n_poses = n * K
+    fbuf = torch.empty((n_poses, 256), dtype=torch.float32, device="cuda")
+    pred = torch.empty(n_poses, dtype=torch.float32, device="cuda")
+    N.ligate_plan_run(chosen.h, None, sh)
+    ms = []
+    for _ in range(max(2, args.steps)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        N.ligate_plan_pose_features(chosen.h, fbuf, sh)
+        N.ligate_surrogate_predict(sel_net, fbuf, n_poses, pred, sh)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    p_ = pred.cpu().numpy().reshape(n, K)
+    rbuf = torch.empty(n_poses * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_plan_rescore(chosen.h, rbuf, sh)
+    torch.cuda.synchronize()
+    ex = rbuf.cpu().numpy().view(N.RESCORED_DTYPE).reshape(n, K)
+    N.ligate_surrogate_destroy(sel_net)
+    best_idx, best_e = D.best_passing(ex)
+    has = best_idx >= 0
+    p_ = np.where(np.isfinite(ex["energy"]), p_, np.inf)
+    pick = np.argmin(p_, axis=1)
+    rows = np.arange(n)
+
+    def stats(choice):
+        ok = ex["pass"][rows, choice] == 1
+        gap = np.where(ok & has, ex["energy"][rows, choice] - best_e, np.nan)
+        return {"top1_agreement": float(np.mean(choice[has] == best_idx[has])),
+                "chosen_passes": float(np.mean(ok[has])),
+                "mean_energy_gap_when_passing": float(np.nanmean(gap))}
+
+    # the selector's rule: the best-docked pose predicted to pass, else the
+    # lowest prediction
+    first_ok = SEL.select(p_, np.isfinite(ex["energy"]), fail_label)
+    t = statistics.mean(ms)
+    return {"value": n_poses / (t / 1000), "unit": "poses selected/s", "ms_per_step": t,
+            "train_ligands": tw.ligands.n, "train_poses": int(live.sum()), "train_s": round(t_train, 2),
+            "selector": stats(first_ok), "network_argmin": stats(pick),
+            "docking_rank0": stats(np.zeros(n, np.int64)),
+            "ligands_with_passing_pose": float(np.mean(has)),
+            "form": "pose features (FP32 maps) + triage network trained on exact rescoring labels; "
+                    "the truth is the exact rescoring of all top-16 poses"}
 
 
 class Clocks:
@@ -470,6 +559,12 @@ def main():
                            "no capped atom; receptor staged in shared memory, one warp per pose"}
         del sbuf
 
+    selector = None
+    if not args.no_selector and w.pocket.receptor_xyz is not None and rank == 0:
+        selector = run_pose_selector(args, w, ph, chosen, tile, stream, sh)
+        if rescore is not None:
+            selector["speedup_vs_exact_rescoring"] = rescore["ms_per_step"] / selector["ms_per_step"]
+
     triage = None
     if not args.no_triage and rank == 0:  # one-GPU form; other ranks only time docking
         triage = run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh)
@@ -502,7 +597,8 @@ def main():
                                          "pair_tests": work.done_pair_tests,
                                          "pair_survivors": work.done_pair_survivors,
                                          "pair_candidates_x_S": work.pair_evals, "poses": work.poses}},
-        "triage": triage, "refine": refine, "rescore": rescore, "model_tile": model,
+        "triage": triage, "refine": refine, "rescore": rescore, "pose_selector": selector,
+        "model_tile": model,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
         "gpu_launches": launches_per_run * args.steps,
     }

@@ -374,6 +374,25 @@ ligate_status ligate_rescore_poses(const ligate_pocket *pocket, const ligate_bat
 ligate_status ligate_plan_rescore(const ligate_plan *plan, ligate_rescored *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Per-pose selector features (paper Sec. 3.5: a high-throughput pose
+ * selector trading a little accuracy for throughput; a learned model on
+ * these features -- e.g. the triage surrogate network trained on exact
+ * rescoring results -- picks the pose to keep without rescoring them all).
+ * Per pose 256 FP32: [0, 64) log1p of the counts of atoms whose FP32 grid
+ * value v (FP32 maps; the penalty outside) falls in bin min(63, max(0,
+ * floor((v + 4) * 4))); [64, 72) mean v of the atoms of each type 0..7 (0
+ * if none); [72] docking score / atom count; [73] clash term; [74]
+ * log1p(atom count); [75] rotatable-bond count; [76] log1p of the count of
+ * atoms with v >= 9; [77, 256) zero.  Explicit poses as in
+ * ligate_rescore_poses (DEVICE arrays, out DEVICE [n][256], synchronises)
+ * or every pose of a plan's last run (out DEVICE [n_ligands][top_k][256];
+ * empty slots all zero; enqueues). */
+ligate_status ligate_pose_features(const ligate_pocket *pocket, const ligate_batch *batch,
+                                   const ligate_sampling *sampling, int n, const int32_t *lig_idx,
+                                   const int32_t *start_id, const uint8_t *tors, float *out, void *stream);
+ligate_status ligate_plan_pose_features(const ligate_plan *plan, float *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Autotuner (paper Sec. 3.3: per-size batch tuning).  Times candidate
  * shapes on a sample of the batch's ligands per size bucket and writes the
  * best to *best (and to the cache file named by LIGATE_TUNE_CACHE, when

@@ -1086,6 +1086,43 @@ extern "C" ligate_status ligate_plan_rescore(const ligate_plan *pl, ligate_resco
   return LIGATE_OK;
 }
 
+extern "C" ligate_status ligate_pose_features(const ligate_pocket *P, const ligate_batch *B,
+                                              const ligate_sampling *s, int n, const int32_t *lig_idx,
+                                              const int32_t *start_id, const uint8_t *tors, float *out,
+                                              void *stream) {
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  if (n < 0 || (n > 0 && (!lig_idx || !start_id || !tors || !out))) {
+    set_error("pose_features: bad pose arrays");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n == 0) return LIGATE_OK;
+  DockParams p;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  st = base_params(P, B, s, mode, p, &rot, &anc, &quat);
+  cudaError_t e = cudaSuccess;
+  if (st == LIGATE_OK) {
+    e = launch_pose_features(p, n, lig_idx, start_id, tors, nullptr, nullptr, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  cudaFree(rot); cudaFree(anc); cudaFree(quat);
+  if (st != LIGATE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "pose_features");
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_pose_features(const ligate_plan *pl, float *out, void *stream) {
+  if (!pl || !out) { set_error("plan_pose_features: NULL argument"); return LIGATE_ERR_INVALID; }
+  const int n = pl->n_ligands * pl->p.K;
+  if (n == 0) return LIGATE_OK;
+  cudaError_t e = launch_pose_features(pl->p, n, nullptr, nullptr, nullptr,
+                                       reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, out,
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plan_pose_features");
+  return LIGATE_OK;
+}
+
 // ===========================================================================
 // Autotuner: per size bucket, time a sample of that bucket's ligands under
 // candidate chunk sizes; the CTA shape (warps per CTA) is tuned on the whole

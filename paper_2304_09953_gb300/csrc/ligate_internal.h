@@ -173,6 +173,12 @@ cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses,
                            const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
                            const int32_t *row_lig, ligate_rescored *out, cudaStream_t s);
 
+// Per-pose selector features (dock.cu), [n_poses][256] FP32; explicit
+// poses or a plan's output as for launch_rescore.
+cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t *lig_idx,
+                                 const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
+                                 const int32_t *row_lig, float *out, cudaStream_t s);
+
 // Pose refinement (refine.cu): mode 0 energy + gradient of explicit
 // states, 1 refine explicit states, 2 refine a plan's poses.
 size_t refine_smem_bytes(int nmax);

@@ -119,6 +119,8 @@ _SIGS = {
                                                   ctypes.c_float, ctypes.c_float]),
     "ligate_rescore_poses": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_plan_rescore": (ctypes.c_int, [P, P, P]),
+    "ligate_pose_features": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
+    "ligate_plan_pose_features": (ctypes.c_int, [P, P, P]),
 }
 
 _lib = None
@@ -334,6 +336,15 @@ def ligate_rescore_poses(pocket, batch, sampling_struct, n, lig_idx, start_id, t
 
 def ligate_plan_rescore(plan, out, stream=None):
     check(load().ligate_plan_rescore(plan, _ptr(out), stream), "ligate_plan_rescore")
+
+
+def ligate_pose_features(pocket, batch, sampling_struct, n, lig_idx, start_id, tors, out, stream=None):
+    check(load().ligate_pose_features(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
+                                      _ptr(start_id), _ptr(tors), _ptr(out), stream), "ligate_pose_features")
+
+
+def ligate_plan_pose_features(plan, out, stream=None):
+    check(load().ligate_plan_pose_features(plan, _ptr(out), stream), "ligate_plan_pose_features")
 
 
 def ligate_autotune(pocket, batch, sampling_struct, budget_ms=20000.0):

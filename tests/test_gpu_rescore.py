@@ -107,3 +107,98 @@ def test_rescore_needs_a_receptor(tiny):
     out = torch.zeros(N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError):
         N.ligate_rescore_poses(ph.h, bh.h, s, 1, z, z, t, out)
+
+
+@pytest.mark.parametrize("name", ["tiny", "batched_small"])
+def test_pose_features_match_oracle(name, request):
+    """Histogram counts equal the oracle's (FP32 bin decisions on both sides)
+    for at least 99% of poses; means, score and clash entries within 1e-4 of
+    their term scale; the plan path equals the explicit path."""
+    w = request.getfixturevalue(name)
+    lig, sid, tors = explicit(w, 128 if name == "tiny" else 8, 11)
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    s = N.make_sampling(w.sampling)
+    n = len(lig)
+    out = torch.zeros((n, 256), dtype=torch.float32, device="cuda")
+    N.ligate_pose_features(ph.h, bh.h, s, n, torch.from_numpy(lig).cuda(), torch.from_numpy(sid).cuda(),
+                           torch.from_numpy(tors).cuda(), out)
+    f = out.cpu().numpy().astype(np.float64)
+    same_hist = 0
+    for li in np.unique(lig):
+        sel = np.nonzero(lig == li)[0]
+        R_n = int(w.ligands.n_rot[li])
+        L = w.ligands.ligand(li)
+        x = oracle.pose_coords(L, w.pocket.anchors, w.sampling, sid[sel], tors[sel, :R_n].astype(np.int32))
+        o = oracle.pose_features(L, w.pocket, w.sampling, x)
+        _, scale = oracle.score_poses(L, w.pocket, w.sampling, sid[sel], tors[sel, :R_n].astype(np.int32),
+                                      with_scale=True)
+        n_at = len(L[1])
+        for m, k in enumerate(sel):
+            same = np.array_equal(np.round(np.expm1(f[k, :64])), np.round(np.expm1(o[m, :64])))
+            same_hist += same
+            if same:
+                np.testing.assert_allclose(f[k, :64], o[m, :64], rtol=2e-6, atol=2e-6)
+            tol = 1e-4 * max(scale[m], 1.0)
+            assert abs(f[k, 72] - o[m, 72]) * n_at <= tol
+            assert abs(f[k, 73] - o[m, 73]) <= tol
+            np.testing.assert_allclose(f[k, 64:72], o[m, 64:72], atol=tol)
+            np.testing.assert_allclose(f[k, 74:77], o[m, 74:77], rtol=1e-6)
+            assert np.all(f[k, 77:] == 0)
+    assert same_hist >= 0.99 * n, (same_hist, n)
+
+
+def test_learned_selector_beats_docking_rank(workload_factory):
+    """Train the network on pose features of 6,000 seeded training ligands
+    (labels from the exact rescoring kernel) and select on 2,000 library
+    ligands: the kept pose passes the filter more often than the best-docked
+    pose does, and is the exact-best passing pose at least as often."""
+    from paper_2304_09953_gb300 import selector as SEL
+    w = workload_factory("batched", n_ligands=2000)
+    tw = workload_factory("learned_train", n_ligands=6000)
+    assert np.array_equal(tw.pocket.maps, w.pocket.maps)
+    ph = D.PocketHandle(w.pocket)
+    K = w.sampling.top_k
+
+    def features_and_truth(lig_w):
+        bh = D.BatchHandle(lig_w.ligands)
+        pl = D.Plan(ph, bh, lig_w.sampling, mode="bf16")
+        pl.run()
+        n = lig_w.ligands.n * K
+        f = torch.empty((n, 256), dtype=torch.float32, device="cuda")
+        N.ligate_plan_pose_features(pl.h, f)
+        r = torch.empty(n * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        N.ligate_plan_rescore(pl.h, r)
+        torch.cuda.synchronize()
+        out = f, r.cpu().numpy().view(N.RESCORED_DTYPE)
+        pl.close()
+        bh.close()
+        return out
+
+    ftr, rtr = features_and_truth(tw)
+    live = np.isfinite(rtr["energy"])
+    idx = torch.from_numpy(np.nonzero(live)[0]).cuda()
+    net = N.ligate_surrogate_create(None, 5)
+    try:
+        N.ligate_surrogate_train(net, ftr[idx].contiguous(), torch.from_numpy(SEL.labels(rtr[live])).cuda(),
+                                 len(idx), 10, 1024, 1e-3, 5)
+        f, r = features_and_truth(w)
+        pred = torch.empty(f.shape[0], dtype=torch.float32, device="cuda")
+        N.ligate_surrogate_predict(net, f, f.shape[0], pred)
+        p = pred.cpu().numpy().reshape(-1, K)
+    finally:
+        N.ligate_surrogate_destroy(net)
+    ex = r.reshape(-1, K)
+    best_idx, _ = D.best_passing(ex)
+    has = best_idx >= 0
+    rows = np.arange(len(ex))
+    pick = SEL.select(p, np.isfinite(ex["energy"]))
+    rank0 = np.zeros(len(ex), np.int64)
+    pass_sel = np.mean(ex["pass"][rows, pick][has] == 1)
+    pass_r0 = np.mean(ex["pass"][rows, rank0][has] == 1)
+    top_sel = np.mean(pick[has] == best_idx[has])
+    top_r0 = np.mean(rank0[has] == best_idx[has])
+    print("passes: selector %.3f rank-0 %.3f; exact-best: selector %.3f rank-0 %.3f"
+          % (pass_sel, pass_r0, top_sel, top_r0))
+    assert pass_sel >= pass_r0 + 0.03
+    assert top_sel >= top_r0
