@@ -783,22 +783,31 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
       const float4 u = w.pose[i];
       const int t = __float_as_int(w.ref[i].w);
       const float2 *prow = pair + t * r.n_types;
-      float acc = 0.f;
-      for (int j = lane; j < r.n_rec; j += 32) {
-        const float4 a = rec[j];
-        const float dx = u.x - a.x, dy = u.y - a.y, dz = u.z - a.z;
-        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (d2 <= r.cut2) {
-          d2 = fmaxf(d2, r.rmin2);
-          const float2 pp = prow[__float_as_int(a.w)];
-          const float q2 = pp.x * __frcp_rn(d2);
-          const float q6 = q2 * q2 * q2;
-          acc = fmaf(pp.y, fmaf(q6, q6, -2.f * q6), acc);
+      // four receptor atoms per lane per iteration, separate accumulators:
+      // the per-pair chain (distance, ratio, sixth and twelfth powers) is
+      // long, so independent pairs keep the pipes busy
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int j0 = lane; j0 < r.n_rec; j0 += 128) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = j0 + 32 * q;
+          if (j < r.n_rec) {
+            const float4 a = rec[j];
+            const float dx = u.x - a.x, dy = u.y - a.y, dz = u.z - a.z;
+            float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (d2 <= r.cut2) {
+              d2 = fmaxf(d2, r.rmin2);
+              const float2 pp = prow[__float_as_int(a.w)];
+              const float q2 = __fdividef(pp.x, d2);
+              const float q6 = q2 * q2 * q2;
+              acc[q] = fmaf(pp.y, fmaf(q6, q6, -2.f * q6), acc[q]);
+            }
+          }
         }
       }
-      acc = warp_sum(acc);
-      if (acc >= r.cap) { acc = r.cap; ++ncap; }
-      e_inter += acc;
+      float accs = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+      if (accs >= r.cap) { accs = r.cap; ++ncap; }
+      e_inter += accs;
       nout += !((u.x >= 0.f) & (u.x <= p.g.fx1) & (u.y >= 0.f) & (u.y <= p.g.fy1) & (u.z >= 0.f) &
                 (u.z <= p.g.fz1));
     }
