@@ -138,7 +138,9 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     pred_cal = torch.empty(n_cal, dtype=torch.float32, device="cuda")
     N.ligate_surrogate_predict(sur, desc_tr[n_fit:], n_cal, pred_cal, sh)
     torch.cuda.synchronize()
-    keep_cal = T.keep_for_recall(pred_cal.cpu().numpy(), labels[n_fit:], 0.99)
+    # calibrated for 0.995 on the held-out set: its top 1% is a sample of a
+    # few hundred ligands, so the margin covers the library's sampling spread
+    keep_cal = T.keep_for_recall(pred_cal.cpu().numpy(), labels[n_fit:], 0.995)
     del desc_tr, lab, pred_cal
     tb.close()
 
@@ -193,8 +195,8 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
             "value": n / tc, "unit": "ligands/s", "ms_per_step": 1000 * tc,
             "keep_frac": round(keep_cal, 4), "docked_per_step": kc, "recall_top1pct": recc,
             "meets_target": recc >= 0.99,
-            "note": "keep fraction reaching 0.99 recall of the top 1% on the held-out 10% of the "
-                    "training library"}
+            "note": "keep fraction reaching 0.995 recall of the top 1% on the held-out 10% of the "
+                    "training library (margin for a 0.99 target)"}
     else:
         out["at_calibrated_keep"] = {"keep_frac": 1.0, "note": "calibration needs the whole library: "
                                      "triage gives no speed-up at 0.99 recall"}
