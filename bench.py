@@ -517,6 +517,24 @@ def main():
             b.synchronize()
             rms.append(a.elapsed_time(b))
         rr = rbuf.cpu().numpy().view(N.REFINED_DTYPE)
+        after = None
+        if w.pocket.receptor_xyz is not None:  # exact rescoring of the docked and of the refined poses
+            b0 = torch.empty(n_poses * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+            b1 = torch.empty_like(b0)
+            N.ligate_plan_rescore(chosen.h, b0, sh)
+            N.ligate_plan_rescore_refined(chosen.h, rbuf, b1, sh)
+            torch.cuda.synchronize()
+            r0 = b0.cpu().numpy().view(N.RESCORED_DTYPE).reshape(n_lig, K)
+            r1 = b1.cpu().numpy().view(N.RESCORED_DTYPE).reshape(n_lig, K)
+            i0, e0 = D.best_passing(r0)
+            i1, e1 = D.best_passing(r1)
+            both = (i0 >= 0) & (i1 >= 0)
+            after = {"pass_frac_docked": float(np.mean(r0["pass"] == 1)),
+                     "pass_frac_refined": float(np.mean(r1["pass"] == 1)),
+                     "ligands_with_passing_pose_docked": float(np.mean(i0 >= 0)),
+                     "ligands_with_passing_pose_refined": float(np.mean(i1 >= 0)),
+                     "mean_best_exact_energy_drop": float(np.mean(e0[both] - e1[both])) if both.any() else None}
+            del b0, b1
         live = rr["accepted"] >= 0
         drop = (rr["score_in"] - rr["score"])[np.isfinite(rr["score_in"])]
         best_before = rr["score_in"].reshape(n_lig, K).min(axis=1)
@@ -526,6 +544,7 @@ def main():
                   "poses": n_poses, "iterations": args.refine_iters, "eta0": 0.1,
                   "mean_energy_drop": float(np.mean(drop)), "improved_frac": float(np.mean(drop > 1e-6)),
                   "mean_best_drop_per_ligand": float(np.mean(best_before - best_after)),
+                  "exact_rescoring": after,
                   "form": "gradient descent over translation, rotation and torsions from the chosen "
                           "form's top-16 poses, FP32 maps, one warp per pose"}
         del rbuf, live

@@ -372,6 +372,16 @@ ligate_status ligate_rescore_poses(const ligate_pocket *pocket, const ligate_bat
 /* Every pose of the plan's last run into DEVICE out[n_ligands][top_k]
  * (same order).  Enqueues on stream. */
 ligate_status ligate_plan_rescore(const ligate_plan *plan, ligate_rescored *out, void *stream);
+/* Poses given as continuous states (see ligate_pose_state): explicit DEVICE
+ * lig_idx[n] and states[n] (synchronises), or the DEVICE records of a
+ * ligate_plan_refine run of the same plan (refined[n_ligands][top_k], their
+ * refined states; enqueues; empty slots, score_in not finite, give the
+ * empty-slot record). */
+ligate_status ligate_rescore_states(const ligate_pocket *pocket, const ligate_batch *batch,
+                                    const ligate_sampling *sampling, int n, const int32_t *lig_idx,
+                                    const ligate_pose_state *states, ligate_rescored *out, void *stream);
+ligate_status ligate_plan_rescore_refined(const ligate_plan *plan, const ligate_refined *refined,
+                                          ligate_rescored *out, void *stream);
 
 /* ------------------------------------------------------------------------
  * Per-pose selector features (paper Sec. 3.5: a high-throughput pose

@@ -80,6 +80,7 @@ def _load():
         lib.or_exhaustive.argtypes = [P, P, P, I, P, P]
         lib.or_descriptor.argtypes = [P, I, P]
         lib.or_pose_grad.argtypes = [P, P, P, I, P, P, P, P, P, P]
+        lib.or_state_coords.argtypes = [P, I, P, P]
         lib.or_refine.argtypes = [P, P, P, I, P, I, D, P, D, P, P, P, P, P, P]
         lib.or_rescore_coords.argtypes = [P, P, P, P, I, P, P, P, P, P, P]
         lib.or_pose_features.argtypes = [P, P, P, I, P, P]
@@ -302,6 +303,18 @@ def docked_state(sampling, anchors, start, tors) -> np.ndarray:
     t = np.asarray(anchors, np.float64)[a]
     phi = 2.0 * np.pi * np.asarray(tors, np.float64) / sampling.torsion_steps
     return np.concatenate([R.reshape(-1), t, phi])
+
+
+def state_coords(lig, states) -> np.ndarray:
+    """Coordinates [n, n_atoms, 3] of state rows [R (9), t (3), phi (nrot)]."""
+    lib = _load()
+    k = _Keep()
+    L = _lig(k, *lig)
+    st = _c(np.atleast_2d(states), np.float64)
+    out = np.zeros((st.shape[0], L.n_atoms, 3))
+    if lib.or_state_coords(_ref(L), st.shape[0], st.ctypes.data, out.ctypes.data):
+        raise ValueError("ligand bonds do not form a tree")
+    return out
 
 
 def pose_grad(lig, pocket, sampling, states):

@@ -724,6 +724,19 @@ static void state_out(const or_lig *L, const or_state *q, double *s) {
   for (int b = 0; b < L->nrot; ++b) s[12 + b] = q->phi[b];
 }
 
+/* Coordinates [n][n_atoms][3] of n states (rows [12 + nrot]). */
+OR_EXPORT int or_state_coords(const or_ligand_in *li, int n_states, const double *states, double *out) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  for (int p = 0; p < n_states; ++p) {
+    or_state q;
+    state_in(&L, states + (size_t)p * (12 + L.nrot), &q);
+    state_coords(&L, &q, (double(*)[3])(out + (size_t)p * L.n * 3));
+  }
+  lig_free(&L);
+  return 0;
+}
+
 /* E, generalised gradient and scales at n states.  states: [n][12 + nrot]
  * (R row-major, t, phi); g_out [n][6 + nrot]; scale_out [n][7 + nrot];
  * inert_out [n][1 + nrot]; face_out [n]. */

@@ -1033,6 +1033,8 @@ static ligate_status rec_params(const ligate_pocket *P, const ligate_batch *B, R
   }
   r.rec = P->d.rec; r.pair = P->d.rec_pair; r.n_rec = P->d.n_rec; r.n_types = P->d.rec_types;
   r.cut2 = P->d.rec_cut2; r.cap = P->d.rec_cap; r.rmin2 = P->d.rec_rmin2;
+  r.ox = (float)P->d.origin[0]; r.oy = (float)P->d.origin[1]; r.oz = (float)P->d.origin[2];
+  r.inv_h = (float)(1.0 / P->d.spacing);
   return LIGATE_OK;
 }
 
@@ -1059,7 +1061,7 @@ extern "C" ligate_status ligate_rescore_poses(const ligate_pocket *P, const liga
     st = LIGATE_ERR_UNSUPPORTED;
   }
   if (st == LIGATE_OK) {
-    e = launch_rescore(p, r, n, lig_idx, start_id, tors, nullptr, nullptr, out, (cudaStream_t)stream);
+    e = launch_rescore(p, r, n, lig_idx, start_id, tors, nullptr, nullptr, nullptr, out, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   }
   cudaFree(rot); cudaFree(anc); cudaFree(quat);
@@ -1080,9 +1082,71 @@ extern "C" ligate_status ligate_plan_rescore(const ligate_plan *pl, ligate_resco
     return LIGATE_ERR_UNSUPPORTED;
   }
   cudaError_t e = launch_rescore(pl->p, r, n, nullptr, nullptr, nullptr,
-                                 reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, out,
+                                 reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, nullptr, out,
                                  (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "plan_rescore");
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_rescore_states(const ligate_pocket *P, const ligate_batch *B,
+                                               const ligate_sampling *s, int n, const int32_t *lig_idx,
+                                               const ligate_pose_state *states, ligate_rescored *out,
+                                               void *stream) {
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  if (n < 0 || (n > 0 && (!lig_idx || !states || !out))) {
+    set_error("rescore_states: bad arrays");
+    return LIGATE_ERR_INVALID;
+  }
+  RecParams r;
+  if ((st = rec_params(P, B, r, "rescore_states")) != LIGATE_OK) return st;
+  if (n == 0) return LIGATE_OK;
+  DockParams p;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  st = base_params(P, B, s, mode, p, &rot, &anc, &quat);
+  cudaError_t e = cudaSuccess;
+  if (st == LIGATE_OK && rescore_smem_bytes(p, r, 1) > 227 * 1024) {
+    set_error("rescore_states: %d receptor atoms do not fit in shared memory", r.n_rec);
+    st = LIGATE_ERR_UNSUPPORTED;
+  }
+  if (st == LIGATE_OK) {
+    StateSrc ss;
+    ss.base = reinterpret_cast<const unsigned char *>(states);
+    ss.stride = (int)sizeof(ligate_pose_state);
+    ss.lig_offset = 0;
+    ss.score_offset = -1;
+    ss.lig_idx = lig_idx;
+    e = launch_rescore(p, r, n, nullptr, nullptr, nullptr, nullptr, nullptr, &ss, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  cudaFree(rot); cudaFree(anc); cudaFree(quat);
+  if (st != LIGATE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "rescore_states");
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_rescore_refined(const ligate_plan *pl, const ligate_refined *refined,
+                                                     ligate_rescored *out, void *stream) {
+  if (!pl || !refined || !out) { set_error("plan_rescore_refined: NULL argument"); return LIGATE_ERR_INVALID; }
+  RecParams r;
+  ligate_status st = rec_params(pl->pocket, pl->batch, r, "plan_rescore_refined");
+  if (st != LIGATE_OK) return st;
+  const int n = pl->n_ligands * pl->p.K;
+  if (n == 0) return LIGATE_OK;
+  if (rescore_smem_bytes(pl->p, r, 1) > 227 * 1024) {
+    set_error("plan_rescore_refined: %d receptor atoms do not fit in shared memory", r.n_rec);
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  StateSrc ss;
+  ss.base = reinterpret_cast<const unsigned char *>(refined);
+  ss.stride = (int)sizeof(ligate_refined);
+  ss.lig_offset = (int)offsetof(ligate_refined, ligand);
+  ss.score_offset = (int)offsetof(ligate_refined, score_in);
+  ss.lig_idx = nullptr;
+  cudaError_t e = launch_rescore(pl->p, r, n, nullptr, nullptr, nullptr, nullptr, nullptr, &ss, out,
+                                 (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plan_rescore_refined");
   return LIGATE_OK;
 }
 

@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -736,6 +737,7 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
                                                      const uint8_t *__restrict__ tors,
                                                      const PoseOut *__restrict__ poses,
                                                      const int32_t *__restrict__ row_lig,
+                                                     const StateSrc ss,
                                                      ligate_rescored *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *rec = reinterpret_cast<float4 *>(smem_raw);
@@ -751,7 +753,13 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
   for (int pi = blockIdx.x * W + warp; pi < n_poses; pi += gridDim.x * W) {
     int li, sid;
     uint32_t tt[4] = {0u, 0u, 0u, 0u};
-    if (poses) {
+    const unsigned char *st_rec = nullptr;
+    if (ss.base) {  // continuous state
+      st_rec = ss.base + (size_t)pi * ss.stride;
+      li = ss.lig_idx ? ss.lig_idx[pi] : *reinterpret_cast<const int32_t *>(st_rec + ss.lig_offset);
+      sid = (ss.score_offset >= 0 && !isfinite(*reinterpret_cast<const float *>(st_rec + ss.score_offset)))
+                ? -1 : 0;  // an empty slot of a refined plan output
+    } else if (poses) {
       const PoseOut po = poses[pi];
       li = row_lig[pi / p.K];
       sid = po.start_id;
@@ -776,7 +784,45 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
       (void)load_ligand(p, w, li, d, lane);
       cur = li;
     }
-    build_pose<MODE_F32_PLAIN>(p, w, w.pose, d, sid, tt, lane);
+    if (st_rec) {
+      // state (R, t, phi): torsions on the centred input coordinates about
+      // the current axes, then x = R y + t (A) and u = (x - origin) / h
+      const float *R = reinterpret_cast<const float *>(st_rec);
+      const float *T = R + 9, *phi = R + 12;
+      for (int i = lane; i < d.n_atoms; i += 32) w.pose[i] = w.ref[i];
+      __syncwarp();
+      for (int b = 0; b < d.n_rot; ++b) {
+        const float ang = phi[b];
+        if (ang == 0.f) continue;
+        const BondRec br = w.bonds[b];
+        float nx, ny, nz;
+        const float4 pv = w.pose[br.v];
+        bond_axis(w.pose[br.u], pv, nx, ny, nz);
+        float sn, cs;
+        sincosf(ang, &sn, &cs);
+        Rot rot;
+        rot.make(cs, sn, nx, ny, nz, pv.x, pv.y, pv.z);
+        __syncwarp();
+        for (int i = br.v + 1 + lane; i < br.end; i += 32) {
+          float4 q = w.pose[i];
+          rot.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+          w.pose[i] = q;
+        }
+        __syncwarp();
+      }
+      for (int i = lane; i < d.n_atoms; i += 32) {
+        const float4 y = w.pose[i];
+        float4 u;
+        u.x = (fmaf(R[0], y.x, fmaf(R[1], y.y, fmaf(R[2], y.z, T[0]))) - r.ox) * r.inv_h;
+        u.y = (fmaf(R[3], y.x, fmaf(R[4], y.y, fmaf(R[5], y.z, T[1]))) - r.oy) * r.inv_h;
+        u.z = (fmaf(R[6], y.x, fmaf(R[7], y.y, fmaf(R[8], y.z, T[2]))) - r.oz) * r.inv_h;
+        u.w = y.w;
+        w.pose[i] = u;
+      }
+      __syncwarp();
+    } else {
+      build_pose<MODE_F32_PLAIN>(p, w, w.pose, d, sid, tt, lane);
+    }
     float e_inter = 0.f;
     int ncap = 0, nout = 0;
     for (int i = 0; i < d.n_atoms; ++i) {
@@ -977,7 +1023,8 @@ size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps) {
 
 cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,
                            const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
-                           const int32_t *row_lig, ligate_rescored *out, cudaStream_t s) {
+                           const int32_t *row_lig, const StateSrc *states, ligate_rescored *out,
+                           cudaStream_t s) {
   if (n_poses <= 0) return cudaSuccess;
   int warps = 4;
   while (warps > 1 && rescore_smem_bytes(p, r, warps) > 227 * 1024) --warps;
@@ -991,8 +1038,11 @@ cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses,
     return e;
   const long long need = (n_poses + warps - 1) / warps;
   const int grid = (int)std::min<long long>(need, (long long)sms * std::max(occ, 1));
+  StateSrc ss;
+  memset(&ss, 0, sizeof(ss));
+  if (states) ss = *states;
   rescore_kernel<<<grid, 32 * warps, smem, s>>>(p, r, n_poses, lig_idx, start_id, tors,
-                                                reinterpret_cast<const PoseOut *>(poses), row_lig, out);
+                                                reinterpret_cast<const PoseOut *>(poses), row_lig, ss, out);
   return cudaGetLastError();
 }
 

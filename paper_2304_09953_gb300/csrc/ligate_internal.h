@@ -85,6 +85,17 @@ struct RecParams {
   const float2 *pair;
   int n_rec, n_types;
   float cut2, cap, rmin2;
+  float ox, oy, oz, inv_h;  // Angstrom -> grid units, for poses given as states
+};
+
+// Poses given as continuous states (ligate_pose_state at base + i * stride);
+// the ligand index comes from lig_idx[i] or, with lig_idx NULL, from the
+// int32 at base + i * stride + lig_offset (ligate_refined records, whose
+// float at score_offset is not finite for an empty slot; -1: no such field).
+struct StateSrc {
+  const unsigned char *base;
+  int stride, lig_offset, score_offset;
+  const int32_t *lig_idx;
 };
 
 // Map-read modes of the docking kernel.
@@ -171,7 +182,8 @@ inline void fill_step_table(int S, float *tab) {
 size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps);
 cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,
                            const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
-                           const int32_t *row_lig, ligate_rescored *out, cudaStream_t s);
+                           const int32_t *row_lig, const StateSrc *states, ligate_rescored *out,
+                           cudaStream_t s);
 
 // Per-pose selector features (dock.cu), [n_poses][256] FP32; explicit
 // poses or a plan's output as for launch_rescore.

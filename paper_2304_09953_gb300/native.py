@@ -119,6 +119,8 @@ _SIGS = {
                                                   ctypes.c_float, ctypes.c_float]),
     "ligate_rescore_poses": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_plan_rescore": (ctypes.c_int, [P, P, P]),
+    "ligate_rescore_states": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P]),
+    "ligate_plan_rescore_refined": (ctypes.c_int, [P, P, P, P]),
     "ligate_pose_features": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_plan_pose_features": (ctypes.c_int, [P, P, P]),
 }
@@ -345,6 +347,16 @@ def ligate_pose_features(pocket, batch, sampling_struct, n, lig_idx, start_id, t
 
 def ligate_plan_pose_features(plan, out, stream=None):
     check(load().ligate_plan_pose_features(plan, _ptr(out), stream), "ligate_plan_pose_features")
+
+
+def ligate_rescore_states(pocket, batch, sampling_struct, n, lig_idx, states, out, stream=None):
+    check(load().ligate_rescore_states(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
+                                       _ptr(states), _ptr(out), stream), "ligate_rescore_states")
+
+
+def ligate_plan_rescore_refined(plan, refined, out, stream=None):
+    check(load().ligate_plan_rescore_refined(plan, _ptr(refined), _ptr(out), stream),
+          "ligate_plan_rescore_refined")
 
 
 def ligate_autotune(pocket, batch, sampling_struct, budget_ms=20000.0):

@@ -202,3 +202,50 @@ def test_learned_selector_beats_docking_rank(workload_factory):
           % (pass_sel, pass_r0, top_sel, top_r0))
     assert pass_sel >= pass_r0 + 0.03
     assert top_sel >= top_r0
+
+
+def test_rescore_states_matches_oracle_and_refined_plan_path(batched_small):
+    """Continuous states: seeded states vs the oracle; and the refined records
+    of a plan rescore exactly as their states do through the explicit path."""
+    from tests.test_gpu_refine import seeded_states, to_dev
+    w = batched_small
+    rng = np.random.default_rng(17)
+    lig, rec, st64 = seeded_states(w, np.arange(w.ligands.n), rng, 4, spread=1.0)
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    s = N.make_sampling(w.sampling)
+    n = len(lig)
+    out = torch.zeros(n * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_rescore_states(ph.h, bh.h, s, n, torch.from_numpy(lig).cuda(), to_dev(rec), out)
+    r = out.cpu().numpy().view(N.RESCORED_DTYPE)
+    same = 0
+    for li in np.unique(lig):
+        sel = np.nonzero(lig == li)[0]
+        L = w.ligands.ligand(li)
+        x = oracle.state_coords(L, np.array([st64[k] for k in sel]))
+        o = oracle.rescore_coords(L, w.pocket, w.sampling, w.pocket.receptor(), x)
+        for m, k in enumerate(sel):
+            tol = 1e-4 * max(o["scale"][m], 1.0)
+            assert abs(r[k]["e_inter"] - o["e_inter"][m]) <= tol
+            assert abs(r[k]["e_clash"] - o["e_clash"][m]) <= tol
+            same += r[k]["n_outside"] == o["n_outside"][m] and r[k]["n_capped"] == o["n_capped"][m]
+    assert same >= 0.98 * n
+    # refined plan records vs their states through the explicit path
+    pl = D.Plan(ph, bh, w.sampling, mode="bf16")
+    pl.run()
+    K = w.sampling.top_k
+    rbuf = torch.empty(w.ligands.n * K * N.REFINED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_plan_refine(pl.h, 16, 0.1, rbuf)
+    a = torch.empty(w.ligands.n * K * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_plan_rescore_refined(pl.h, rbuf, a)
+    torch.cuda.synchronize()
+    refined = rbuf.cpu().numpy().view(N.REFINED_DTYPE)
+    via_plan = a.cpu().numpy().view(N.RESCORED_DTYPE)
+    live = np.isfinite(refined["score_in"])
+    st = np.ascontiguousarray(refined["state"][live])
+    b = torch.empty(int(live.sum()) * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_rescore_states(ph.h, bh.h, pl.s, int(live.sum()),
+                           torch.from_numpy(refined["ligand"][live].astype(np.int32)).cuda(), to_dev(st), b)
+    np.testing.assert_array_equal(via_plan[live], b.cpu().numpy().view(N.RESCORED_DTYPE))
+    assert np.all(np.isinf(via_plan[~live]["energy"]))
+    pl.close()

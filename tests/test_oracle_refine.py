@@ -182,3 +182,16 @@ def test_docked_state_reproduces_the_docking_score(tiny):
     e = oracle.pose_grad(lig, w.pocket, w.sampling, st)[0]
     want = oracle.score_poses(lig, w.pocket, w.sampling, starts, tors)
     np.testing.assert_allclose(e, want, rtol=1e-12, atol=1e-12)
+
+
+def test_state_coords_of_a_docked_state_are_the_docked_pose(tiny):
+    w = tiny
+    lig = w.ligands.ligand(0)
+    R_n = int(np.sum(lig[3] != 0))
+    rng = np.random.default_rng(12)
+    starts = rng.integers(0, w.sampling.n_starts, size=5)
+    tors = rng.integers(0, w.sampling.torsion_steps, size=(5, R_n))
+    st = np.array([oracle.docked_state(w.sampling, w.pocket.anchors, s, t) for s, t in zip(starts, tors)])
+    np.testing.assert_allclose(oracle.state_coords(lig, st),
+                               oracle.pose_coords(lig, w.pocket.anchors, w.sampling, starts, tors),
+                               rtol=0, atol=1e-12)
