@@ -39,7 +39,7 @@ WORKLOAD = ("batched: 10000 ligands (N~U{15..60}, R~U{0..12}), 8x64^3 maps @0.37
 WORKLOADS = {"batched": WORKLOAD,
              "combined": ("combined: 1000000 ligands (N log-uniform {10..80}, R~U{0..15}), "
                           "8x96^3 maps @0.375 A, 256 orient x 32 anchors x S=16, top-16")}
-# FP32 operations (FMA = 2) per unit of executed work, see the design doc:
+# FP32 operations (FMA = 2) per unit of executed work:
 #   atom interpolation: 9 FMA rotation + 3 fraction subs + 7 lerps (sub + FMA) + 1 add = 43
 #   clash candidate test (once per bond): 2 subs + mul + FMA against the circle bound = 5
 #   surviving pair set-up (once per bond): P, Q, D0 and the scaled coefficients = 33

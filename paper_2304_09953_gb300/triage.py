@@ -1,6 +1,6 @@
 """Host-side triage bookkeeping (paper Sec. 3.5: a learned predictor ranks
 the library so that only its top fraction is docked; full docking stays the
-judge of recall).
+arbiter of recall).
 
 Scores are docking scores (lower = better).  The true top set is the
 ceil(n * top_frac) ligands with the lowest full-docking score (ties: smaller

@@ -8,7 +8,7 @@ order.  |E_gpu - E_64| <= 1e-4 * max(sum |terms|, 1).
 
 The search is greedy, so FP32 and FP64 may pick different torsion steps
 where two trials score within rounding of each other; after such a step the
-two paths continue from different poses.  The rules therefore judge the GPU
+two paths continue from different poses.  The rules therefore check the GPU
 along its own choice path:
   * path check: for a GPU pose (start, tors), at every bond the GPU's step
     scores (FP64, other bonds as the GPU had them) within tolerance of the
