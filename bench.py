@@ -57,15 +57,21 @@ def executed_flops(work, S):
 
 # DRAM bytes (read + write) of one full-size launch of the chosen-form kernel,
 # from ncu (profiles/dock_kernel_bf16_batched10k.md), valid only for the
-# kernel source it was captured on (sha1 prefix of csrc/dock.cu).
+# kernel source it was captured on (kernel_source_sha).
 TRAFFIC_BYTES = {("30881babca3d", "batched", 10000): 73092352 + 10049792}
 
 
-def kernel_traffic(workload, n_ligands):
+def kernel_source_sha():
+    """sha1 prefix of the docking kernel's sources (dock.cu + dock_device.cuh)."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2304_09953_gb300", "csrc", "dock.cu")
-    sha = hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
-    return TRAFFIC_BYTES.get((sha, workload, n_ligands))
+    h = hashlib.sha1()
+    for f in ("dock.cu", "dock_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2304_09953_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def kernel_traffic(workload, n_ligands):
+    return TRAFFIC_BYTES.get((kernel_source_sha(), workload, n_ligands))
 
 
 def fp32_peak_tflops(sms=152, lanes=128, mhz=2070.0):

@@ -1,0 +1,316 @@
+// Device building blocks shared by the docking kernel (dock.cu) and the
+// rescoring and pose-feature kernels (rescore.cu): trilinear map reads in
+// every layout, rotations about a bond, the warp-distributed top-K list,
+// the per-warp shared-memory slot, ligand loading, start frames and the
+// construction and full scoring of a pose (paper Sec. 2: rigid start x
+// torsion steps, geometric score = grid terms + intramolecular clash).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "ligate_internal.h"
+
+namespace ligate {
+
+constexpr unsigned FULL = 0xffffffffu;  // full-warp mask
+constexpr int EMPTY_SID = 0x7fffffff;   // start id of an empty top-K slot
+
+// ---------------------------------------------------------------------------
+// Trilinear interpolation at grid coordinates (ux, uy, uz) of the map whose
+// first element (plain) or cell (corner layouts) is at `toff`.  Outside
+// [0, n-1] on any axis the atom scores the penalty.  Cell = min(floor, n-2),
+// then successive linear interpolation along x, y, z.
+template <int MODE>
+__device__ __forceinline__ float grid_eval(const void *__restrict__ maps, int toff, float ux,
+                                           float uy, float uz, const GridConst &g) {
+  if (!((ux >= 0.f) & (ux <= g.fx1) & (uy >= 0.f) & (uy <= g.fy1) & (uz >= 0.f) &
+        (uz <= g.fz1)))
+    return g.penalty;
+  const int ix = min((int)ux, g.nx - 2), iy = min((int)uy, g.ny - 2), iz = min((int)uz, g.nz - 2);
+  const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+  float v0, v1, v2, v3, v4, v5, v6, v7;
+  if (MODE == MODE_F32_PLAIN) {
+    const float *m = (const float *)maps + toff + (iz * g.ny + iy) * g.nx + ix;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    v0 = __ldg(m); v1 = __ldg(m + 1); v2 = __ldg(m + sy); v3 = __ldg(m + sy + 1);
+    v4 = __ldg(m + sz); v5 = __ldg(m + sz + 1); v6 = __ldg(m + sz + sy); v7 = __ldg(m + sz + sy + 1);
+  } else {
+    const int cell = toff + (iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;  // < 2^28: host limit
+    if (MODE == MODE_F32_CORNER) {
+      const float4 *m = (const float4 *)maps + 2 * cell;
+      const float4 a = __ldg(m), b = __ldg(m + 1);
+      v0 = a.x; v1 = a.y; v2 = a.z; v3 = a.w; v4 = b.x; v5 = b.y; v6 = b.z; v7 = b.w;
+    } else {
+      const uint4 w = __ldg((const uint4 *)maps + cell);
+      if (MODE == MODE_BF16_CORNER) {
+        v0 = __uint_as_float(w.x << 16); v1 = __uint_as_float(w.x & 0xffff0000u);
+        v2 = __uint_as_float(w.y << 16); v3 = __uint_as_float(w.y & 0xffff0000u);
+        v4 = __uint_as_float(w.z << 16); v5 = __uint_as_float(w.z & 0xffff0000u);
+        v6 = __uint_as_float(w.w << 16); v7 = __uint_as_float(w.w & 0xffff0000u);
+      } else {
+        float2 f;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.x)); v0 = f.x; v1 = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.y)); v2 = f.x; v3 = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.z)); v4 = f.x; v5 = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.w)); v6 = f.x; v7 = f.y;
+      }
+    }
+  }
+  const float y0z0 = fmaf(fx, v1 - v0, v0);
+  const float y1z0 = fmaf(fx, v3 - v2, v2);
+  const float y0z1 = fmaf(fx, v5 - v4, v4);
+  const float y1z1 = fmaf(fx, v7 - v6, v6);
+  const float z0 = fmaf(fy, y1z0 - y0z0, y0z0);
+  const float z1 = fmaf(fy, y1z1 - y0z1, y0z1);
+  return fmaf(fz, z1 - z0, z0);
+}
+
+// Element stride of one atom type's map in a given mode (plain: nodes;
+// corner: cells).
+__host__ __device__ inline int type_stride(int mode, const GridConst &g) {
+  return mode == MODE_F32_PLAIN ? g.nx * g.ny * g.nz : (g.nx - 1) * (g.ny - 1) * (g.nz - 1);
+}
+
+// Rotation by angle (c = cos, s = sin) about unit axis n through point p:
+// y = R x + t, with R = c I + s [n]x + (1 - c) n n^T and t = p - R p.
+struct Rot {
+  float r00, r01, r02, r10, r11, r12, r20, r21, r22, tx, ty, tz;
+  __device__ __forceinline__ void make(float c, float s, float nx, float ny, float nz, float px,
+                                       float py, float pz) {
+    const float o = 1.f - c;
+    r00 = fmaf(o * nx, nx, c);       r01 = fmaf(o * nx, ny, -s * nz); r02 = fmaf(o * nx, nz, s * ny);
+    r10 = fmaf(o * ny, nx, s * nz);  r11 = fmaf(o * ny, ny, c);       r12 = fmaf(o * ny, nz, -s * nx);
+    r20 = fmaf(o * nz, nx, -s * ny); r21 = fmaf(o * nz, ny, s * nx);  r22 = fmaf(o * nz, nz, c);
+    tx = px - fmaf(r00, px, fmaf(r01, py, r02 * pz));
+    ty = py - fmaf(r10, px, fmaf(r11, py, r12 * pz));
+    tz = pz - fmaf(r20, px, fmaf(r21, py, r22 * pz));
+  }
+  __device__ __forceinline__ void apply(float x, float y, float z, float &ox, float &oy,
+                                        float &oz) const {
+    ox = fmaf(r00, x, fmaf(r01, y, fmaf(r02, z, tx)));
+    oy = fmaf(r10, x, fmaf(r11, y, fmaf(r12, z, ty)));
+    oz = fmaf(r20, x, fmaf(r21, y, fmaf(r22, z, tz)));
+  }
+};
+
+// Unit axis from atom u to atom v of a pose.
+__device__ __forceinline__ void bond_axis(const float4 &pu, const float4 &pv, float &nx, float &ny,
+                                          float &nz) {
+  nx = pv.x - pu.x; ny = pv.y - pu.y; nz = pv.z - pu.z;
+  const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+  nx *= inv; ny *= inv; nz *= inv;
+}
+
+// (E, s) lexicographic order; an empty slot is (+inf, EMPTY_SID).
+__device__ __forceinline__ bool pose_less(float e1, int s1, float e2, int s2) {
+  return e1 < e2 || (e1 == e2 && s1 < s2);
+}
+
+// Warp-distributed sorted top-K list: lane j < K holds entry j.
+struct TopK {
+  float e;
+  int s;
+  uint32_t t0, t1, t2, t3;
+  __device__ __forceinline__ void clear() {
+    e = __int_as_float(0x7f800000); s = EMPTY_SID; t0 = t1 = t2 = t3 = 0;
+  }
+  // Insert a warp-uniform candidate (all lanes pass the same values).
+  __device__ __forceinline__ void insert(float ce, int cs, uint32_t c0, uint32_t c1, uint32_t c2,
+                                         uint32_t c3, int K, int lane) {
+    const float ke = __shfl_sync(FULL, e, K - 1);
+    const int ks = __shfl_sync(FULL, s, K - 1);
+    if (!pose_less(ce, cs, ke, ks)) return;  // warp-uniform
+    const bool before = lane < K && pose_less(e, s, ce, cs);
+    const int pos = __popc(__ballot_sync(FULL, before));
+    const float ue = __shfl_up_sync(FULL, e, 1);
+    const int us = __shfl_up_sync(FULL, s, 1);
+    const uint32_t u0 = __shfl_up_sync(FULL, t0, 1), u1 = __shfl_up_sync(FULL, t1, 1),
+                   u2 = __shfl_up_sync(FULL, t2, 1), u3 = __shfl_up_sync(FULL, t3, 1);
+    if (lane > pos && lane < K) { e = ue; s = us; t0 = u0; t1 = u1; t2 = u2; t3 = u3; }
+    if (lane == pos) { e = ce; s = cs; t0 = c0; t1 = c1; t2 = c2; t3 = c3; }
+  }
+};
+
+// Per-warp shared-memory slot.
+struct WarpSmem {
+  float4 *ref;     // [nmax]  (x - c, y - c, z - c) Angstrom, .w = atom type (int bits)
+  float4 *pose;    // [G][nmax + 1] current pose, grid units, .w = map offset (int bits)
+  float4 *list;    // [PAIR_WARP] clash pairs that survive the circle bound of a bond
+  float2 *cab;     // [G][nmax] (axial coordinate, radial distance) about the bond axis
+  BondRec *bonds;  // [LIGATE_MAX_ROT]
+  float *memo;     // [memo_floats(S)] clash sums of the first bonds' sweeps
+};
+
+// Surviving clash pairs buffered per warp before they are evaluated for
+// every torsion step: 192 entries, 192 / G = 6 L per start group (the
+// buffer is flushed whenever a group may overflow).
+constexpr int PAIR_WARP = 192;
+
+// The clash term of a bond's sweep depends only on the ligand's internal
+// conformation, which before bond b is set by the steps chosen at bonds
+// 0 .. b-1.  Bond 0 therefore sweeps the same conformation for every start
+// and bond 1 one of S conformations: their clash sums are computed once per
+// ligand (S values for bond 0, S x S for bond 1 when S <= 16) and looked up
+// by every start.
+__host__ __device__ inline int memo_bonds(int S) { return S <= 16 ? 2 : 1; }
+__host__ __device__ inline int memo_floats(int S) {
+  return S <= 0 ? 0 : (S + (memo_bonds(S) == 2 ? S * S : 0) + 3) / 4 * 4;
+}
+
+__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int S, int G) {
+  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
+         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)memo_floats(S) * 4;
+}
+
+
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int G) {
+  WarpSmem w;
+  w.ref = reinterpret_cast<float4 *>(base);
+  w.pose = w.ref + nmax;
+  w.list = w.pose + (size_t)G * (nmax + 1);
+  w.cab = reinterpret_cast<float2 *>(w.list + PAIR_WARP);
+  w.bonds = reinterpret_cast<BondRec *>(w.cab + (size_t)G * nmax);
+  w.memo = reinterpret_cast<float *>(w.bonds + LIGATE_MAX_ROT);
+  return w;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Load ligand `li` into the warp's slot: reference coordinates centred on
+// their centroid, bond table, clash masks.  Returns the clash sum (without
+// the weight) of the input conformation, which every pose shares up to the
+// torsion-dependent part.
+__device__ inline float load_ligand(const DockParams &p, const WarpSmem &w, int li, LigDesc &d,
+                             int lane) {
+  d = p.lig[li];
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 a = __ldg(p.atoms + d.atom_base + i);
+    w.ref[i] = a;
+    sx += a.x; sy += a.y; sz += a.z;
+  }
+  sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+  const float inv_n = 1.f / (float)d.n_atoms;
+  const float cx = sx * inv_n, cy = sy * inv_n, cz = sz * inv_n;
+  __syncwarp();
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    float4 a = w.ref[i];
+    a.x -= cx; a.y -= cy; a.z -= cz;
+    w.ref[i] = a;
+  }
+  for (int b = lane; b < d.n_rot; b += 32) w.bonds[b] = p.bonds[d.bond_base + b];
+  __syncwarp();
+  float cl = 0.f;
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 xi = w.ref[i];
+    for (int wd = 0; wd < d.n_words; ++wd) {
+      uint32_t m = __ldg(p.elig + d.elig_base + i * d.n_words + wd);
+      const int lo = i + 1 - 32 * wd;  // keep only j > i
+      if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
+      while (m) {
+        const int j = 32 * wd + __ffs(m) - 1;
+        m &= m - 1;
+        const float4 xj = w.ref[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_ang, 1.f));
+        cl = fmaf(t, t, cl);
+      }
+    }
+  }
+  return warp_sum(cl);
+}
+
+// Rigid start frame: rows of R_o / h and (anchor - origin) / h.
+__device__ __forceinline__ void start_frame(const DockParams &p, int sid, float (&R)[9],
+                                            float (&T)[3]) {
+  const int o = sid / p.n_anchor, a = sid - o * p.n_anchor;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) R[q] = __ldg(p.rot + 9 * o + q);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) T[q] = __ldg(p.anc + 3 * a + q);
+}
+
+// cos/sin of 2 pi k / S from the run's table (FP64 on the host, rounded).
+__device__ __forceinline__ void step_cs(const DockParams &p, int k, float &c, float &s) {
+  c = p.cs_tab[2 * k];
+  s = p.cs_tab[2 * k + 1];
+}
+
+// Coordinates (grid units, .w = map offset of the atom's type for map
+// layout MODE) of pose (sid, tors) of the loaded ligand into buf:
+// rigid start frame, then each bond's step about its current axis.
+// Warp-cooperative.
+template <int MODE>
+__device__ void build_pose(const DockParams &p, const WarpSmem &w, float4 *buf, const LigDesc &d, int sid,
+                           const uint32_t (&tors)[4], int lane) {
+  float R[9], T[3];
+  start_frame(p, sid, R, T);
+  const int ts = type_stride(MODE, p.g);
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 r = w.ref[i];
+    float4 u;
+    u.x = fmaf(R[0], r.x, fmaf(R[1], r.y, fmaf(R[2], r.z, T[0])));
+    u.y = fmaf(R[3], r.x, fmaf(R[4], r.y, fmaf(R[5], r.z, T[1])));
+    u.z = fmaf(R[6], r.x, fmaf(R[7], r.y, fmaf(R[8], r.z, T[2])));
+    u.w = __int_as_float(__float_as_int(r.w) * ts);
+    buf[i] = u;
+  }
+  __syncwarp();
+  for (int b = 0; b < d.n_rot; ++b) {
+    const int kb = (tors[b >> 2] >> (8 * (b & 3))) & 0xff;
+    if (kb % p.S == 0) continue;
+    const BondRec br = w.bonds[b];
+    float nx, ny, nz;
+    const float4 pv = buf[br.v];
+    bond_axis(buf[br.u], pv, nx, ny, nz);
+    float c, s;
+    step_cs(p, kb % p.S, c, s);
+    Rot rot;
+    rot.make(c, s, nx, ny, nz, pv.x, pv.y, pv.z);
+    __syncwarp();
+    for (int i = br.v + 1 + lane; i < br.end; i += 32) {
+      float4 q = buf[i];
+      rot.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+      buf[i] = q;
+    }
+    __syncwarp();
+  }
+}
+
+// Full FP32 score of pose (sid, tors) of the loaded ligand, warp-cooperative,
+// using the map `maps` read in mode MODE (scratch: pose slot `buf`).
+template <int MODE>
+__device__ float full_score(const DockParams &p, const void *maps, const WarpSmem &w, float4 *buf,
+                            const LigDesc &d, int sid, const uint32_t (&tors)[4], int lane) {
+  build_pose<MODE>(p, w, buf, d, sid, tors, lane);
+  float e = 0.f, cl = 0.f;
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 xi = buf[i];
+    e += grid_eval<MODE>(maps, __float_as_int(xi.w), xi.x, xi.y, xi.z, p.g);
+    for (int wd = 0; wd < d.n_words; ++wd) {
+      uint32_t m = __ldg(p.elig + d.elig_base + i * d.n_words + wd);
+      const int lo = i + 1 - 32 * wd;
+      if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
+      while (m) {
+        const int j = 32 * wd + __ffs(m) - 1;
+        m &= m - 1;
+        const float4 xj = buf[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_grid, 1.f));
+        cl = fmaf(t, t, cl);
+      }
+    }
+  }
+  e = warp_sum(e);
+  cl = warp_sum(cl);
+  __syncwarp();
+  return fmaf(p.clash_w, cl, e);
+}
+
+}  // namespace ligate

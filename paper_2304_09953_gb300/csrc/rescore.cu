@@ -1,0 +1,339 @@
+// Exact rescoring, pose filter and per-pose selector features (paper
+// Sec. 2: a more accurate scoring of the generated poses and a filter;
+// Sec. 3.5: a high-throughput pose selector).  Poses come from explicit
+// (ligand, start, torsion steps) arrays, from a plan's output, or as
+// continuous states (refined poses).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "dock_device.cuh"
+
+namespace ligate {
+
+// ---------------------------------------------------------------------------
+// Exact rescoring and filter of explicit or planned poses (paper Sec. 2: a
+// more accurate scoring of the generated poses, then a filter).  The
+// receptor term is the maps' pair potential evaluated at each atom:
+// min(cap, sum_j eps_tj ((r0/r)^12 - 2 (r0/r)^6)) over receptor atoms within
+// the cutoff, r floored at rmin (grid units throughout); the clash term is
+// the docking score's.  The CTA stages all receptor atoms in shared memory;
+// each warp takes poses, builds the pose, and for every ligand atom its
+// lanes split the receptor atoms (conflict-free consecutive reads).
+__global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const RecParams r, int n_poses,
+                                                     const int32_t *__restrict__ lig_idx,
+                                                     const int32_t *__restrict__ start_id,
+                                                     const uint8_t *__restrict__ tors,
+                                                     const PoseOut *__restrict__ poses,
+                                                     const int32_t *__restrict__ row_lig,
+                                                     const StateSrc ss,
+                                                     ligate_rescored *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *rec = reinterpret_cast<float4 *>(smem_raw);
+  float2 *pair = reinterpret_cast<float2 *>(rec + r.n_rec);
+  unsigned char *slots = reinterpret_cast<unsigned char *>(pair + ((r.n_types * r.n_types + 1) & ~1));
+  for (int j = threadIdx.x; j < r.n_rec; j += blockDim.x) rec[j] = r.rec[j];
+  for (int j = threadIdx.x; j < r.n_types * r.n_types; j += blockDim.x) pair[j] = r.pair[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const WarpSmem w = warp_smem(slots + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1), p.nmax, 1);
+  int cur = -1;
+  LigDesc d;
+  for (int pi = blockIdx.x * W + warp; pi < n_poses; pi += gridDim.x * W) {
+    int li, sid;
+    uint32_t tt[4] = {0u, 0u, 0u, 0u};
+    const unsigned char *st_rec = nullptr;
+    if (ss.base) {  // continuous state
+      st_rec = ss.base + (size_t)pi * ss.stride;
+      li = ss.lig_idx ? ss.lig_idx[pi] : *reinterpret_cast<const int32_t *>(st_rec + ss.lig_offset);
+      sid = (ss.score_offset >= 0 && !isfinite(*reinterpret_cast<const float *>(st_rec + ss.score_offset)))
+                ? -1 : 0;  // an empty slot of a refined plan output
+    } else if (poses) {
+      const PoseOut po = poses[pi];
+      li = row_lig[pi / p.K];
+      sid = po.start_id;
+      for (int q = 0; q < 4; ++q) tt[q] = po.tors[q];
+    } else {
+      li = lig_idx[pi];
+      sid = start_id[pi];
+      for (int q = 0; q < 16; ++q) tt[q >> 2] |= (uint32_t)tors[(size_t)pi * 16 + q] << (8 * (q & 3));
+    }
+    if (li < 0 || li >= p.n_ligands || sid < 0 || sid >= p.n_starts) {  // empty slot or bad index
+      if (lane == 0) {
+        ligate_rescored o;
+        o.energy = o.e_inter = o.e_clash = __int_as_float(0x7f800000);
+        o.n_outside = o.n_capped = -1;
+        o.pass = 0;
+        out[pi] = o;
+      }
+      continue;
+    }
+    if (li != cur) {
+      __syncwarp();
+      (void)load_ligand(p, w, li, d, lane);
+      cur = li;
+    }
+    if (st_rec) {
+      // state (R, t, phi): torsions on the centred input coordinates about
+      // the current axes, then x = R y + t (A) and u = (x - origin) / h
+      const float *R = reinterpret_cast<const float *>(st_rec);
+      const float *T = R + 9, *phi = R + 12;
+      for (int i = lane; i < d.n_atoms; i += 32) w.pose[i] = w.ref[i];
+      __syncwarp();
+      for (int b = 0; b < d.n_rot; ++b) {
+        const float ang = phi[b];
+        if (ang == 0.f) continue;
+        const BondRec br = w.bonds[b];
+        float nx, ny, nz;
+        const float4 pv = w.pose[br.v];
+        bond_axis(w.pose[br.u], pv, nx, ny, nz);
+        float sn, cs;
+        sincosf(ang, &sn, &cs);
+        Rot rot;
+        rot.make(cs, sn, nx, ny, nz, pv.x, pv.y, pv.z);
+        __syncwarp();
+        for (int i = br.v + 1 + lane; i < br.end; i += 32) {
+          float4 q = w.pose[i];
+          rot.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+          w.pose[i] = q;
+        }
+        __syncwarp();
+      }
+      for (int i = lane; i < d.n_atoms; i += 32) {
+        const float4 y = w.pose[i];
+        float4 u;
+        u.x = (fmaf(R[0], y.x, fmaf(R[1], y.y, fmaf(R[2], y.z, T[0]))) - r.ox) * r.inv_h;
+        u.y = (fmaf(R[3], y.x, fmaf(R[4], y.y, fmaf(R[5], y.z, T[1]))) - r.oy) * r.inv_h;
+        u.z = (fmaf(R[6], y.x, fmaf(R[7], y.y, fmaf(R[8], y.z, T[2]))) - r.oz) * r.inv_h;
+        u.w = y.w;
+        w.pose[i] = u;
+      }
+      __syncwarp();
+    } else {
+      build_pose<MODE_F32_PLAIN>(p, w, w.pose, d, sid, tt, lane);
+    }
+    float e_inter = 0.f;
+    int ncap = 0, nout = 0;
+    for (int i = 0; i < d.n_atoms; ++i) {
+      const float4 u = w.pose[i];
+      const int t = __float_as_int(w.ref[i].w);
+      const float2 *prow = pair + t * r.n_types;
+      // four receptor atoms per lane per iteration, separate accumulators:
+      // the per-pair chain (distance, ratio, sixth and twelfth powers) is
+      // long, so independent pairs keep the pipes busy
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int j0 = lane; j0 < r.n_rec; j0 += 128) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = j0 + 32 * q;
+          if (j < r.n_rec) {
+            const float4 a = rec[j];
+            const float dx = u.x - a.x, dy = u.y - a.y, dz = u.z - a.z;
+            float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (d2 <= r.cut2) {
+              d2 = fmaxf(d2, r.rmin2);
+              const float2 pp = prow[__float_as_int(a.w)];
+              const float q2 = __fdividef(pp.x, d2);
+              const float q6 = q2 * q2 * q2;
+              acc[q] = fmaf(pp.y, fmaf(q6, q6, -2.f * q6), acc[q]);
+            }
+          }
+        }
+      }
+      float accs = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+      if (accs >= r.cap) { accs = r.cap; ++ncap; }
+      e_inter += accs;
+      nout += !((u.x >= 0.f) & (u.x <= p.g.fx1) & (u.y >= 0.f) & (u.y <= p.g.fy1) & (u.z >= 0.f) &
+                (u.z <= p.g.fz1));
+    }
+    float cl = 0.f;
+    for (int i = lane; i < d.n_atoms; i += 32) {
+      const float4 xi = w.pose[i];
+      for (int wd = 0; wd < d.n_words; ++wd) {
+        uint32_t m = __ldg(p.elig + d.elig_base + i * d.n_words + wd);
+        const int lo = i + 1 - 32 * wd;
+        if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
+        while (m) {
+          const int j = 32 * wd + __ffs(m) - 1;
+          m &= m - 1;
+          const float4 xj = w.pose[j];
+          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+          const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_grid, 1.f));
+          cl = fmaf(t, t, cl);
+        }
+      }
+    }
+    cl = p.clash_w * warp_sum(cl);
+    if (lane == 0) {
+      ligate_rescored o;
+      o.e_inter = e_inter;
+      o.e_clash = cl;
+      o.energy = e_inter + cl;
+      o.n_outside = nout;
+      o.n_capped = ncap;
+      o.pass = (nout == 0 && ncap == 0) ? 1 : 0;
+      out[pi] = o;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-pose selector features (paper Sec. 3.5: a high-throughput pose
+// selector).  Per pose 256 FP32: [0, 64) log1p of the counts of atoms whose
+// FP32 grid value v falls in bin min(63, max(0, floor((v + 4) * 4)));
+// [64, 72) mean v per atom type 0..7; [72] docking score / atoms; [73] clash
+// term; [74] log1p(atoms); [75] rotatable bonds; [76] log1p(count of
+// v >= 9); rest 0.  One warp per pose; the histogram lives in the warp's
+// pair-list slot.  An empty or invalid pose gives all zeros.
+__global__ void __launch_bounds__(128) pose_features_kernel(const DockParams p, int n_poses,
+                                                           const int32_t *__restrict__ lig_idx,
+                                                           const int32_t *__restrict__ start_id,
+                                                           const uint8_t *__restrict__ tors,
+                                                           const PoseOut *__restrict__ poses,
+                                                           const int32_t *__restrict__ row_lig,
+                                                           float *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1), p.nmax, 1);
+  int *hist = reinterpret_cast<int *>(w.list);
+  int cur = -1;
+  LigDesc d;
+  for (int pi = blockIdx.x * W + warp; pi < n_poses; pi += gridDim.x * W) {
+    float *f = out + (size_t)pi * 256;
+    int li, sid;
+    uint32_t tt[4] = {0u, 0u, 0u, 0u};
+    if (poses) {
+      const PoseOut po = poses[pi];
+      li = row_lig[pi / p.K];
+      sid = po.start_id;
+      for (int q = 0; q < 4; ++q) tt[q] = po.tors[q];
+    } else {
+      li = lig_idx[pi];
+      sid = start_id[pi];
+      for (int q = 0; q < 16; ++q) tt[q >> 2] |= (uint32_t)tors[(size_t)pi * 16 + q] << (8 * (q & 3));
+    }
+    if (li < 0 || li >= p.n_ligands || sid < 0 || sid >= p.n_starts) {
+      for (int k = lane; k < 256; k += 32) f[k] = 0.f;
+      continue;
+    }
+    if (li != cur) {
+      __syncwarp();
+      (void)load_ligand(p, w, li, d, lane);
+      cur = li;
+    }
+    build_pose<MODE_F32_PLAIN>(p, w, w.pose, d, sid, tt, lane);
+    for (int b = lane; b < 64; b += 32) hist[b] = 0;
+    __syncwarp();
+    float e = 0.f, high = 0.f, ts[8], tn[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) { ts[t] = 0.f; tn[t] = 0.f; }
+    for (int i = lane; i < d.n_atoms; i += 32) {
+      const float4 u = w.pose[i];
+      const float v = grid_eval<MODE_F32_PLAIN>(p.maps_f32, __float_as_int(u.w), u.x, u.y, u.z, p.g);
+      e += v;
+      int b = (int)floorf((v + 4.f) * 4.f);
+      b = min(63, max(0, b));
+      atomicAdd(&hist[b], 1);
+      const int ty = __float_as_int(w.ref[i].w);
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t == ty) { ts[t] += v; tn[t] += 1.f; }
+      high += v >= 9.f ? 1.f : 0.f;
+    }
+    float cl = 0.f;
+    for (int i = lane; i < d.n_atoms; i += 32) {
+      const float4 xi = w.pose[i];
+      for (int wd = 0; wd < d.n_words; ++wd) {
+        uint32_t m = __ldg(p.elig + d.elig_base + i * d.n_words + wd);
+        const int lo = i + 1 - 32 * wd;
+        if (lo >= 32) m = 0; else if (lo > 0) m &= ~0u << lo;
+        while (m) {
+          const int j = 32 * wd + __ffs(m) - 1;
+          m &= m - 1;
+          const float4 xj = w.pose[j];
+          const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+          const float t = fmaxf(0.f, fmaf(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)), p.inv_dc2_grid, 1.f));
+          cl = fmaf(t, t, cl);
+        }
+      }
+    }
+    e = warp_sum(e);
+    cl = p.clash_w * warp_sum(cl);
+    high = warp_sum(high);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) { ts[t] = warp_sum(ts[t]); tn[t] = warp_sum(tn[t]); }
+    __syncwarp();
+    for (int b = lane; b < 64; b += 32) f[b] = log1pf((float)hist[b]);
+    if (lane < 8) {
+      float m = 0.f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t == lane) m = tn[t] > 0.f ? ts[t] / tn[t] : 0.f;
+      f[64 + lane] = m;
+    }
+    if (lane == 0) {
+      f[72] = (e + cl) / (float)d.n_atoms;
+      f[73] = cl;
+      f[74] = log1pf((float)d.n_atoms);
+      f[75] = (float)d.n_rot;
+      f[76] = log1pf(high);
+    }
+    for (int k = 77 + lane; k < 256; k += 32) f[k] = 0.f;
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t *lig_idx,
+                                 const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
+                                 const int32_t *row_lig, float *out, cudaStream_t s) {
+  if (n_poses <= 0) return cudaSuccess;
+  const int warps = 4;
+  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(pose_features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pose_features_kernel, 32 * warps, smem)))
+    return e;
+  const long long need = (n_poses + warps - 1) / warps;
+  const int grid = (int)std::min<long long>(need, (long long)sms * std::max(occ, 1));
+  pose_features_kernel<<<grid, 32 * warps, smem, s>>>(p, n_poses, lig_idx, start_id, tors,
+                                                      reinterpret_cast<const PoseOut *>(poses), row_lig, out);
+  return cudaGetLastError();
+}
+
+size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps) {
+  return (size_t)r.n_rec * 16 + (size_t)((r.n_types * r.n_types + 1) & ~1) * 8 +
+         (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1);
+}
+
+cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,
+                           const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
+                           const int32_t *row_lig, const StateSrc *states, ligate_rescored *out,
+                           cudaStream_t s) {
+  if (n_poses <= 0) return cudaSuccess;
+  int warps = 4;
+  while (warps > 1 && rescore_smem_bytes(p, r, warps) > 227 * 1024) --warps;
+  const size_t smem = rescore_smem_bytes(p, r, warps);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rescore_kernel, 32 * warps, smem)))
+    return e;
+  const long long need = (n_poses + warps - 1) / warps;
+  const int grid = (int)std::min<long long>(need, (long long)sms * std::max(occ, 1));
+  StateSrc ss;
+  memset(&ss, 0, sizeof(ss));
+  if (states) ss = *states;
+  rescore_kernel<<<grid, 32 * warps, smem, s>>>(p, r, n_poses, lig_idx, start_id, tors,
+                                                reinterpret_cast<const PoseOut *>(poses), row_lig, ss, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ligate
