@@ -176,7 +176,9 @@ typedef struct {
  * shapes tuned per ligand size).  Size bucket b of a ligand is
  * min(n_rot / 4, 3) + 4 * (n_atoms > 64); starts_per_item[b] is how many
  * starts one warp takes from the work queue at a time (a multiple of the
- * warp's start group, 32 / pow2ceil(S)).  A zeroed field means "default". */
+ * warp's start group, 32 / pow2ceil(S)).  A zeroed field means "default":
+ * 4 warps, the mode's register cap, all SMs, chunks from the work model
+ * (see ligate_model_tile). */
 #define LIGATE_N_BUCKETS 8
 typedef struct {
   int warps_per_cta;   /* 1..4 */
@@ -403,10 +405,13 @@ ligate_status ligate_pose_features(const ligate_pocket *pocket, const ligate_bat
 ligate_status ligate_plan_pose_features(const ligate_plan *plan, float *out, void *stream);
 
 /* ------------------------------------------------------------------------
- * Autotuner (paper Sec. 3.3: per-size batch tuning).  Times candidate
- * shapes on a sample of the batch's ligands per size bucket and writes the
- * best to *best (and to the cache file named by LIGATE_TUNE_CACHE, when
- * set).  budget_ms bounds the total measuring time. */
+ * Autotuner (paper Sec. 3.3: per-size batch tuning).  Times the six CTA
+ * shapes (2 or 4 warps x register caps 85 / 102 / 128) on up to 2048
+ * ligands spread over the batch and writes the fastest to *best with zero
+ * chunk fields (and to the cache file named by LIGATE_TUNE_CACHE, when set):
+ * a plan fills zero chunk fields from the work model below for its own
+ * batch, so a tuned shape carries over to batches of any size.  budget_ms
+ * bounds the total measuring time. */
 ligate_status ligate_autotune(const ligate_pocket *pocket, const ligate_batch *batch,
                               const ligate_sampling *sampling, double budget_ms,
                               ligate_tile *best);
@@ -416,13 +421,14 @@ ligate_status ligate_autotune(const ligate_pocket *pocket, const ligate_batch *b
  * that keep the most warps resident on one SM under the register file and
  * shared-memory limits (for the plain FP32 layout only among the 128-register
  * instances: its eight scalar gathers per interpolation need registers for
- * loads in flight).  Chunk of size bucket b: starts_per_item[b] =
- * W / (8 P c_b) clamped to [128, 2048] and rounded down to the start group,
- * with W the run's total work (sum over ligands of starts x per-start cost
- * atoms + 0.35 clash pairs + 40), P the resident warps of the whole GPU and
- * c_b the bucket's mean per-start cost: the largest item stays under an
- * eighth of a warp's share, small enough to balance the tail, large enough
- * to amortise loading a ligand.  Writes *out; needs the current device. */
+ * loads in flight).  Chunk of size bucket b (the work model, also used by
+ * every plan for zero chunk fields): starts_per_item[b] = W / (8 P c_b)
+ * clamped to [128, 2048] and rounded down to the start group, with W the
+ * run's total work (sum over ligands of starts x per-start cost atoms +
+ * 0.35 clash pairs + 40), P the resident warps of the whole GPU and c_b the
+ * bucket's mean per-start cost: the largest item stays under an eighth of a
+ * warp's share, small enough to balance the tail, large enough to amortise
+ * loading a ligand.  Writes *out; needs the current device. */
 ligate_status ligate_model_tile(const ligate_pocket *pocket, const ligate_batch *batch,
                                 const ligate_sampling *sampling, ligate_tile *out);
 

@@ -654,14 +654,37 @@ static void free_plan(ligate_plan *pl) {
 // Tile shape: explicit, from the autotuner cache file, or the default.
 static bool read_tune_cache(int S, int mode, ligate_tile *t);
 
-static void default_tile(const DockParams &p, int n_ligands, int sms, ligate_tile *t) {
+static void default_tile(ligate_tile *t) {
   if (t->warps_per_cta <= 0) t->warps_per_cta = 4;
-  const int total_warps = sms * std::max(1, t->ctas_per_sm > 0 ? t->ctas_per_sm : 4) * t->warps_per_cta;
-  const double starts = (double)n_ligands * p.n_starts;
-  int chunk = (int)std::min(2048.0, std::max(4.0 * p.G, starts / (4.0 * total_warps)));
-  chunk = std::max(p.G, chunk / p.G * p.G);
-  for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
-    if (t->starts_per_item[b] <= 0) t->starts_per_item[b] = chunk;
+}
+
+// Work model of the launch (paper Sec. 3.3: a batch shape per ligand size):
+// chunk of size bucket b = W / (8 P c_b) starts, clamped to [128, 2048] and
+// rounded down to the start group, with W the run's total work (starts x
+// per-start cost atoms + 0.35 clash pairs + 40, the queue's own estimate),
+// P the warps resident on the whole GPU and c_b the bucket's mean per-start
+// cost: the largest item stays under an eighth of a warp's share (tail
+// balance) while still amortising the load of a ligand and its clash memo.
+// Buckets without ligands get 512.  Ligands: sel[0..n) or all of B.
+static void model_chunks(const BatchDev &B, const int32_t *sel, int n, int S, int n_starts, double P_warps,
+                         int G, int *chunks) {
+  double W = 0.0, cb[LIGATE_N_BUCKETS] = {0}, nb[LIGATE_N_BUCKETS] = {0};
+  for (int r = 0; r < n; ++r) {
+    const int i = sel ? sel[r] : r;
+    double a, q;
+    start_work(B, i, S, a, q);
+    const double c = a + 0.35 * q + 40.0;
+    W += c * n_starts;
+    const int b = bucket_of(B.h_lig[i]);
+    cb[b] += c;
+    nb[b] += 1.0;
+  }
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
+    double chunk = 512.0;
+    if (nb[b] > 0) chunk = W / (8.0 * std::max(P_warps, 1.0) * (cb[b] / nb[b]));
+    chunk = std::min(2048.0, std::max(128.0, chunk));
+    chunks[b] = std::max(G, (int)chunk / G * G);
+  }
 }
 
 // Plan over all ligands of B (sel == NULL) or over the ligands sel[0..n_sel),
@@ -706,25 +729,10 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   memset(&pl->tile, 0, sizeof(pl->tile));
   if (tile) pl->tile = *tile;
   else read_tune_cache(p.S, mode, &pl->tile);
-  default_tile(p, pl->n_ligands, sms, &pl->tile);
+  default_tile(&pl->tile);
   ligate_tile &t = pl->tile;
   t.warps_per_cta = std::max(1, std::min(4, t.warps_per_cta));
   if (t.reg_cap < 0 || t.reg_cap > 3) t.reg_cap = 0;
-  for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
-    t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
-  {  // keep the partial top-K lists (items x K poses) within 1 GiB: larger chunks for large batches
-    const double budget = 1024.0 * 1024.0 * 1024.0;
-    const int smallest = *std::min_element(t.starts_per_item, t.starts_per_item + LIGATE_N_BUCKETS);
-    const double bytes = (double)pl->n_ligands * std::ceil((double)p.n_starts / smallest) * p.K *
-                         sizeof(PoseOut);
-    if (bytes > budget) {
-      const double f = bytes / budget;
-      for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
-        const double c = std::ceil(t.starts_per_item[b] * f / p.G) * p.G;
-        t.starts_per_item[b] = (int)std::min<double>(c, std::max(p.n_starts, p.G));
-      }
-    }
-  }
   {  // fewer warps per CTA when large ligands or many start groups need more shared memory
     const size_t per_warp = dock_smem_per_warp(p.nmax, p.S, p.G);
     const int fit = (int)std::max<size_t>(1, (size_t)(227 * 1024) / per_warp);
@@ -746,6 +754,27 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   }
   t.ctas_per_sm = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, occ) : occ;
   pl->grid = sms * t.ctas_per_sm;
+  {  // chunks not given: the work model for this batch and these resident warps
+    int mc[LIGATE_N_BUCKETS];
+    model_chunks(B->d, sel, pl->n_ligands, p.S, p.n_starts, (double)pl->grid * t.warps_per_cta, p.G, mc);
+    for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
+      if (t.starts_per_item[b] <= 0) t.starts_per_item[b] = mc[b];
+  }
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b)
+    t.starts_per_item[b] = std::max(p.G, t.starts_per_item[b] / p.G * p.G);
+  {  // keep the partial top-K lists (items x K poses) within 1 GiB: larger chunks for large batches
+    const double budget = 1024.0 * 1024.0 * 1024.0;
+    const int smallest = *std::min_element(t.starts_per_item, t.starts_per_item + LIGATE_N_BUCKETS);
+    const double bytes = (double)pl->n_ligands * std::ceil((double)p.n_starts / smallest) * p.K *
+                         sizeof(PoseOut);
+    if (bytes > budget) {
+      const double f = bytes / budget;
+      for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
+        const double c = std::ceil(t.starts_per_item[b] * f / p.G) * p.G;
+        t.starts_per_item[b] = (int)std::min<double>(c, std::max(p.n_starts, p.G));
+      }
+    }
+  }
 
   // work queue: (ligand, start chunk) items, most expensive first
   const int n = pl->n_ligands;
@@ -1188,9 +1217,9 @@ extern "C" ligate_status ligate_plan_pose_features(const ligate_plan *pl, float 
 }
 
 // ===========================================================================
-// Autotuner: per size bucket, time a sample of that bucket's ligands under
-// candidate chunk sizes; the CTA shape (warps per CTA) is tuned on the whole
-// sample.  Results are cached per (device, S, mode) in LIGATE_TUNE_CACHE.
+// Autotuner: times the CTA shapes and register caps on a sample of the
+// batch; chunk sizes per size bucket come from the work model when a plan is
+// created.  Results are cached per (device, S, mode) in LIGATE_TUNE_CACHE.
 static std::string tune_key(int S, int mode) {
   cudaDeviceProp prop;
   int dev = 0;
@@ -1366,24 +1395,8 @@ extern "C" ligate_status ligate_model_tile(const ligate_pocket *P, const ligate_
     set_error("model_tile: ligands too large for any CTA shape");
     return LIGATE_ERR_UNSUPPORTED;
   }
-  const double P_w = (double)sms * best_res;
-  const int n_starts = s->n_orient * s->n_anchor;
-  double W = 0.0, cb[LIGATE_N_BUCKETS] = {0}, nb[LIGATE_N_BUCKETS] = {0};
-  for (int i = 0; i < B->d.n_ligands; ++i) {
-    double a, q;
-    start_work(B->d, i, S, a, q);
-    const double c = a + 0.35 * q + 40.0;
-    W += c * n_starts;
-    const int b = bucket_of(B->d.h_lig[i]);
-    cb[b] += c;
-    nb[b] += 1.0;
-  }
-  for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
-    double chunk = 512.0;
-    if (nb[b] > 0) chunk = W / (8.0 * P_w * (cb[b] / nb[b]));
-    chunk = std::min(2048.0, std::max(128.0, chunk));
-    t.starts_per_item[b] = std::max(G, (int)chunk / G * G);
-  }
+  model_chunks(B->d, nullptr, B->d.n_ligands, S, s->n_orient * s->n_anchor, (double)sms * best_res, G,
+               t.starts_per_item);
   *out = t;
   return LIGATE_OK;
 }
@@ -1399,30 +1412,17 @@ extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_ba
   auto elapsed = [&]() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   };
-  // sample: up to `per` ligands of each bucket, spread over the batch
-  std::vector<std::vector<int>> by_bucket(LIGATE_N_BUCKETS);
-  for (int i = 0; i < B->d.n_ligands; ++i) by_bucket[bucket_of(B->d.h_lig[i])].push_back(i);
-  const int per = 48;
-  std::vector<int> sample;
-  std::vector<std::vector<int>> bsample(LIGATE_N_BUCKETS);
-  for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
-    const auto &v = by_bucket[b];
-    const int m = std::min<int>(per, (int)v.size());
-    for (int j = 0; j < m; ++j) bsample[b].push_back(v[(size_t)j * v.size() / m]);
-    sample.insert(sample.end(), bsample[b].begin(), bsample[b].end());
-  }
   ligate_tile cur;
   memset(&cur, 0, sizeof(cur));
-  const int G = 32 / pow2ceil(s->torsion_steps);
-  if (sample.empty()) {
+  if (B->d.n_ligands == 0) {  // nothing to time: the default shape
     cur.warps_per_cta = 4;
-    for (int b = 0; b < LIGATE_N_BUCKETS; ++b) cur.starts_per_item[b] = std::max(G, 512 / G * G);
     *best = cur;
     return LIGATE_OK;
   }
-  // 1) CTA shape and register cap on up to 2048 ligands spread over the
-  //    batch (long enough a run for the steady state the full run sees),
-  //    with a mid chunk
+  // CTA shape and register cap, timed on up to 2048 ligands spread over the
+  // batch (long enough a run for the steady state the full run sees); chunk
+  // sizes come from the work model at plan time (zero fields), so the shape
+  // carries over to batches of any size
   std::vector<int> shape_sample;
   {
     const int n = B->d.n_ligands, m = std::min(n, 2048);
@@ -1430,7 +1430,6 @@ extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_ba
   }
   ligate_batch *SB = nullptr;
   if ((st = sub_batch(B, shape_sample, &SB)) != LIGATE_OK) return st;
-  const int mid = std::max(G, 512 / G * G);
   double best_ms = -1;
   ligate_tile best_t = cur;
   for (int shape = 0; shape < 6; ++shape) {  // 2 or 4 warps x register caps 85 / 102 / 128
@@ -1438,7 +1437,6 @@ extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_ba
     memset(&t, 0, sizeof(t));
     t.warps_per_cta = (shape & 1) ? 4 : 2;
     t.reg_cap = 1 + (shape >> 1);
-    for (int b = 0; b < LIGATE_N_BUCKETS; ++b) t.starts_per_item[b] = mid;
     const double ms = time_tile(P, SB, s, t, 3);
     if (ms > 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; best_t = t; }
     if (elapsed() > budget_ms) break;
@@ -1446,24 +1444,6 @@ extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_ba
   ligate_batch_destroy(SB);
   if (best_ms < 0) { set_error("autotune: no candidate shape ran"); return LIGATE_ERR_CUDA; }
   cur = best_t;
-  // 2) chunk per bucket, timed on that bucket's sample alone
-  for (int b = 0; b < LIGATE_N_BUCKETS && elapsed() < budget_ms; ++b) {
-    if (bsample[b].empty()) continue;
-    ligate_batch *BB = nullptr;
-    if (sub_batch(B, bsample[b], &BB) != LIGATE_OK) continue;
-    double bms = -1;
-    int bchunk = cur.starts_per_item[b];
-    for (int c : {128, 256, 512, 1024, 2048}) {
-      const int chunk = std::max(G, c / G * G);
-      ligate_tile t = cur;
-      for (int q = 0; q < LIGATE_N_BUCKETS; ++q) t.starts_per_item[q] = chunk;
-      const double ms = time_tile(P, BB, s, t, 2);
-      if (ms > 0 && (bms < 0 || ms < bms * 0.98)) { bms = ms; bchunk = chunk; }
-      if (elapsed() > budget_ms) break;
-    }
-    cur.starts_per_item[b] = bchunk;
-    ligate_batch_destroy(BB);
-  }
   *best = cur;
   write_tune_cache(s->torsion_steps, mode, cur);
   return LIGATE_OK;
