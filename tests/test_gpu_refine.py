@@ -257,3 +257,46 @@ def test_refine_argument_errors(tiny):
         with pytest.raises(RuntimeError):
             N.ligate_refine_states(ph.h, bh.h, s, 1, lig, rec, iters, eta, out)
     N.ligate_refine_states(ph.h, bh.h, s, 0, None, None, 4, 0.1, None)  # empty is fine
+
+
+def test_largest_ligands_refine_and_rescore():
+    """128 atoms and 16 rotatable bonds: gradient, one refinement step and
+    exact rescoring of states against the oracle at the library limits."""
+    from paper_2304_09953_gb300.workload import Pocket, Sampling, make_ligands, make_workload
+    w = make_workload("tiny", n_ligands=0)
+    big = make_ligands(5, np.array([128, 100], np.int32), np.array([16, 16], np.int32), 6)
+    rng = np.random.default_rng(0)
+    maps = (np.zeros((6, 80, 80, 80), np.float32) + w.pocket.maps.mean()
+            + rng.normal(size=(6, 80, 80, 80)).astype(np.float32)).astype(np.float32)
+    rec_xyz = rng.uniform(0, 39.5, size=(500, 3))
+    P = Pocket(maps, np.zeros(3), 0.5, np.array([[19.75, 19.75, 19.75]], np.float32),
+               rec_xyz, rng.integers(0, 6, size=500).astype(np.int32),
+               np.linspace(1.5, 2.0, 6), np.linspace(0.1, 0.3, 6))
+    samp = Sampling(w.sampling.quats[:4], 1, 4, 4)
+
+    class W:
+        pocket, ligands, sampling = P, big, samp
+
+    lig, rec, st64 = seeded_states(W, np.arange(2), rng, 8, spread=2.0)
+    ph = D.PocketHandle(P)
+    bh = D.BatchHandle(big)
+    s = N.make_sampling(samp, N.LIGATE_FP32, N.LIGATE_LAYOUT_PLAIN, False, None)
+    n = len(lig)
+    e = torch.zeros(n, dtype=torch.float32, device="cuda")
+    g = torch.zeros((n, N.LIGATE_GRAD_DIM), dtype=torch.float32, device="cuda")
+    N.ligate_pose_gradient(ph.h, bh.h, s, n, torch.from_numpy(lig).cuda(), to_dev(rec), e, g)
+    out = torch.zeros(n * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_rescore_states(ph.h, bh.h, s, n, torch.from_numpy(lig).cuda(), to_dev(rec), out)
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    r = out.cpu().numpy().view(N.RESCORED_DTYPE)
+    for li in range(2):
+        sel = np.nonzero(lig == li)[0]
+        L = big.ligand(li)
+        init = np.array([st64[k] for k in sel])
+        e64, g64, sc, _, face = oracle.pose_grad(L, P, samp, init)
+        o = oracle.rescore_coords(L, P, samp, P.receptor(), oracle.state_coords(L, init))
+        for m, k in enumerate(sel):
+            assert abs(e[k] - e64[m]) <= 1e-4 * max(sc[m, 0], 1.0)
+            if face[m] >= 1e-4:
+                np.testing.assert_array_less(np.abs(g[k, :22] - g64[m]), 2e-4 * np.maximum(sc[m, 1:], 1.0))
+            assert abs(r[k]["e_inter"] - o["e_inter"][m]) <= 1e-4 * max(o["scale"][m], 1.0)
