@@ -147,6 +147,21 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     # calibrated for 0.995 on the held-out set: its top 1% is a sample of a
     # few hundred ligands, so the margin covers the library's sampling spread
     keep_cal = T.keep_for_recall(pred_cal.cpu().numpy(), labels[n_fit:], 0.995)
+
+    # coarse-docking variant: the same network also sees the best score of a
+    # cheap docking pass (first 32 orientations x 8 anchors = 256 starts, 1/32
+    # of the sampling) in the free descriptor column 233
+    import dataclasses
+    coarse_s = dataclasses.replace(w.sampling, quats=w.sampling.quats[:32], n_anchor=8, top_k=1)
+    cp_tr = D.Plan(ph, tb, coarse_s, mode="bf16", rescore=False)
+    cp_tr.run(sh)
+    N.ligate_plan_best_scores(cp_tr.h, desc_tr, 256, 233, sh)
+    cp_tr.close()
+    sur_c = N.ligate_surrogate_create(None, 1004)
+    N.ligate_surrogate_train(sur_c, desc_tr[:n_fit], lab[:n_fit], n_fit, 20, 1024, 1e-3, 1004, sh)
+    N.ligate_surrogate_predict(sur_c, desc_tr[n_fit:], n_cal, pred_cal, sh)
+    torch.cuda.synchronize()
+    keep_cal_c = T.keep_for_recall(pred_cal.cpu().numpy(), labels[n_fit:], 0.995)
     del desc_tr, lab, pred_cal
     tb.close()
 
@@ -207,6 +222,57 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
         out["at_calibrated_keep"] = {"keep_frac": 1.0, "note": "calibration needs the whole library: "
                                      "triage gives no speed-up at 0.99 recall"}
     N.ligate_surrogate_destroy(sur)
+
+    # coarse docking + network
+    cplan = D.Plan(ph, bh, coarse_s, mode="bf16", rescore=False)
+
+    def timed_c(keep):
+        k = int(np.ceil(n * keep - 1e-9))
+        idx_dev = torch.empty(max(k, 1), dtype=torch.int32, device="cuda")
+
+        def step():
+            N.ligate_descriptors(bh.h, desc, sh)
+            N.ligate_plan_run(cplan.h, None, sh)
+            N.ligate_plan_best_scores(cplan.h, desc, 256, 233, sh)
+            N.ligate_surrogate_rank(sur_c, desc, n, keep, idx_dev, pred_all, sh)
+            sel = idx_dev[:k].cpu().numpy()
+            pl = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile, subset=sel)
+            pl.result(sh)
+            pl.close()
+            return sel
+
+        for _ in range(2):
+            step()
+        times = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            sel = step()
+            times.append(time.perf_counter() - a)
+        return k, sel, statistics.mean(times)
+
+    kc5, selc5, tc5 = timed_c(args.keep_frac)
+    pred_c = pred_all.cpu().numpy()
+    coarse_only = cplan.result(sh)["score"][:, 0]
+    coarse = {"value": n / tc5, "unit": "ligands/s", "ms_per_step": 1000 * tc5, "keep_frac": args.keep_frac,
+              "recall_top1pct": T.recall(truth_scores, selc5),
+              "recall_curve": {str(f): round(r, 4) for f, r in
+                               T.recall_curve(pred_c, truth_scores, [0.05, 0.1, 0.2, 0.3, 0.5]).items()},
+              "keep_needed_on_library_for_0.99": round(T.keep_for_recall(pred_c, truth_scores, 0.99), 4),
+              "coarse_score_alone_recall_curve": {str(f): round(r, 4) for f, r in
+                                                  T.recall_curve(coarse_only, truth_scores,
+                                                                 [0.05, 0.1, 0.2, 0.3, 0.5]).items()},
+              "form": "descriptors + coarse docking score (256 starts, bf16) in column 233 + MLP rank + "
+                      "dock kept fraction (chosen form)"}
+    if keep_cal_c < 1.0:
+        kcc, selcc, tcc = timed_c(keep_cal_c)
+        recc = T.recall(truth_scores, selcc)
+        coarse["at_calibrated_keep"] = {"value": n / tcc, "unit": "ligands/s", "ms_per_step": 1000 * tcc,
+                                        "keep_frac": round(keep_cal_c, 4), "docked_per_step": kcc,
+                                        "recall_top1pct": recc, "meets_target": recc >= 0.99}
+    cplan.close()
+    N.ligate_surrogate_destroy(sur_c)
+    out["with_coarse_docking"] = coarse
     return out
 
 

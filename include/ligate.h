@@ -217,6 +217,12 @@ ligate_status ligate_plan_create_subset(const ligate_pocket *pocket, const ligat
  * synchronised. */
 ligate_status ligate_plan_run(ligate_plan *plan, ligate_pose *out, void *stream);
 ligate_status ligate_plan_output(const ligate_plan *plan, const ligate_pose **device_ptr);
+/* Best score (the first pose) of every output row r of the plan's last run
+ * into DEVICE out[r * stride + column] (FP32; +inf for a row without a
+ * pose): e.g. a coarse docking run's scores into a free column of the
+ * ligand descriptors, so the triage network sees them (enqueues). */
+ligate_status ligate_plan_best_scores(const ligate_plan *plan, float *out, int stride, int column,
+                                      void *stream);
 /* Kernel launches one run enqueues, and the shape in use. */
 ligate_status ligate_plan_get_tile(const ligate_plan *plan, ligate_tile *tile_out,
                                    int *kernel_launches);

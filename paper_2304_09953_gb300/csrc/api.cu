@@ -978,6 +978,26 @@ extern "C" ligate_status ligate_score_poses(const ligate_pocket *P, const ligate
   return LIGATE_OK;
 }
 
+__global__ void best_scores_kernel(const PoseOut *__restrict__ poses, int n, int K, float *__restrict__ out,
+                                   int stride, int column) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) out[(size_t)r * stride + column] = poses[(size_t)r * K].score;
+}
+
+extern "C" ligate_status ligate_plan_best_scores(const ligate_plan *pl, float *out, int stride, int column,
+                                                 void *stream) {
+  if (!pl || !out || stride < 1 || column < 0 || column >= stride) {
+    set_error("plan_best_scores: bad arguments");
+    return LIGATE_ERR_INVALID;
+  }
+  const int n = pl->n_ligands;
+  if (n == 0) return LIGATE_OK;
+  best_scores_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(pl->out, n, pl->p.K, out, stride, column);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "plan_best_scores");
+  return LIGATE_OK;
+}
+
 // ===========================================================================
 // Pose refinement (refine.cu).
 static ligate_status refine_explicit(int mode, const ligate_pocket *P, const ligate_batch *B,

@@ -94,6 +94,7 @@ _SIGS = {
     "ligate_plan_create_subset": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, P]),
     "ligate_plan_run": (ctypes.c_int, [P, P, P]),
     "ligate_plan_output": (ctypes.c_int, [P, P]),
+    "ligate_plan_best_scores": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, P]),
     "ligate_plan_get_tile": (ctypes.c_int, [P, P, P]),
     "ligate_plan_work": (ctypes.c_int, [P, P]),
     "ligate_plan_destroy": (None, [P]),
@@ -357,6 +358,11 @@ def ligate_rescore_states(pocket, batch, sampling_struct, n, lig_idx, states, ou
 def ligate_plan_rescore_refined(plan, refined, out, stream=None):
     check(load().ligate_plan_rescore_refined(plan, _ptr(refined), _ptr(out), stream),
           "ligate_plan_rescore_refined")
+
+
+def ligate_plan_best_scores(plan, out, stride, column, stream=None):
+    check(load().ligate_plan_best_scores(plan, _ptr(out), int(stride), int(column), stream),
+          "ligate_plan_best_scores")
 
 
 def ligate_autotune(pocket, batch, sampling_struct, budget_ms=20000.0):
