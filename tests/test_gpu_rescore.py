@@ -249,3 +249,34 @@ def test_rescore_states_matches_oracle_and_refined_plan_path(batched_small):
     np.testing.assert_array_equal(via_plan[live], b.cpu().numpy().view(N.RESCORED_DTYPE))
     assert np.all(np.isinf(via_plan[~live]["energy"]))
     pl.close()
+
+
+def test_empty_slots_pass_through_every_stage(tiny):
+    """Two starts and top-4: slots 2 and 3 of the plan's output are empty;
+    refinement, exact rescoring (of docked and of refined poses) and the
+    selector features all mark them empty and handle the two real poses."""
+    import dataclasses
+    w = tiny
+    samp = dataclasses.replace(w.sampling, quats=w.sampling.quats[:1], n_anchor=2, top_k=4)
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    pl = D.Plan(ph, bh, samp, mode="fp32")
+    res = pl.result()
+    assert np.all(res[0]["start_id"][:2] >= 0) and list(res[0]["start_id"][2:]) == [-1, -1]
+    ref = pl.refine(iterations=8, eta0=0.1)
+    assert np.all(np.isinf(ref[0, 2:]["score_in"])) and np.all(ref[0, 2:]["accepted"] == 0)
+    assert np.all(np.isfinite(ref[0, :2]["score"]))
+    rs = pl.rescore_exact()
+    assert np.all(np.isinf(rs[0, 2:]["energy"])) and np.all(rs[0, 2:]["pass"] == 0)
+    rbuf = torch.from_numpy(ref.reshape(-1).view(np.uint8).copy()).cuda()
+    out = torch.empty(4 * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    N.ligate_plan_rescore_refined(pl.h, rbuf, out)
+    torch.cuda.synchronize()
+    rr = out.cpu().numpy().view(N.RESCORED_DTYPE)
+    assert np.all(np.isinf(rr[2:]["energy"])) and np.all(np.isfinite(rr[:2]["energy"]))
+    f = torch.empty((4, 256), dtype=torch.float32, device="cuda")
+    N.ligate_plan_pose_features(pl.h, f)
+    torch.cuda.synchronize()
+    f = f.cpu().numpy()
+    assert np.all(f[2:] == 0) and np.all(f[:2, 74] > 0)
+    pl.close()
