@@ -498,6 +498,14 @@ ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s, float *out
  * predict then returns only after its kernels have finished. */
 int ligate_surrogate_engine(const ligate_surrogate *s);
 
+/* Test hook for the failure path, not for normal use.  kind 1: the next CTA
+ * of a tcgen05 contraction on the current device issues none of its tensor
+ * loads, so its bounded wait on the first stage runs out (after 2 s); the
+ * kernel records the timeout, releases its tensor memory and returns, and
+ * the surrogate call that launched it returns LIGATE_ERR_TIMEOUT.  Nothing
+ * hangs and the context stays usable.  Other kinds: INVALID. */
+ligate_status ligate_debug_inject_fault(int kind);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

@@ -49,6 +49,9 @@ bool tc05_supported(int M, int N, int K);
 cudaError_t gemm_tc05(int epi, const __nv_bfloat16 *a, int M, int K, const __nv_bfloat16 *b, int N,
                       const float *bias, const __nv_bfloat16 *mask, __nv_bfloat16 *out, int *err,
                       cudaStream_t s);
+// Test hook: the next CTA of a tcgen05 contraction issues no loads, so its
+// bounded wait runs out (err set, LIGATE_ERR_TIMEOUT at the next check).
+cudaError_t inject_skip_loads_once();
 // wt[n][k] = bf16(w[k][n]) for row-major FP32 w [K][N].
 cudaError_t transpose_bf16(const float *w, int K, int N, __nv_bfloat16 *wt, cudaStream_t s);
 

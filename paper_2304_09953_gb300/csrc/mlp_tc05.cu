@@ -100,6 +100,10 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// Fault flag for tests of the timeout path (ligate_debug_inject_fault):
+// nothing in normal operation sets it.
+__device__ int g_fault_skip_loads = 0;
+
 struct __align__(1024) Smem {
   uint8_t a[STAGES][A_BYTES];
   uint8_t b[STAGES][B_BYTES];
@@ -142,7 +146,10 @@ __global__ void __launch_bounds__(128, 1)
   if (threadIdx.x == 0) {
     bool ok = true;
     int issued = 0;  // K slices whose loads were issued
-    for (int kb = 0; kb < nk && kb < STAGES; ++kb, ++issued) {
+    // test hook: a CTA that takes the fault flag issues no loads, so its
+    // bounded wait on the first stage runs out and the error path runs
+    const bool skip_loads = atomicExch(&g_fault_skip_loads, 0) != 0;
+    for (int kb = 0; kb < nk && kb < STAGES && !skip_loads; ++kb, ++issued) {
       mbar_expect_tx(&s.full[kb], A_BYTES + B_BYTES);
       tma_load_2d(s.a[kb], &tm_a, &s.full[kb], kb * TK, m0);
       tma_load_2d(s.b[kb], &tm_b, &s.full[kb], kb * TK, n0);
@@ -289,6 +296,11 @@ cudaError_t gemm_tc05(int epi, const __nv_bfloat16 *a, int M, int K, const __nv_
   else
     gemm_tc05_kernel<EPI_RELU_MASK><<<grid, 128, smem, s>>>(ta, tb, M, K, nullptr, mask, out, N, err);
   return cudaGetLastError();
+}
+
+cudaError_t inject_skip_loads_once() {
+  const int one = 1;
+  return cudaMemcpyToSymbol(g_fault_skip_loads, &one, sizeof(int));
 }
 
 // Wt[n][k] = bf16(W[k][n]) for a row-major [K][N] FP32 weight matrix.

@@ -450,3 +450,10 @@ extern "C" ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s,
 }
 
 extern "C" int ligate_surrogate_engine(const ligate_surrogate *s) { return s ? (s->tc05 ? 1 : 0) : -1; }
+
+extern "C" ligate_status ligate_debug_inject_fault(int kind) {
+  if (kind != 1) { set_error("debug_inject_fault: unknown kind %d", kind); return LIGATE_ERR_INVALID; }
+  cudaError_t e = mlp::inject_skip_loads_once();
+  if (e != cudaSuccess) return cuda_fail(e, "debug_inject_fault");
+  return LIGATE_OK;
+}

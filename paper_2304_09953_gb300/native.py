@@ -113,6 +113,7 @@ _SIGS = {
     "ligate_surrogate_grad": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P]),
     "ligate_surrogate_get_weights": (ctypes.c_int, [P, P]),
     "ligate_surrogate_engine": (ctypes.c_int, [P]),
+    "ligate_debug_inject_fault": (ctypes.c_int, [ctypes.c_int]),
     "ligate_pose_gradient": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_refine_states": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_float, P, P]),
     "ligate_plan_refine": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_float, P, P]),
@@ -428,3 +429,9 @@ def ligate_surrogate_get_weights(h):
 def ligate_surrogate_engine(h):
     """1: tcgen05 contractions, 0: mma.sync (LIGATE_MLP_GEMM=mma at creation)."""
     return int(load().ligate_surrogate_engine(h))
+
+
+def ligate_debug_inject_fault(kind):
+    """Test hook: see include/ligate.h."""
+    check(load().ligate_debug_inject_fault(int(kind)), "ligate_debug_inject_fault")
+

@@ -252,3 +252,31 @@ def test_coarse_docking_feature_lifts_triage_recall():
     # 40 true top-1% ligands: one ligand is 0.025 of recall
     assert recalls["with coarse"][0.05] >= alone[0.05] - 0.05
     assert recalls["with coarse"][0.1] >= alone[0.1] - 0.025
+
+
+def test_tcgen05_wait_timeout_is_reported_and_recoverable(monkeypatch):
+    """Failure path without a GPU fault: the test hook makes one CTA of the
+    next tcgen05 contraction skip its tensor loads (a flag nothing else
+    sets), so its bounded wait runs out; predict returns LIGATE_ERR_TIMEOUT,
+    and the next predict on the same context gives the normal results."""
+    monkeypatch.setenv("LIGATE_MLP_GEMM", "tc05")
+    rng = np.random.default_rng(21)
+    s = N.ligate_surrogate_create(None, 3)
+    try:
+        assert N.ligate_surrogate_engine(s) == 1
+        n = 1000
+        desc = torch.from_numpy(rng.normal(size=(n, 256)).astype(np.float32)).cuda()
+        ref = torch.zeros(n, dtype=torch.float32, device="cuda")
+        N.ligate_surrogate_predict(s, desc, n, ref)
+        N.ligate_debug_inject_fault(1)
+        bad = torch.zeros(n, dtype=torch.float32, device="cuda")
+        with pytest.raises(N.LigateError) as ei:
+            N.ligate_surrogate_predict(s, desc, n, bad)
+        assert ei.value.status == N.LIGATE_ERR_TIMEOUT
+        again = torch.zeros(n, dtype=torch.float32, device="cuda")
+        N.ligate_surrogate_predict(s, desc, n, again)
+        np.testing.assert_array_equal(again.cpu().numpy(), ref.cpu().numpy())
+    finally:
+        N.ligate_surrogate_destroy(s)
+    with pytest.raises(N.LigateError):
+        N.ligate_debug_inject_fault(7)
