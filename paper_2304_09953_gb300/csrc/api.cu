@@ -354,6 +354,7 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
 }  // namespace
 
 extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_batch **out) {
+  NvtxRange nvtx_("ligate:batch_create");
   if (!out || !L) { set_error("batch_create: NULL argument"); return LIGATE_ERR_INVALID; }
   *out = nullptr;
   const int n = L->n_ligands;
@@ -692,6 +693,7 @@ static void model_chunks(const BatchDev &B, const int32_t *sel, int n, int S, in
 static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch *B,
                                       const ligate_sampling *s, const ligate_tile *tile,
                                       const int32_t *sel, int n_sel, ligate_plan **out) {
+  NvtxRange nvtx_("ligate:plan_create");
   if (!out) { set_error("plan_create: out is NULL"); return LIGATE_ERR_INVALID; }
   *out = nullptr;
   int mode = 0;
@@ -889,6 +891,7 @@ static bool is_host_ptr(const void *p) {
 }
 
 extern "C" ligate_status ligate_plan_run(ligate_plan *pl, ligate_pose *out, void *stream) {
+  NvtxRange nvtx_("ligate:plan_run");
   if (!pl) { set_error("plan_run: NULL plan"); return LIGATE_ERR_INVALID; }
   ligate_status st = plan_capture(pl);
   if (st != LIGATE_OK) return st;
@@ -934,6 +937,7 @@ extern "C" void ligate_plan_destroy(ligate_plan *pl) { free_plan(pl); }
 extern "C" ligate_status ligate_dock_batch(const ligate_pocket *P, const ligate_ligands *L,
                                            const ligate_sampling *s, ligate_pose *out,
                                            void *stream) {
+  NvtxRange nvtx_("ligate:dock_batch");
   if (!out && L && L->n_ligands > 0) { set_error("dock_batch: out is NULL"); return LIGATE_ERR_INVALID; }
   ligate_batch *B = nullptr;
   ligate_status st = ligate_batch_create(L, &B);
@@ -1054,6 +1058,7 @@ extern "C" ligate_status ligate_refine_states(const ligate_pocket *P, const liga
 
 extern "C" ligate_status ligate_plan_refine(const ligate_plan *pl, int iterations, float eta0,
                                             ligate_refined *out, void *stream) {
+  NvtxRange nvtx_("ligate:plan_refine");
   if (!pl || !out) { set_error("plan_refine: NULL argument"); return LIGATE_ERR_INVALID; }
   if (iterations < 0 || iterations > LIGATE_REFINE_MAX_ITERS || !(eta0 > 0.f) || !std::isfinite(eta0)) {
     set_error("plan_refine: iterations must be 0..%d and eta0 finite and > 0", LIGATE_REFINE_MAX_ITERS);
@@ -1120,6 +1125,7 @@ extern "C" ligate_status ligate_rescore_poses(const ligate_pocket *P, const liga
 }
 
 extern "C" ligate_status ligate_plan_rescore(const ligate_plan *pl, ligate_rescored *out, void *stream) {
+  NvtxRange nvtx_("ligate:plan_rescore");
   if (!pl || !out) { set_error("plan_rescore: NULL argument"); return LIGATE_ERR_INVALID; }
   RecParams r;
   ligate_status st = rec_params(pl->pocket, pl->batch, r, "plan_rescore");
@@ -1226,6 +1232,7 @@ extern "C" ligate_status ligate_pose_features(const ligate_pocket *P, const liga
 }
 
 extern "C" ligate_status ligate_plan_pose_features(const ligate_plan *pl, float *out, void *stream) {
+  NvtxRange nvtx_("ligate:plan_pose_features");
   if (!pl || !out) { set_error("plan_pose_features: NULL argument"); return LIGATE_ERR_INVALID; }
   const int n = pl->n_ligands * pl->p.K;
   if (n == 0) return LIGATE_OK;
@@ -1424,6 +1431,7 @@ extern "C" ligate_status ligate_model_tile(const ligate_pocket *P, const ligate_
 extern "C" ligate_status ligate_autotune(const ligate_pocket *P, const ligate_batch *B,
                                          const ligate_sampling *s, double budget_ms,
                                          ligate_tile *best) {
+  NvtxRange nvtx_("ligate:autotune");
   int mode = 0;
   ligate_status st = check_sampling(P, B, s, &mode);
   if (st != LIGATE_OK) return st;

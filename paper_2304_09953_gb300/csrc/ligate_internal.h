@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ligate.h"
 
 namespace ligate {
@@ -219,6 +221,15 @@ cudaError_t launch_corner_pack(const float *plain, int n_types, int nx, int ny, 
 // Descriptor + surrogate kernels (surrogate.cu): declared there.
 
 // Error helpers (api.cu).
+// NVTX range over a scope (a named span on the profiler's timeline; free
+// when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 void set_error(const char *fmt, ...);
 ligate_status cuda_fail(cudaError_t e, const char *what);
 

@@ -305,6 +305,7 @@ extern "C" void ligate_surrogate_destroy(ligate_surrogate *s) {
 extern "C" ligate_status ligate_surrogate_train(ligate_surrogate *s, const float *desc,
                                                 const float *labels, int n, int epochs, int batch,
                                                 float lr, uint64_t seed, float *loss_out, void *stream) {
+  NvtxRange nvtx_("ligate:surrogate_train");
   if (!s || !desc || !labels) { set_error("surrogate_train: NULL argument"); return LIGATE_ERR_INVALID; }
   if (n < 1 || batch < 8 || batch % 8 != 0 || batch > n || epochs < 0 || !(lr > 0)) {
     set_error("surrogate_train: need 8 <= batch <= n, batch % 8 == 0, epochs >= 0, lr > 0");
@@ -393,6 +394,7 @@ extern "C" ligate_status ligate_surrogate_grad(const ligate_surrogate *cs, const
 
 extern "C" ligate_status ligate_surrogate_predict(const ligate_surrogate *cs, const float *desc, int n,
                                                   float *pred, void *stream) {
+  NvtxRange nvtx_("ligate:surrogate_predict");
   ligate_surrogate *s = const_cast<ligate_surrogate *>(cs);
   if (!s || (n > 0 && (!desc || !pred)) || n < 0) { set_error("surrogate_predict: bad argument"); return LIGATE_ERR_INVALID; }
   cudaStream_t st = (cudaStream_t)stream;
@@ -414,6 +416,7 @@ extern "C" ligate_status ligate_surrogate_predict(const ligate_surrogate *cs, co
 extern "C" ligate_status ligate_surrogate_rank(const ligate_surrogate *s, const float *desc, int n,
                                                double keep_frac, int32_t *idx_out, float *pred_out,
                                                void *stream) {
+  NvtxRange nvtx_("ligate:surrogate_rank");
   if (!s || n < 0 || !(keep_frac >= 0.0 && keep_frac <= 1.0) || (n > 0 && (!desc || !idx_out))) {
     set_error("surrogate_rank: bad argument");
     return LIGATE_ERR_INVALID;
