@@ -487,6 +487,12 @@ ligate_status ligate_surrogate_rank(const ligate_surrogate *s, const float *desc
  * into DEVICE grad[LIGATE_SURROGATE_PARAMS]; *loss_out (host) = MSE. */
 ligate_status ligate_surrogate_grad(const ligate_surrogate *s, const float *x, const float *t,
                                     int b, float *grad, float *loss_out, void *stream);
+/* Checkpoint of the whole training state (weights, Adam moments and step,
+ * input and label standardisation) to a binary file and back; training
+ * resumed from a loaded checkpoint continues exactly as it would have
+ * without the save.  Errors: INVALID for an unreadable or foreign file. */
+ligate_status ligate_surrogate_save(const ligate_surrogate *s, const char *path);
+ligate_status ligate_surrogate_load(const char *path, ligate_surrogate **out);
 /* Copy the FP32 master weights (host [LIGATE_SURROGATE_PARAMS]). */
 ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s, float *out);
 /* Contraction engine chosen at creation: 1 when the forward layers and the

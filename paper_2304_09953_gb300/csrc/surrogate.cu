@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -460,3 +461,77 @@ extern "C" ligate_status ligate_debug_inject_fault(int kind) {
   if (e != cudaSuccess) return cuda_fail(e, "debug_inject_fault");
   return LIGATE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Checkpoint: a little-endian binary file: 8-byte magic "LGSURR01", int32
+// parameter count, int32 feature count, int64 Adam step, FP64 label mean and
+// standard deviation, int32 statistics flag, then FP32 arrays: weights,
+// Adam first and second moments (parameter count each), feature means and
+// inverse standard deviations (feature count each).
+namespace {
+const char kMagic[8] = {'L', 'G', 'S', 'U', 'R', 'R', '0', '1'};
+}
+
+extern "C" ligate_status ligate_surrogate_save(const ligate_surrogate *s, const char *path) {
+  if (!s || !path) { set_error("surrogate_save: NULL argument"); return LIGATE_ERR_INVALID; }
+  std::vector<float> buf((size_t)3 * NPAR + 2 * F0);
+  cudaError_t e;
+  if ((e = cudaMemcpy(buf.data(), s->w, (size_t)NPAR * 4, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(buf.data() + NPAR, s->m, (size_t)NPAR * 4, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(buf.data() + 2 * (size_t)NPAR, s->v, (size_t)NPAR * 4, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(buf.data() + 3 * (size_t)NPAR, s->mu, (size_t)F0 * 4, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(buf.data() + 3 * (size_t)NPAR + F0, s->inv_sd, (size_t)F0 * 4, cudaMemcpyDeviceToHost)))
+    return cuda_fail(e, "surrogate_save");
+  FILE *f = fopen(path, "wb");
+  if (!f) { set_error("surrogate_save: cannot open %s", path); return LIGATE_ERR_INVALID; }
+  const int32_t np = NPAR, nf = F0, st = s->stats ? 1 : 0;
+  const int64_t step = s->step;
+  bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(&np, 4, 1, f) == 1 && fwrite(&nf, 4, 1, f) == 1 &&
+            fwrite(&step, 8, 1, f) == 1 && fwrite(&s->label_mu, 8, 1, f) == 1 &&
+            fwrite(&s->label_sd, 8, 1, f) == 1 && fwrite(&st, 4, 1, f) == 1 &&
+            fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) { set_error("surrogate_save: write to %s failed", path); return LIGATE_ERR_INVALID; }
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_surrogate_load(const char *path, ligate_surrogate **out) {
+  if (!path || !out) { set_error("surrogate_load: NULL argument"); return LIGATE_ERR_INVALID; }
+  *out = nullptr;
+  FILE *f = fopen(path, "rb");
+  if (!f) { set_error("surrogate_load: cannot open %s", path); return LIGATE_ERR_INVALID; }
+  char magic[8];
+  int32_t np = 0, nf = 0, st = 0;
+  int64_t step = 0;
+  double lmu = 0, lsd = 1;
+  std::vector<float> buf((size_t)3 * NPAR + 2 * F0);
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 && fread(&np, 4, 1, f) == 1 &&
+            fread(&nf, 4, 1, f) == 1 && np == NPAR && nf == F0 && fread(&step, 8, 1, f) == 1 &&
+            fread(&lmu, 8, 1, f) == 1 && fread(&lsd, 8, 1, f) == 1 && fread(&st, 4, 1, f) == 1 &&
+            fread(buf.data(), 4, buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok || step < 0 || !std::isfinite(lmu) || !(lsd > 0)) {
+    set_error("surrogate_load: %s is not a surrogate checkpoint of this network", path);
+    return LIGATE_ERR_INVALID;
+  }
+  for (float x : buf)
+    if (!std::isfinite(x)) { set_error("surrogate_load: non-finite value in %s", path); return LIGATE_ERR_INVALID; }
+  ligate_surrogate *s = nullptr;
+  ligate_status r = ligate_surrogate_create(buf.data(), 0, &s);
+  if (r != LIGATE_OK) return r;
+  cudaError_t e;
+  if ((e = cudaMemcpy(s->m, buf.data() + NPAR, (size_t)NPAR * 4, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(s->v, buf.data() + 2 * (size_t)NPAR, (size_t)NPAR * 4, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(s->mu, buf.data() + 3 * (size_t)NPAR, (size_t)F0 * 4, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(s->inv_sd, buf.data() + 3 * (size_t)NPAR + F0, (size_t)F0 * 4, cudaMemcpyHostToDevice))) {
+    ligate_surrogate_destroy(s);
+    return cuda_fail(e, "surrogate_load");
+  }
+  s->step = step;
+  s->label_mu = lmu;
+  s->label_sd = lsd;
+  s->stats = st != 0;
+  *out = s;
+  return LIGATE_OK;
+}
+

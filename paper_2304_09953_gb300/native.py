@@ -113,6 +113,8 @@ _SIGS = {
     "ligate_surrogate_grad": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P]),
     "ligate_surrogate_get_weights": (ctypes.c_int, [P, P]),
     "ligate_surrogate_engine": (ctypes.c_int, [P]),
+    "ligate_surrogate_save": (ctypes.c_int, [P, ctypes.c_char_p]),
+    "ligate_surrogate_load": (ctypes.c_int, [ctypes.c_char_p, P]),
     "ligate_debug_inject_fault": (ctypes.c_int, [ctypes.c_int]),
     "ligate_pose_gradient": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_refine_states": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_float, P, P]),
@@ -434,4 +436,14 @@ def ligate_surrogate_engine(h):
 def ligate_debug_inject_fault(kind):
     """Test hook: see include/ligate.h."""
     check(load().ligate_debug_inject_fault(int(kind)), "ligate_debug_inject_fault")
+
+
+def ligate_surrogate_save(h, path):
+    check(load().ligate_surrogate_save(h, str(path).encode()), "ligate_surrogate_save")
+
+
+def ligate_surrogate_load(path):
+    h = ctypes.c_void_p()
+    check(load().ligate_surrogate_load(str(path).encode(), ctypes.byref(h)), "ligate_surrogate_load")
+    return h
 

@@ -226,3 +226,27 @@ def test_model_tile_is_valid_and_changes_nothing(batched_small, mode):
     pl = D.Plan(ph, bh, w.sampling, mode=mode, tile=t)
     ref = D.Plan(ph, bh, w.sampling, mode=mode, tile=N.ligate_tile()).result()
     assert np.array_equal(pl.result(), ref)
+
+
+def test_journaled_screening_resumes_after_an_interruption(batched_small, tmp_path):
+    """Chunks of 16 ligands; the first run stops (an exception raised on the
+    host) after the second chunk is journaled; the rerun docks only the
+    missing chunks and the result equals one run over the whole library."""
+    from paper_2304_09953_gb300.screen import screen_library
+    w = batched_small
+    seen = []
+
+    def stop_after_two(c):
+        seen.append(c)
+        if len(seen) == 2:
+            raise KeyboardInterrupt("simulated interruption")
+
+    with pytest.raises(KeyboardInterrupt):
+        screen_library(w.pocket, w.ligands, w.sampling, tmp_path / "j", chunk=16, on_chunk=stop_after_two)
+    rest = []
+    out = screen_library(w.pocket, w.ligands, w.sampling, tmp_path / "j", chunk=16, on_chunk=rest.append)
+    assert seen == [0, 1] and rest == [2, 3]
+    ref = D.dock(w.pocket, w.ligands, w.sampling, mode="bf16")
+    assert np.array_equal(out, ref)
+    with pytest.raises(ValueError):
+        screen_library(w.pocket, w.ligands.subset(np.arange(10)), w.sampling, tmp_path / "j", chunk=16)

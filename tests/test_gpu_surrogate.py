@@ -280,3 +280,37 @@ def test_tcgen05_wait_timeout_is_reported_and_recoverable(monkeypatch):
         N.ligate_surrogate_destroy(s)
     with pytest.raises(N.LigateError):
         N.ligate_debug_inject_fault(7)
+
+
+def test_checkpoint_resumes_training_exactly(tmp_path):
+    """Save after one epoch, load into a new object, train both one more
+    epoch with the same seed: identical weights (Adam moments, step and
+    standardisation travel with the checkpoint) and identical predictions."""
+    rng = np.random.default_rng(31)
+    n = 4096
+    desc = torch.from_numpy(rng.normal(size=(n, 256)).astype(np.float32)).cuda()
+    lab = torch.from_numpy(rng.normal(size=n).astype(np.float32)).cuda()
+    a = N.ligate_surrogate_create(None, 5)
+    b = None
+    try:
+        N.ligate_surrogate_train(a, desc, lab, n, 1, 512, 1e-3, 1)
+        path = tmp_path / "sur.bin"
+        N.ligate_surrogate_save(a, path)
+        b = N.ligate_surrogate_load(path)
+        np.testing.assert_array_equal(N.ligate_surrogate_get_weights(a), N.ligate_surrogate_get_weights(b))
+        N.ligate_surrogate_train(a, desc, lab, n, 1, 512, 1e-3, 2)
+        N.ligate_surrogate_train(b, desc, lab, n, 1, 512, 1e-3, 2)
+        np.testing.assert_array_equal(N.ligate_surrogate_get_weights(a), N.ligate_surrogate_get_weights(b))
+        pa = torch.zeros(n, dtype=torch.float32, device="cuda")
+        pb = torch.zeros(n, dtype=torch.float32, device="cuda")
+        N.ligate_surrogate_predict(a, desc, n, pa)
+        N.ligate_surrogate_predict(b, desc, n, pb)
+        np.testing.assert_array_equal(pa.cpu().numpy(), pb.cpu().numpy())
+        bad = tmp_path / "bad.bin"
+        bad.write_bytes(b"not a checkpoint")
+        with pytest.raises(N.LigateError):
+            N.ligate_surrogate_load(bad)
+    finally:
+        N.ligate_surrogate_destroy(a)
+        if b is not None:
+            N.ligate_surrogate_destroy(b)
