@@ -253,16 +253,31 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         Rot rot;
         rot.make(ck, sk, nx, ny, nz, pv.x, pv.y, pv.z);
         // grid part: every moved atom at this lane's torsion step, two atoms
-        // per iteration so two map gathers are in flight per lane
+        // per iteration: two map gathers in flight per lane, and the rotation
+        // and interpolation arithmetic of the pair in packed FP32 (FFMA2)
         float ag = 0.f, ag2 = 0.f;
         int i = br.v + 1;
         for (; i + 1 < br.end; i += 2) {
           const float4 q = pose[i], q2 = pose[i + 1];
-          float yx, yy, yz, zx, zy, zz;
-          rot.apply(q.x, q.y, q.z, yx, yy, yz);
-          rot.apply(q2.x, q2.y, q2.z, zx, zy, zz);
-          ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
-          ag2 += grid_eval<MODE>(p.maps, __float_as_int(q2.w), zx, zy, zz, p.g);
+          if (MODE == MODE_F32_PLAIN) {  // eight scalar gathers each: registers go to loads in flight
+            float yx, yy, yz, zx, zy, zz;
+            rot.apply(q.x, q.y, q.z, yx, yy, yz);
+            rot.apply(q2.x, q2.y, q2.z, zx, zy, zz);
+            ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
+            ag2 += grid_eval<MODE>(p.maps, __float_as_int(q2.w), zx, zy, zz, p.g);
+            continue;
+          }
+          const float2 X = make_float2(q.x, q2.x), Y = make_float2(q.y, q2.y), Z = make_float2(q.z, q2.z);
+          const float2 ox = __ffma2_rn(make_float2(rot.r00, rot.r00), X, __ffma2_rn(make_float2(rot.r01, rot.r01), Y,
+                            __ffma2_rn(make_float2(rot.r02, rot.r02), Z, make_float2(rot.tx, rot.tx))));
+          const float2 oy = __ffma2_rn(make_float2(rot.r10, rot.r10), X, __ffma2_rn(make_float2(rot.r11, rot.r11), Y,
+                            __ffma2_rn(make_float2(rot.r12, rot.r12), Z, make_float2(rot.ty, rot.ty))));
+          const float2 oz = __ffma2_rn(make_float2(rot.r20, rot.r20), X, __ffma2_rn(make_float2(rot.r21, rot.r21), Y,
+                            __ffma2_rn(make_float2(rot.r22, rot.r22), Z, make_float2(rot.tz, rot.tz))));
+          const float2 v = grid_eval2<MODE>(p.maps, __float_as_int(q.w), ox.x, oy.x, oz.x, __float_as_int(q2.w),
+                                            ox.y, oy.y, oz.y, p.g);
+          ag += v.x;
+          ag2 += v.y;
         }
         if (i < br.end) {
           const float4 q = pose[i];

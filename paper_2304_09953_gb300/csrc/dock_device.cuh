@@ -67,6 +67,71 @@ __device__ __forceinline__ float grid_eval(const void *__restrict__ maps, int to
   return fmaf(fz, z1 - z0, z0);
 }
 
+
+// Two atoms at once with packed FP32 (FFMA2 / FADD2: per component the same
+// rounding as fmaf / the scalar add, so each value equals grid_eval's).
+template <int MODE>
+__device__ __forceinline__ void load_corners(const void *__restrict__ maps, int toff, int ix, int iy, int iz,
+                                             const GridConst &g, float (&v)[8]) {
+  if (MODE == MODE_F32_PLAIN) {
+    const float *m = (const float *)maps + toff + (iz * g.ny + iy) * g.nx + ix;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    v[0] = __ldg(m); v[1] = __ldg(m + 1); v[2] = __ldg(m + sy); v[3] = __ldg(m + sy + 1);
+    v[4] = __ldg(m + sz); v[5] = __ldg(m + sz + 1); v[6] = __ldg(m + sz + sy); v[7] = __ldg(m + sz + sy + 1);
+  } else {
+    const int cell = toff + (iz * (g.ny - 1) + iy) * (g.nx - 1) + ix;
+    if (MODE == MODE_F32_CORNER) {
+      const float4 *m = (const float4 *)maps + 2 * cell;
+      const float4 a = __ldg(m), b = __ldg(m + 1);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+      const uint4 w = __ldg((const uint4 *)maps + cell);
+      if (MODE == MODE_BF16_CORNER) {
+        v[0] = __uint_as_float(w.x << 16); v[1] = __uint_as_float(w.x & 0xffff0000u);
+        v[2] = __uint_as_float(w.y << 16); v[3] = __uint_as_float(w.y & 0xffff0000u);
+        v[4] = __uint_as_float(w.z << 16); v[5] = __uint_as_float(w.z & 0xffff0000u);
+        v[6] = __uint_as_float(w.w << 16); v[7] = __uint_as_float(w.w & 0xffff0000u);
+      } else {
+        float2 f;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.x)); v[0] = f.x; v[1] = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.y)); v[2] = f.x; v[3] = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.z)); v[4] = f.x; v[5] = f.y;
+        f = __half22float2(*reinterpret_cast<const __half2 *>(&w.w)); v[6] = f.x; v[7] = f.y;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+template <int MODE>
+__device__ __forceinline__ float2 grid_eval2(const void *__restrict__ maps, int toffa, float ax, float ay, float az,
+                                             int toffb, float bx, float by, float bz, const GridConst &g) {
+  const bool ina = (ax >= 0.f) & (ax <= g.fx1) & (ay >= 0.f) & (ay <= g.fy1) & (az >= 0.f) & (az <= g.fz1);
+  const bool inb = (bx >= 0.f) & (bx <= g.fx1) & (by >= 0.f) & (by <= g.fy1) & (bz >= 0.f) & (bz <= g.fz1);
+  const int ixa = ina ? min((int)ax, g.nx - 2) : 0, iya = ina ? min((int)ay, g.ny - 2) : 0,
+            iza = ina ? min((int)az, g.nz - 2) : 0;
+  const int ixb = inb ? min((int)bx, g.nx - 2) : 0, iyb = inb ? min((int)by, g.ny - 2) : 0,
+            izb = inb ? min((int)bz, g.nz - 2) : 0;
+  const float2 fx = sub2(make_float2(ax, bx), make_float2((float)ixa, (float)ixb));
+  const float2 fy = sub2(make_float2(ay, by), make_float2((float)iya, (float)iyb));
+  const float2 fz = sub2(make_float2(az, bz), make_float2((float)iza, (float)izb));
+  float va[8], vb[8];
+  load_corners<MODE>(maps, ina ? toffa : 0, ixa, iya, iza, g, va);
+  load_corners<MODE>(maps, inb ? toffb : 0, ixb, iyb, izb, g, vb);
+  const float2 v0 = make_float2(va[0], vb[0]), v1 = make_float2(va[1], vb[1]), v2 = make_float2(va[2], vb[2]),
+               v3 = make_float2(va[3], vb[3]), v4 = make_float2(va[4], vb[4]), v5 = make_float2(va[5], vb[5]),
+               v6 = make_float2(va[6], vb[6]), v7 = make_float2(va[7], vb[7]);
+  const float2 y0z0 = __ffma2_rn(fx, sub2(v1, v0), v0);
+  const float2 y1z0 = __ffma2_rn(fx, sub2(v3, v2), v2);
+  const float2 y0z1 = __ffma2_rn(fx, sub2(v5, v4), v4);
+  const float2 y1z1 = __ffma2_rn(fx, sub2(v7, v6), v6);
+  const float2 z0 = __ffma2_rn(fy, sub2(y1z0, y0z0), y0z0);
+  const float2 z1 = __ffma2_rn(fy, sub2(y1z1, y0z1), y0z1);
+  const float2 r = __ffma2_rn(fz, sub2(z1, z0), z0);
+  return make_float2(ina ? r.x : g.penalty, inb ? r.y : g.penalty);
+}
+
 // Element stride of one atom type's map in a given mode (plain: nodes;
 // corner: cells).
 __host__ __device__ inline int type_stride(int mode, const GridConst &g) {
