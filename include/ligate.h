@@ -425,9 +425,10 @@ ligate_status ligate_autotune(const ligate_pocket *pocket, const ligate_batch *b
 /* Analytic launch model (paper Sec. 3.3: a batch shape per ligand size),
  * chosen without timing anything.  Shape: the CTA size and register cap
  * that keep the most warps resident on one SM under the register file and
- * shared-memory limits (for the plain FP32 layout only among the 128-register
- * instances: its eight scalar gathers per interpolation need registers for
- * loads in flight).  Chunk of size bucket b (the work model, also used by
+ * shared-memory limits, among the kernel instances that do not spill
+ * registers to local memory (for the plain FP32 layout only the
+ * 128-register instances: its eight scalar gathers per interpolation need
+ * registers for loads in flight).  Chunk of size bucket b (the work model, also used by
  * every plan for zero chunk fields): starts_per_item[b] = W / (8 P c_b)
  * clamped to [128, 2048] and rounded down to the start group, with W the
  * run's total work (sum over ligands of starts x per-start cost atoms +

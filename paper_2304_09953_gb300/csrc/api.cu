@@ -1408,6 +1408,7 @@ extern "C" ligate_status ligate_model_tile(const ligate_pocket *P, const ligate_
   int best_res = 0;
   for (int cap = 1; cap <= 3; ++cap) {
     if (mode == MODE_F32_PLAIN && cap != 3) continue;
+    if (cap < 3 && dock_kernel_local_bytes(mode, cap) > 0) continue;  // spills: registers too tight
     const int minb = cap == 1 ? 6 : cap == 2 ? 5 : 4;  // CTAs of 128 threads the register cap allows
     for (int warps : {2, 4}) {
       const size_t cta_smem = per_warp * warps + 1024;  // + the per-CTA reserve

@@ -505,6 +505,12 @@ cudaError_t launch_dock(int mode, int reg_cap, const DockParams &p, int grid, in
   return cudaLaunchKernel(dock_fn(mode, reg_cap), dim3(grid), dim3(block), args, smem, s);
 }
 
+size_t dock_kernel_local_bytes(int mode, int reg_cap) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, dock_fn(mode, reg_cap)) != cudaSuccess) return 0;
+  return a.localSizeBytes;
+}
+
 int dock_kernel_max_ctas_per_sm(int mode, int reg_cap, int block, size_t smem) {
   int n = 0;
   const void *f = dock_fn(mode, reg_cap);

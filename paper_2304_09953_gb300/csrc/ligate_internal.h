@@ -213,6 +213,8 @@ cudaError_t launch_score_poses(int mode, const DockParams &p, int n_poses, const
                                const int32_t *start_id, const uint8_t *tors, float *out,
                                cudaStream_t s);
 int dock_kernel_max_ctas_per_sm(int mode, int reg_cap, int block, size_t smem);
+// Local (spill) memory per thread of a kernel instance, in bytes.
+size_t dock_kernel_local_bytes(int mode, int reg_cap);
 
 // Pocket kernels (pocket.cu).
 cudaError_t launch_corner_pack(const float *plain, int n_types, int nx, int ny, int nz,
