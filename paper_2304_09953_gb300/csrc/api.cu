@@ -335,16 +335,26 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
       if (dist[j] >= 4) P.elig[(size_t)s * P.words + (j >> 5)] |= 1u << (j & 31);
   }
   // clash candidates of each bond: moved atom i (v < i < end) x fixed atom j
-  // (outside [v, end), j != u), at least 4 bonds apart
+  // (outside [v, end), j != u), at least 4 bonds apart; first those whose j
+  // no earlier bond separates from the moved subtree (an earlier bond e
+  // separates j when exactly one of j and v lies in e's subtree [v_e, end_e))
   P.cand.clear();
-  for (auto &r : br) {
+  std::vector<uint16_t> rest;
+  for (size_t bi = 0; bi < br.size(); ++bi) {
+    BondRec &r = br[bi];
     r.cand_off = (int)P.cand.size();
+    rest.clear();
     for (int i = r.v + 1; i < r.end; ++i)
       for (int j = 0; j < n; ++j) {
         if ((j >= r.v && j < r.end) || j == r.u) continue;
-        if (P.elig[(size_t)i * P.words + (j >> 5)] >> (j & 31) & 1u)
-          P.cand.push_back((uint16_t)(i | (j << 8)));
+        if (!(P.elig[(size_t)i * P.words + (j >> 5)] >> (j & 31) & 1u)) continue;
+        bool fixed_geometry = true;
+        for (size_t e = 0; e < bi && fixed_geometry; ++e)
+          fixed_geometry = (j >= br[e].v && j < br[e].end) == (r.v >= br[e].v && r.v < br[e].end);
+        (fixed_geometry ? P.cand : rest).push_back((uint16_t)(i | (j << 8)));
       }
+    r.n_cand0 = (int)P.cand.size() - r.cand_off;
+    P.cand.insert(P.cand.end(), rest.begin(), rest.end());
     r.n_cand = (int)P.cand.size() - r.cand_off;
   }
   P.bonds = br;
@@ -595,6 +605,7 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   p.rescore = s->rescore_fp32 ? 1 : 0;
   p.nmax = std::max(32, (B->d.max_atoms + 31) / 32 * 32);
   p.wmax = p.nmax / 32;
+  p.rmax = B->d.max_rot;
   std::vector<float> qf(4 * (size_t)s->n_orient);
   for (size_t i = 0; i < qf.size(); ++i) qf[i] = (float)s->orientations[i];
   CK(dmalloc(quat, qf.size()), "quaternions");
@@ -736,12 +747,12 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   t.warps_per_cta = std::max(1, std::min(4, t.warps_per_cta));
   if (t.reg_cap < 0 || t.reg_cap > 3) t.reg_cap = 0;
   {  // fewer warps per CTA when large ligands or many start groups need more shared memory
-    const size_t per_warp = dock_smem_per_warp(p.nmax, p.S, p.G);
+    const size_t per_warp = dock_smem_per_warp(p.nmax, p.S, p.G, p.rmax);
     const int fit = (int)std::max<size_t>(1, (size_t)(227 * 1024) / per_warp);
     t.warps_per_cta = std::min(t.warps_per_cta, fit);
   }
   pl->block = 32 * t.warps_per_cta;
-  pl->smem = dock_smem_per_warp(p.nmax, p.S, p.G) * t.warps_per_cta;
+  pl->smem = dock_smem_per_warp(p.nmax, p.S, p.G, p.rmax) * t.warps_per_cta;
   if (pl->smem > 227 * 1024) {
     free_plan(pl);
     set_error("plan_create: %zu B shared memory per CTA exceeds 227 KB; use fewer warps", pl->smem);
@@ -1402,7 +1413,7 @@ extern "C" ligate_status ligate_model_tile(const ligate_pocket *P, const ligate_
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   const int S = s->torsion_steps, G = 32 / pow2ceil(S);
   const int nmax = std::max(32, (B->d.max_atoms + 31) / 32 * 32);
-  const size_t per_warp = dock_smem_per_warp(nmax, S, G);
+  const size_t per_warp = dock_smem_per_warp(nmax, S, G, B->d.max_rot);
   ligate_tile t;
   memset(&t, 0, sizeof(t));
   int best_res = 0;

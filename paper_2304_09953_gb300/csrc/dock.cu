@@ -25,7 +25,7 @@
 
 namespace ligate {
 
-size_t dock_smem_per_warp(int nmax, int S, int G) { return smem_bytes_per_warp(nmax, S, G); }
+size_t dock_smem_per_warp(int nmax, int S, int G, int rmax) { return smem_bytes_per_warp(nmax, S, G, rmax); }
 
 // Clash part of the sweep of bond br at this lane's torsion step (ck, sk):
 // the sum over the bond's crossing candidate pairs of max(0, 1 - d^2/d_c^2)^2
@@ -130,7 +130,9 @@ __device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem
 
 // Clash sums of the first n_memo bonds' sweeps into w.memo: memo[k] for
 // bond 0 on the input conformation, memo[S + k0 S + k] for bond 1 after
-// bond 0 turned by step k0.  Conformations are posed by start 0's frame
+// bond 0 turned by step k0; and of each later bond b, the sums over its
+// first n_cand0 candidates on the input conformation, memo[memo_row0(S) +
+// (b - memo_bonds(S)) S + k].  Conformations are posed by start 0's frame
 // (the clash term is invariant under the rigid move); group g takes
 // k0 = g, g + G, ...  Warp-collective.
 __device__ void build_memo(const DockParams &p, const WarpSmem &w, float4 *pose, const LigDesc &d,
@@ -155,6 +157,17 @@ __device__ void build_memo(const DockParams &p, const WarpSmem &w, float4 *pose,
       const float ac = clash_sweep(p, w, pose, d, b0, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
       if (g == 0 && k < S) w.memo[k] = ac;
       __syncwarp();
+      for (int b = memo_bonds(S); b < d.n_rot; ++b) {  // the fixed-geometry pairs of later bonds
+        BondRec bb = w.bonds[b];
+        if (bb.n_cand0 == 0) continue;  // warp-uniform
+        bb.n_cand = bb.n_cand0;
+        float mx, my, mz;
+        const float4 qv = pose[bb.v];
+        bond_axis(pose[bb.u], qv, mx, my, mz);
+        const float a0 = clash_sweep(p, w, pose, d, bb, mx, my, mz, qv, ck, sk, g, k, L, G, n_test, n_pair);
+        if (g == 0 && k < S) w.memo[memo_row0(S) + (b - memo_bonds(S)) * S + k] = a0;
+        __syncwarp();
+      }
       continue;
     }
     const int k0 = min(r * G + g, S - 1);  // groups past S repeat the last step
@@ -188,7 +201,7 @@ template <int MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.S, p.G),
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, p.S, p.G, p.rmax),
                                p.nmax, p.G);
   const int L = p.L, G = p.G, S = p.S, K = p.K;
   const int g = lane / L, k = lane - g * L;
@@ -290,8 +303,12 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         float ac;
         if (b < n_memo) {  // looked up: bond 0, or bond 1 after bond 0's step
           ac = k < S ? w.memo[b == 0 ? k : S + (int)(t0 & 0xffu) * S + k] : 0.f;
-        } else {
-          ac = clash_sweep(p, w, pose, d, br, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
+        } else {  // pairs whose geometry earlier steps change, swept live, + the memoised rest
+          BondRec live = br;
+          live.cand_off += br.n_cand0;
+          live.n_cand -= br.n_cand0;
+          ac = clash_sweep(p, w, pose, d, live, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
+          if (br.n_cand0 > 0 && k < S) ac += w.memo[memo_row0(S) + (b - memo_bonds(S)) * S + k];
         }
         const float V = (k < S) ? fmaf(p.clash_w, ac, ag) : INF;
         float best = V;
@@ -420,7 +437,7 @@ __global__ void __launch_bounds__(256) score_poses_kernel(const DockParams p, in
                                                           float *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1), p.nmax, 1);
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0), p.nmax, 1);
   const int pi = blockIdx.x * (blockDim.x >> 5) + warp;
   if (pi >= n_poses) return;
   const int li = lig_idx[pi], sid = start_id[pi];
@@ -535,7 +552,7 @@ static cudaError_t launch_score_t(const DockParams &p, int n_poses, const int32_
                                   const int32_t *start_id, const uint8_t *tors, float *out,
                                   cudaStream_t s) {
   const int warps = 4;
-  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1);
+  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
   cudaError_t e = cudaFuncSetAttribute(score_poses_kernel<MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;

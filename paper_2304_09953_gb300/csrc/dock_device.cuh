@@ -205,7 +205,7 @@ struct WarpSmem {
   float4 *list;    // [PAIR_WARP] clash pairs that survive the circle bound of a bond
   float2 *cab;     // [G][nmax] (axial coordinate, radial distance) about the bond axis
   BondRec *bonds;  // [LIGATE_MAX_ROT]
-  float *memo;     // [memo_floats(S)] clash sums of the first bonds' sweeps
+  float *memo;     // [memo_floats(S, rmax)] clash sums that every start shares
 };
 
 // Surviving clash pairs buffered per warp before they are evaluated for
@@ -218,15 +218,21 @@ constexpr int PAIR_WARP = 192;
 // 0 .. b-1.  Bond 0 therefore sweeps the same conformation for every start
 // and bond 1 one of S conformations: their clash sums are computed once per
 // ligand (S values for bond 0, S x S for bond 1 when S <= 16) and looked up
-// by every start.
+// by every start.  Of a later bond b, the pairs no earlier bond separates
+// (the first n_cand0 candidates) have the same geometry in every start's
+// sweep too: their sums are one row of S values per bond, the rest of the
+// pairs are swept live.
 __host__ __device__ inline int memo_bonds(int S) { return S <= 16 ? 2 : 1; }
-__host__ __device__ inline int memo_floats(int S) {
-  return S <= 0 ? 0 : (S + (memo_bonds(S) == 2 ? S * S : 0) + 3) / 4 * 4;
+__host__ __device__ inline int memo_rows(int S, int rmax) { return rmax > memo_bonds(S) ? rmax - memo_bonds(S) : 0; }
+// first float of the rows of bonds memo_bonds(S), memo_bonds(S) + 1, ...
+__host__ __device__ inline int memo_row0(int S) { return S + (memo_bonds(S) == 2 ? S * S : 0); }
+__host__ __device__ inline int memo_floats(int S, int rmax) {
+  return S <= 0 ? 0 : (memo_row0(S) + memo_rows(S, rmax) * S + 3) / 4 * 4;
 }
 
-__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int S, int G) {
+__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int S, int G, int rmax) {
   return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
-         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)memo_floats(S) * 4;
+         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)memo_floats(S, rmax) * 4;
 }
 
 

@@ -34,11 +34,15 @@ struct LigDesc {
 // subtree of v), and its clash candidates: the pairs (i, j) with i moved by
 // the bond (v < i < end), j on the fixed side (outside [v, end), j != u) and
 // at least 4 bonds apart, stored as i | j << 8 at cand[cand_base + cand_off].
-// Only these pairs change distance while the bond turns.
+// Only these pairs change distance while the bond turns.  The first n_cand0
+// of them have j on the same side of every earlier bond (in sweep order) as
+// the moved subtree: no earlier step changes their geometry in this bond's
+// sweep, so their clash sums are the same for every start.
 struct BondRec {
   int u, v, end, n_cand;
   int cand_off;
-  int pad[3];
+  int n_cand0;
+  int pad[2];
 };
 
 struct BatchDev {
@@ -167,6 +171,7 @@ struct DockParams {
   // shared-memory shape
   int nmax;                // atoms capacity per warp slot (multiple of 32)
   int wmax;                // words per clash-mask row
+  int rmax;                // rotatable bonds of the batch's largest ligand (memo rows)
 };
 
 // cos/sin of the S torsion steps 2 pi k / S (k = 0 exactly (1, 0)), FP64
@@ -202,7 +207,7 @@ cudaError_t launch_refine(int mode, const DockParams &p, const double origin[3],
                           float *energy, float *grad, cudaStream_t s);
 
 // Host launch wrappers (dock.cu).
-size_t dock_smem_per_warp(int nmax, int S, int G);
+size_t dock_smem_per_warp(int nmax, int S, int G, int rmax);
 cudaError_t launch_dock(int mode, int reg_cap, const DockParams &p, int grid, int block, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_start_frames(const double *quat_unused, const float *quat_f32_dev,

@@ -196,9 +196,10 @@ extern "C" ligate_status ligate_dock_noalloc(const ligate_pocket *P, const ligat
   p.out = reinterpret_cast<PoseOut *>(out);
   p.nmax = std::max(32, (bt.max_atoms + 31) / 32 * 32);
   p.wmax = p.nmax / 32;
+  p.rmax = bt.max_rot;
 
   // launch shape: 4 warps per CTA (fewer if shared memory is short), all SMs
-  const size_t per_warp = dock_smem_per_warp(p.nmax, p.S, G);
+  const size_t per_warp = dock_smem_per_warp(p.nmax, p.S, G, p.rmax);
   const int warps = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(227 * 1024) / per_warp));
   const size_t smem = per_warp * warps;
   const int occ = dock_kernel_max_ctas_per_sm(mode, 0, 32 * warps, smem);

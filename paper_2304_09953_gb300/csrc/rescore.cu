@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
   for (int j = threadIdx.x; j < r.n_types * r.n_types; j += blockDim.x) pair[j] = r.pair[j];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const WarpSmem w = warp_smem(slots + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1), p.nmax, 1);
+  const WarpSmem w = warp_smem(slots + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0), p.nmax, 1);
   int cur = -1;
   LigDesc d;
   for (int pi = blockIdx.x * W + warp; pi < n_poses; pi += gridDim.x * W) {
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128) pose_features_kernel(const DockParams p, 
                                                            float *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1), p.nmax, 1);
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0), p.nmax, 1);
   int *hist = reinterpret_cast<int *>(w.list);
   int cur = -1;
   LigDesc d;
@@ -290,7 +290,7 @@ cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t
                                  const int32_t *row_lig, float *out, cudaStream_t s) {
   if (n_poses <= 0) return cudaSuccess;
   const int warps = 4;
-  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1);
+  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(pose_features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -308,7 +308,7 @@ cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t
 
 size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps) {
   return (size_t)r.n_rec * 16 + (size_t)((r.n_types * r.n_types + 1) & ~1) * 8 +
-         (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1);
+         (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
 }
 
 cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,

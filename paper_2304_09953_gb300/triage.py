@@ -53,3 +53,38 @@ def keep_for_recall(pred, truth_scores, target=0.99, top_frac=0.01):
     need = _count(len(top), target)
     r = np.sort(rank[top])[need - 1] if need > 0 else -1
     return (r + 1) / n
+
+
+def calibration_target(n_library, recall_target=0.99, top_frac=0.01, confidence=0.95):
+    """Per-ligand hit rate to calibrate the keep fraction for, so that a
+    library of `n_library` ligands meets `recall_target` with probability
+    `confidence`.
+
+    The library's true top set holds P = ceil(n_library * top_frac) ligands,
+    and it meets the target while at most a = floor(P * (1 - recall_target))
+    of them are missed.  If each is missed independently at rate m, the
+    misses are close to Poisson(P * m); the returned 1 - m is the rate whose
+    Poisson tail P(misses > a) equals 1 - confidence.  A small library needs
+    a wide margin (100 true top ligands: 0.9964), a large one almost none
+    (10,000: about 0.9916)."""
+    P = _count(n_library, top_frac)
+    if P == 0:
+        return recall_target
+    a = int(math.floor(P * (1.0 - recall_target) + 1e-9))
+
+    def tail(lam):  # P(Poisson(lam) > a), summed in log space
+        if lam <= 0.0:
+            return 0.0
+        logs = [-lam + i * math.log(lam) - math.lgamma(i + 1) for i in range(a + 1)]
+        top = max(logs)
+        cdf = math.exp(top) * sum(math.exp(v - top) for v in logs)
+        return max(0.0, 1.0 - cdf)
+
+    lo, hi = 0.0, float(a + 1) + 10.0 * math.sqrt(a + 1) + 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if tail(mid) > 1.0 - confidence:
+            hi = mid
+        else:
+            lo = mid
+    return max(recall_target, 1.0 - lo / P)
