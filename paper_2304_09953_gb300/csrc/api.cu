@@ -335,28 +335,48 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
       if (dist[j] >= 4) P.elig[(size_t)s * P.words + (j >> 5)] |= 1u << (j & 31);
   }
   // clash candidates of each bond: moved atom i (v < i < end) x fixed atom j
-  // (outside [v, end), j != u), at least 4 bonds apart; first those whose j
-  // no earlier bond separates from the moved subtree (an earlier bond e
-  // separates j when exactly one of j and v lies in e's subtree [v_e, end_e))
+  // (outside [v, end), j != u), at least 4 bonds apart; ordered by the
+  // earlier bonds that separate j from the moved subtree (an earlier bond e
+  // separates j when exactly one of j and v lies in e's subtree [v_e, end_e)):
+  // none, then the most frequent single bond e1, then the rest
   P.cand.clear();
-  std::vector<uint16_t> rest;
+  std::vector<uint16_t> one, rest;
+  std::vector<int> sep_by, n_by(br.size());
   for (size_t bi = 0; bi < br.size(); ++bi) {
     BondRec &r = br[bi];
     r.cand_off = (int)P.cand.size();
+    one.clear();
     rest.clear();
+    sep_by.clear();
+    std::fill(n_by.begin(), n_by.end(), 0);
     for (int i = r.v + 1; i < r.end; ++i)
       for (int j = 0; j < n; ++j) {
         if ((j >= r.v && j < r.end) || j == r.u) continue;
         if (!(P.elig[(size_t)i * P.words + (j >> 5)] >> (j & 31) & 1u)) continue;
-        bool fixed_geometry = true;
-        for (size_t e = 0; e < bi && fixed_geometry; ++e)
-          fixed_geometry = (j >= br[e].v && j < br[e].end) == (r.v >= br[e].v && r.v < br[e].end);
-        (fixed_geometry ? P.cand : rest).push_back((uint16_t)(i | (j << 8)));
+        int nsep = 0, last = -1;
+        for (size_t e = 0; e < bi; ++e)
+          if ((j >= br[e].v && j < br[e].end) != (r.v >= br[e].v && r.v < br[e].end)) { ++nsep; last = (int)e; }
+        const uint16_t c = (uint16_t)(i | (j << 8));
+        if (nsep == 0) {
+          P.cand.push_back(c);
+        } else {
+          one.push_back(c);
+          sep_by.push_back(nsep == 1 ? last : -1);
+          if (nsep == 1) ++n_by[last];
+        }
       }
     r.n_cand0 = (int)P.cand.size() - r.cand_off;
+    r.e1 = -1;
+    for (size_t e = 0; e < bi; ++e)
+      if (n_by[e] > 0 && (r.e1 < 0 || n_by[e] > n_by[r.e1])) r.e1 = (int)e;
+    for (size_t q = 0; q < one.size(); ++q)
+      (sep_by[q] >= 0 && sep_by[q] == r.e1 ? P.cand : rest).push_back(one[q]);
+    r.n_cand1 = (int)P.cand.size() - r.cand_off - r.n_cand0;
     P.cand.insert(P.cand.end(), rest.begin(), rest.end());
     r.n_cand = (int)P.cand.size() - r.cand_off;
   }
+  for (size_t bi = 2, slot = 0; bi < br.size(); ++bi)  // table slots of bonds 2, 3, ...
+    if (br[bi].n_cand1 > 0) br[bi].e1 |= (int)(slot++) << 16;
   P.bonds = br;
   return LIGATE_OK;
 }
@@ -653,6 +673,7 @@ struct ligate_plan {
 
 static void free_plan(ligate_plan *pl) {
   if (!pl) return;
+  cudaFree(pl->p.memo1);
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
@@ -847,6 +868,18 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
       (n && (e = cudaMemcpy(pl->lig_slot0, lig_slot0.data(), 4 * (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess)) {
     free_plan(pl);
     return cuda_fail(e, "plan upload");
+  }
+  {  // per resident warp: the clash tables of the pairs a single earlier bond separates
+    int m1 = 0;
+    for (int r = 0; r < n; ++r) {
+      const LigDesc &ld = B->d.h_lig[sel ? sel[r] : r];
+      m1 = std::max(m1, dock_memo1_tables(ld, B->d.h_bonds.data() + ld.bond_base, p.S));
+    }
+    if (m1 > 0) {
+      const size_t floats = (size_t)pl->grid * t.warps_per_cta * m1 * p.S * p.S;
+      if ((e = dmalloc(&p.memo1, floats)) != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan allocation"); }
+      p.m1max = m1;
+    }
   }
   p.items = pl->items;
   p.n_items = (int)ni;

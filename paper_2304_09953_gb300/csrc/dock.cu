@@ -27,6 +27,12 @@ namespace ligate {
 
 size_t dock_smem_per_warp(int nmax, int S, int G, int rmax) { return smem_bytes_per_warp(nmax, S, G, rmax); }
 
+int dock_memo1_tables(const LigDesc &d, const BondRec *bonds, int) {
+  int n = 0;
+  for (int b = 2; b < d.n_rot; ++b) n += bonds[b].n_cand1 > 0;
+  return n;
+}
+
 // Clash part of the sweep of bond br at this lane's torsion step (ck, sk):
 // the sum over the bond's crossing candidate pairs of max(0, 1 - d^2/d_c^2)^2
 // on the group's conformation `pose` (grid units; axis n through pv).
@@ -55,7 +61,12 @@ __device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem
     const float fx = xj.x - pv.x, fy = xj.y - pv.y, fz = xj.z - pv.z;
     const float a = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
     const float wx = fmaf(-a, nx, fx), wy = fmaf(-a, ny, fy), wz = fmaf(-a, nz, fz);
-    cab[j] = make_float2(a, sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz))));
+    // radial distance by the hardware square-root approximation (relative
+    // error ~1e-7): it only feeds the survivor test, whose threshold carries
+    // a 1e-4 margin, and the pair coefficients' squared radii
+    float rb;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(rb) : "f"(fmaf(wx, wx, fmaf(wy, wy, wz * wz))));
+    cab[j] = make_float2(a, rb);
   }
   __syncwarp();
   auto flush = [&]() {
@@ -132,14 +143,57 @@ __device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem
 // bond 0 on the input conformation, memo[S + k0 S + k] for bond 1 after
 // bond 0 turned by step k0; and of each later bond b, the sums over its
 // first n_cand0 candidates on the input conformation, memo[memo_row0(S) +
-// (b - memo_bonds(S)) S + k].  Conformations are posed by start 0's frame
-// (the clash term is invariant under the rigid move); group g takes
-// k0 = g, g + G, ...  Warp-collective.
+// (b - memo_bonds(S)) S + k]; and, when m1 is given, of each bond b >= 2
+// with pairs that bond e1 alone separates, the sums over those pairs after
+// e1 turned by step t, m1[(slot S + t) S + k] (e1 and slot packed in e1).
+// Conformations are posed by start 0's frame (the clash term is invariant
+// under the rigid move); group g takes k0 = g, g + G, ...  Warp-collective.
 __device__ void build_memo(const DockParams &p, const WarpSmem &w, float4 *pose, const LigDesc &d,
-                           int n_memo, float ck, float sk, int g, int k, int L, int G, int S) {
+                           int n_memo, float ck, float sk, int g, int k, int L, int G, int S,
+                           float *__restrict__ m1) {
   unsigned n_test = 0, n_pair = 0;  // not counted: once per ligand
   float R[9], T[3];
   start_frame(p, 0, R, T);
+  if (m1) {
+    for (int b = 2; b < d.n_rot; ++b) {
+      BondRec bb = w.bonds[b];
+      if (bb.n_cand1 == 0) continue;  // warp-uniform
+      const int slot = bb.e1 >> 16;
+      const BondRec be = w.bonds[bb.e1 & 0xffff];
+      bb.cand_off += bb.n_cand0;
+      bb.n_cand = bb.n_cand1;
+      for (int r = 0; r < (S + G - 1) / G; ++r) {
+        const int te = min(r * G + g, S - 1);  // groups past S repeat the last step
+        for (int i = k; i < d.n_atoms; i += L) {
+          const float4 a = w.ref[i];
+          pose[i] = make_float4(fmaf(R[0], a.x, fmaf(R[1], a.y, fmaf(R[2], a.z, T[0]))),
+                                fmaf(R[3], a.x, fmaf(R[4], a.y, fmaf(R[5], a.z, T[1]))),
+                                fmaf(R[6], a.x, fmaf(R[7], a.y, fmaf(R[8], a.z, T[2]))), 0.f);
+        }
+        __syncwarp();
+        float ex, ey, ez;
+        const float4 ev = pose[be.v];
+        bond_axis(pose[be.u], ev, ex, ey, ez);
+        float ce, se;
+        step_cs(p, te, ce, se);
+        Rot re;
+        re.make(ce, se, ex, ey, ez, ev.x, ev.y, ev.z);
+        __syncwarp();
+        for (int i = be.v + 1 + k; i < be.end; i += L) {
+          float4 q = pose[i];
+          re.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+          pose[i] = q;
+        }
+        __syncwarp();
+        float mx, my, mz;
+        const float4 qv = pose[bb.v];
+        bond_axis(pose[bb.u], qv, mx, my, mz);
+        const float a1 = clash_sweep(p, w, pose, d, bb, mx, my, mz, qv, ck, sk, g, k, L, G, n_test, n_pair);
+        if (r * G + g < S && k < S) m1[(slot * S + te) * S + k] = a1;
+        __syncwarp();
+      }
+    }
+  }
   const int rounds = n_memo == 2 ? (S + G - 1) / G : 0;
   for (int r = -1; r < rounds; ++r) {  // r = -1: bond 0 on the input conformation
     for (int i = k; i < d.n_atoms; i += L) {
@@ -211,6 +265,8 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
   if (k < S) step_cs(p, k, ck, sk);
   const int ts = type_stride(MODE, p.g);
   const float INF = __int_as_float(0x7f800000);
+  float *const m1 = p.memo1 ? p.memo1 + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * p.m1max * S * S
+                            : nullptr;
 
   int cur = -1, n_memo = 0;
   LigDesc d;
@@ -228,7 +284,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
       clash_ref = load_ligand(p, w, item.ligand, d, lane);
       cur = item.ligand;
       n_memo = min(d.n_rot, memo_bonds(S));
-      if (n_memo > 0) build_memo(p, w, pose, d, n_memo, ck, sk, g, k, L, G, S);
+      if (n_memo > 0) build_memo(p, w, pose, d, n_memo, ck, sk, g, k, L, G, S, m1);
     }
     top.clear();
     unsigned n_atom = 0, n_test = 0, n_pair = 0;  // work counters of this lane's group
@@ -304,11 +360,22 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         if (b < n_memo) {  // looked up: bond 0, or bond 1 after bond 0's step
           ac = k < S ? w.memo[b == 0 ? k : S + (int)(t0 & 0xffu) * S + k] : 0.f;
         } else {  // pairs whose geometry earlier steps change, swept live, + the memoised rest
+          // the pairs bond e1 alone separates: their sums by e1's chosen
+          // step, loaded before the live sweep and added after it
+          const bool has1 = m1 && b >= 2 && br.n_cand1 > 0;  // warp-uniform
+          float c1 = 0.f;
+          if (has1 && k < S) {
+            const int e1 = br.e1 & 0xffff, q = e1 >> 2;
+            const uint32_t tw = q == 0 ? t0 : q == 1 ? t1 : q == 2 ? t2 : t3;
+            c1 = __ldcg(m1 + ((br.e1 >> 16) * S + ((tw >> (8 * (e1 & 3))) & 0xff)) * S + k);
+          }
           BondRec live = br;
-          live.cand_off += br.n_cand0;
-          live.n_cand -= br.n_cand0;
+          const int skip = br.n_cand0 + (has1 ? br.n_cand1 : 0);
+          live.cand_off += skip;
+          live.n_cand -= skip;
           ac = clash_sweep(p, w, pose, d, live, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
           if (br.n_cand0 > 0 && k < S) ac += w.memo[memo_row0(S) + (b - memo_bonds(S)) * S + k];
+          ac += c1;
         }
         const float V = (k < S) ? fmaf(p.clash_w, ac, ag) : INF;
         float best = V;

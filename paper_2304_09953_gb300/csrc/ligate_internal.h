@@ -34,15 +34,21 @@ struct LigDesc {
 // subtree of v), and its clash candidates: the pairs (i, j) with i moved by
 // the bond (v < i < end), j on the fixed side (outside [v, end), j != u) and
 // at least 4 bonds apart, stored as i | j << 8 at cand[cand_base + cand_off].
-// Only these pairs change distance while the bond turns.  The first n_cand0
-// of them have j on the same side of every earlier bond (in sweep order) as
-// the moved subtree: no earlier step changes their geometry in this bond's
-// sweep, so their clash sums are the same for every start.
+// Only these pairs change distance while the bond turns.  An earlier bond
+// (in sweep order) separates j from the moved subtree when exactly one of
+// them lies in its subtree; only separating bonds' steps change a pair's
+// geometry in this bond's sweep.  The list holds first the n_cand0 pairs no
+// earlier bond separates (the same clash sums for every start), then the
+// n_cand1 pairs that earlier bond e1 alone separates (sums that depend on
+// e1's step only), then the rest.  e1 holds that bond's index in bits 0-15
+// and, from bond 2 on, the ligand's running count of such bonds before this
+// one in bits 16-31 (the bond's table slot); -1 when n_cand1 = 0.
 struct BondRec {
   int u, v, end, n_cand;
   int cand_off;
   int n_cand0;
-  int pad[2];
+  int n_cand1;
+  int e1;
 };
 
 struct BatchDev {
@@ -172,6 +178,9 @@ struct DockParams {
   int nmax;                // atoms capacity per warp slot (multiple of 32)
   int wmax;                // words per clash-mask row
   int rmax;                // rotatable bonds of the batch's largest ligand (memo rows)
+  float *memo1;            // [resident warps][m1max][S][S] clash sums of the pairs one earlier bond
+                           // separates, by that bond's step (null: those pairs are swept live)
+  int m1max;               // tables per warp (bonds with such pairs, largest ligand)
 };
 
 // cos/sin of the S torsion steps 2 pi k / S (k = 0 exactly (1, 0)), FP64
@@ -208,6 +217,9 @@ cudaError_t launch_refine(int mode, const DockParams &p, const double origin[3],
 
 // Host launch wrappers (dock.cu).
 size_t dock_smem_per_warp(int nmax, int S, int G, int rmax);
+// Clash tables of ligand d the docking kernel keeps in memo1 (its swept
+// bonds with pairs a single earlier bond separates).
+int dock_memo1_tables(const LigDesc &d, const BondRec *bonds, int S);
 cudaError_t launch_dock(int mode, int reg_cap, const DockParams &p, int grid, int block, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_start_frames(const double *quat_unused, const float *quat_f32_dev,
