@@ -58,7 +58,7 @@ def executed_flops(work, S):
 # DRAM bytes (read + write) of one full-size launch of the chosen-form kernel,
 # from ncu (profiles/dock_kernel_bf16_batched10k.md), valid only for the
 # kernel source it was captured on (kernel_source_sha).
-TRAFFIC_BYTES = {("4fdd1f443dbe", "batched", 10000): 75772928 + 11272192}
+TRAFFIC_BYTES = {("906aa2549e6b", "batched", 10000): 103095552 + 68539392}
 
 
 def kernel_source_sha():
