@@ -139,31 +139,30 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     # ligands at 10,000) meets 0.99 recall with 95% probability
     cal_target = T.calibration_target(w.ligands.n)
 
-    def crossfit_keep(x, seed, folds=5, target=cal_target):
-        """Keep fraction from out-of-fold predictions: `folds` networks, each
+    def crossfit(x, seed, folds=5, target=cal_target):
+        """Cross-fitted ranker and keep fraction: `folds` networks, each
         trained on the other folds of the training library, predict their own
-        fold; the smallest fraction whose out-of-fold ranking holds `target`
-        of the training library's true top 1% (2,000 ligands at 200,000)."""
+        fold; the keep fraction is the smallest whose out-of-fold ranking
+        holds `target` of the training library's true top 1% (2,000 ligands
+        at 200,000).  The library is ranked by the mean prediction of the
+        same networks, which ranks at least as well as one of them."""
         oof = np.empty(n_tr, np.float32)
         bounds = np.linspace(0, n_tr, folds + 1).astype(int)
+        nets, losses = [], []
         for f in range(folds):
             a, b = int(bounds[f]), int(bounds[f + 1])
             keep_idx = torch.cat([torch.arange(0, a), torch.arange(b, n_tr)]).cuda()
             net = N.ligate_surrogate_create(None, seed + f)
-            try:
-                N.ligate_surrogate_train(net, x[keep_idx].contiguous(), lab[keep_idx].contiguous(),
-                                         len(keep_idx), 20, 1024, 1e-3, seed + f, sh)
-                pv = torch.empty(b - a, dtype=torch.float32, device="cuda")
-                N.ligate_surrogate_predict(net, x[a:b], b - a, pv, sh)
-                oof[a:b] = pv.cpu().numpy()
-            finally:
-                N.ligate_surrogate_destroy(net)
-        return T.keep_for_recall(oof, labels, target)
+            nets.append(net)
+            losses.append(N.ligate_surrogate_train(net, x[keep_idx].contiguous(), lab[keep_idx].contiguous(),
+                                                   len(keep_idx), 20, 1024, 1e-3, seed + f, sh))
+            pv = torch.empty(b - a, dtype=torch.float32, device="cuda")
+            N.ligate_surrogate_predict(net, x[a:b], b - a, pv, sh)
+            oof[a:b] = pv.cpu().numpy()
+        return T.keep_for_recall(oof, labels, target), nets, float(np.mean(losses))
 
-    keep_cal = crossfit_keep(desc_tr, 2000)
-    sur = N.ligate_surrogate_create(None, 1003)
     t1 = time.perf_counter()
-    loss = N.ligate_surrogate_train(sur, desc_tr, lab, n_tr, 20, 1024, 1e-3, 1003, sh)
+    keep_cal, sur, loss = crossfit(desc_tr, 2000)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
 
@@ -176,9 +175,7 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     cp_tr.run(sh)
     N.ligate_plan_best_scores(cp_tr.h, desc_tr, 256, 233, sh)
     cp_tr.close()
-    keep_cal_c = crossfit_keep(desc_tr, 3000)
-    sur_c = N.ligate_surrogate_create(None, 1004)
-    N.ligate_surrogate_train(sur_c, desc_tr, lab, n_tr, 20, 1024, 1e-3, 1004, sh)
+    keep_cal_c, sur_c, _ = crossfit(desc_tr, 3000)
     torch.cuda.synchronize()
     del desc_tr, lab
     tb.close()
@@ -193,7 +190,7 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
 
         def step():
             N.ligate_descriptors(bh.h, desc, sh)
-            N.ligate_surrogate_rank(sur, desc, n, keep, idx_dev, None, sh)
+            N.ligate_surrogate_rank_ensemble(sur, desc, n, keep, idx_dev, None, sh)
             sel = idx_dev[:k].cpu().numpy()
             pl = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile, subset=sel)
             pl.result(sh)
@@ -212,8 +209,8 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
 
     k, sel, t = timed(args.keep_frac)
     truth_scores = plain.result(sh)["score"][:, 0]
-    N.ligate_surrogate_rank(sur, desc, n, args.keep_frac, torch.empty(max(k, 1), dtype=torch.int32,
-                            device="cuda"), pred_all, sh)
+    N.ligate_surrogate_rank_ensemble(sur, desc, n, args.keep_frac, torch.empty(max(k, 1), dtype=torch.int32,
+                                     device="cuda"), pred_all, sh)
     pred = pred_all.cpu().numpy()
     rec = T.recall(truth_scores, sel)
     flex = np.argsort(-w.ligands.n_rot, kind="stable")[:k]
@@ -224,11 +221,13 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
                             T.recall_curve(pred, truth_scores, [0.05, 0.1, 0.2, 0.3, 0.5, 0.7]).items()},
            "keep_needed_on_library_for_0.99": round(T.keep_for_recall(pred, truth_scores, 0.99), 4),
            "recall_target": 0.99, "meets_target": rec >= 0.99,
-           "train_ligands": n_tr, "calibration": "5-fold cross-fitting on the training library",
+           "train_ligands": n_tr, "calibration": "5-fold cross-fitting on the training library; "
+                                                  "ranked by the mean of the 5 fold networks",
            "calibration_hit_rate": round(cal_target, 5),
            "train_epochs": 20,
            "final_train_loss": loss, "label_docking_s": round(t_label, 2), "train_s": round(t_train, 2),
-           "form": "descriptors + MLP rank (bf16 tensor cores) + dock kept fraction (bf16 maps, fp32 rescore)"}
+           "form": "descriptors + MLP ensemble rank (bf16 tensor cores) + dock kept fraction (bf16 maps, fp32 "
+                   "rescore)"}
     if keep_cal < 1.0:
         kc, selc, tc = timed(keep_cal)
         recc = T.recall(truth_scores, selc)
@@ -242,7 +241,8 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     else:
         out["at_calibrated_keep"] = {"keep_frac": 1.0, "note": "calibration needs the whole library: "
                                      "triage gives no speed-up at 0.99 recall"}
-    N.ligate_surrogate_destroy(sur)
+    for h in sur:
+        N.ligate_surrogate_destroy(h)
 
     # coarse docking + network
     cplan = D.Plan(ph, bh, coarse_s, mode="bf16", rescore=False)
@@ -255,7 +255,7 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
             N.ligate_descriptors(bh.h, desc, sh)
             N.ligate_plan_run(cplan.h, None, sh)
             N.ligate_plan_best_scores(cplan.h, desc, 256, 233, sh)
-            N.ligate_surrogate_rank(sur_c, desc, n, keep, idx_dev, pred_all, sh)
+            N.ligate_surrogate_rank_ensemble(sur_c, desc, n, keep, idx_dev, pred_all, sh)
             sel = idx_dev[:k].cpu().numpy()
             pl = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile, subset=sel)
             pl.result(sh)
@@ -292,7 +292,8 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
                                         "keep_frac": round(keep_cal_c, 4), "docked_per_step": kcc,
                                         "recall_top1pct": recc, "meets_target": recc >= 0.99}
     cplan.close()
-    N.ligate_surrogate_destroy(sur_c)
+    for h in sur_c:
+        N.ligate_surrogate_destroy(h)
     out["with_coarse_docking"] = coarse
     return out
 
@@ -665,12 +666,15 @@ def main():
         n_rec = int(len(w.pocket.receptor_type))
         rescore = {"value": ws * n_poses / (smean / 1000), "unit": "poses rescored/s", "ms_per_step": smean,
                    "poses": n_poses, "receptor_atoms": n_rec,
-                   "pair_terms_per_s": ws * K * float(np.sum(np.diff(w.ligands.atom_offset))) * n_rec
+                   # the exact term's definition sums over every receptor atom (those beyond the
+                   # cutoff add zero); the kernel visits only the 3 x 3 x 3 cells around each atom
+                   "defined_pair_terms_per_s": ws * K * float(np.sum(np.diff(w.ligands.atom_offset))) * n_rec
                    / (smean / 1000),
                    "pass_frac": float(np.mean(rs["pass"] == 1)),
                    "ligands_with_passing_pose": float(np.mean(bidx >= 0)),
                    "form": "exact receptor pair potential (no interpolation) + clash, filter: inside box, "
-                           "no capped atom; receptor staged in shared memory, one warp per pose"}
+                           "no capped atom; receptor sorted into cutoff-wide cells and staged in shared "
+                           "memory, one warp per pose"}
         del sbuf
 
     selector = None

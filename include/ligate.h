@@ -481,6 +481,15 @@ ligate_status ligate_surrogate_predict(const ligate_surrogate *s, const float *d
 ligate_status ligate_surrogate_rank(const ligate_surrogate *s, const float *desc, int n,
                                     double keep_frac, int32_t *idx_out, float *pred_out,
                                     void *stream);
+/* The same ranking by the mean prediction of n_nets networks (host array
+ * nets[n_nets], n_nets >= 1), e.g. the networks of a cross-fitted keep
+ * fraction, each trained without one fold of the training library (paper
+ * Sec. 3.5 keeps a predicted top fraction; the ensemble is what that
+ * fraction was calibrated on, out of fold).  pred_out (DEVICE, optional)
+ * receives the mean predictions.  INVALID on a NULL network or n_nets < 1. */
+ligate_status ligate_surrogate_rank_ensemble(const ligate_surrogate *const *nets, int n_nets,
+                                             const float *desc, int n, double keep_frac,
+                                             int32_t *idx_out, float *pred_out, void *stream);
 
 /* Low-level pieces of one training step, exposed for gradient checks:
  * forward + MSE + backward of one mini-batch on standardised DEVICE inputs

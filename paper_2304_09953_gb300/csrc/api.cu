@@ -148,6 +148,7 @@ extern "C" void ligate_pocket_destroy(ligate_pocket *p) {
   cudaFree(p->d.anchors);
   cudaFree(p->d.rec);
   cudaFree(p->d.rec_pair);
+  cudaFree(p->d.rec_cell);
   delete p;
 }
 
@@ -181,6 +182,43 @@ extern "C" ligate_status ligate_pocket_set_receptor(ligate_pocket *P, const floa
                          (float)(((double)xyz[3 * j + 1] - P->d.origin[1]) / h),
                          (float)(((double)xyz[3 * j + 2] - P->d.origin[2]) / h), tb);
   }
+  // cell grid over the receptor: per axis n_c = floor(extent / (1.001
+  // cutoff)) cells (1 to 16), each at least the cutoff wide with a margin
+  // for FP32 rounding of the cell index on the device; the extent is padded
+  // so no atom sits on the far face
+  const double cut_g = (double)cutoff / h;
+  int nc[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, wd[3] = {1, 1, 1};
+  for (int a = 0; a < 3 && n > 0; ++a) {
+    double mn = 1e300, mx = -1e300;
+    for (int j = 0; j < n; ++j) {
+      const double x = a == 0 ? rec[j].x : a == 1 ? rec[j].y : rec[j].z;
+      mn = std::min(mn, x);
+      mx = std::max(mx, x);
+    }
+    const double ext = (mx - mn) * (1.0 + 1e-6) + 1e-3;
+    nc[a] = (int)std::max(1.0, std::min(16.0, std::floor(ext / (1.001 * cut_g))));
+    lo[a] = mn;
+    wd[a] = ext / nc[a];
+  }
+  const int ncells = nc[0] * nc[1] * nc[2];
+  std::vector<int> cell_of((size_t)n), start((size_t)ncells + 1, 0);
+  for (int j = 0; j < n; ++j) {
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+      const double x = a == 0 ? rec[j].x : a == 1 ? rec[j].y : rec[j].z;
+      c[a] = std::min(nc[a] - 1, std::max(0, (int)std::floor((x - lo[a]) / wd[a])));
+    }
+    cell_of[j] = (c[2] * nc[1] + c[1]) * nc[0] + c[0];
+    ++start[cell_of[j] + 1];
+  }
+  for (int c = 0; c < ncells; ++c) start[c + 1] += start[c];
+  {
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    std::vector<float4> sorted((size_t)n);
+    for (int j = 0; j < n; ++j) sorted[fill[cell_of[j]]++] = rec[j];  // stable: input order within a cell
+    rec.swap(sorted);
+  }
   std::vector<float2> pair((size_t)n_types * n_types);
   for (int t = 0; t < n_types; ++t)
     for (int u = 0; u < n_types; ++u) {
@@ -189,17 +227,26 @@ extern "C" ligate_status ligate_pocket_set_receptor(ligate_pocket *P, const floa
     }
   cudaFree(P->d.rec);
   cudaFree(P->d.rec_pair);
+  cudaFree(P->d.rec_cell);
   P->d.rec = nullptr;
   P->d.rec_pair = nullptr;
+  P->d.rec_cell = nullptr;
   P->d.n_rec = 0;
   cudaError_t e;
   if ((n && ((e = dmalloc(&P->d.rec, (size_t)n)) != cudaSuccess ||
              (e = cudaMemcpy(P->d.rec, rec.data(), 16 * (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess)) ||
       (e = dmalloc(&P->d.rec_pair, pair.size())) != cudaSuccess ||
-      (e = cudaMemcpy(P->d.rec_pair, pair.data(), 8 * pair.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
-    cudaFree(P->d.rec); cudaFree(P->d.rec_pair);
-    P->d.rec = nullptr; P->d.rec_pair = nullptr;
+      (e = cudaMemcpy(P->d.rec_pair, pair.data(), 8 * pair.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = dmalloc(&P->d.rec_cell, start.size())) != cudaSuccess ||
+      (e = cudaMemcpy(P->d.rec_cell, start.data(), 4 * start.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(P->d.rec); cudaFree(P->d.rec_pair); cudaFree(P->d.rec_cell);
+    P->d.rec = nullptr; P->d.rec_pair = nullptr; P->d.rec_cell = nullptr;
     return cuda_fail(e, "pocket_set_receptor");
+  }
+  for (int a = 0; a < 3; ++a) {
+    P->d.rec_nc[a] = nc[a];
+    P->d.rec_lo[a] = (float)lo[a];
+    P->d.rec_inv[a] = (float)(1.0 / wd[a]);
   }
   P->d.n_rec = n;
   P->d.rec_types = n_types;
@@ -1130,6 +1177,10 @@ static ligate_status rec_params(const ligate_pocket *P, const ligate_batch *B, R
     return LIGATE_ERR_INVALID;
   }
   r.rec = P->d.rec; r.pair = P->d.rec_pair; r.n_rec = P->d.n_rec; r.n_types = P->d.rec_types;
+  r.cell = P->d.rec_cell;
+  r.ncx = P->d.rec_nc[0]; r.ncy = P->d.rec_nc[1]; r.ncz = P->d.rec_nc[2];
+  r.lox = P->d.rec_lo[0]; r.loy = P->d.rec_lo[1]; r.loz = P->d.rec_lo[2];
+  r.icx = P->d.rec_inv[0]; r.icy = P->d.rec_inv[1]; r.icz = P->d.rec_inv[2];
   r.cut2 = P->d.rec_cut2; r.cap = P->d.rec_cap; r.rmin2 = P->d.rec_rmin2;
   r.ox = (float)P->d.origin[0]; r.oy = (float)P->d.origin[1]; r.oz = (float)P->d.origin[2];
   r.inv_h = (float)(1.0 / P->d.spacing);

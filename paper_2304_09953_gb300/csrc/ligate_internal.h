@@ -84,20 +84,31 @@ struct PocketDev {
   uint16_t *map_f16c = nullptr;    // corner [T][cells][8]
   size_t n_nodes() const { return (size_t)nx * ny * nz; }
   size_t n_cells() const { return (size_t)(nx - 1) * (ny - 1) * (nz - 1); }
-  // receptor for exact rescoring (ligate_pocket_set_receptor), grid units
+  // receptor for exact rescoring (ligate_pocket_set_receptor), grid units,
+  // sorted by cell of a uniform grid whose cells are at least the cutoff
+  // wide (x fastest), so the atoms within the cutoff of any point lie in
+  // its 3 x 3 x 3 cell neighbourhood and each of its 9 rows of 3 cells is one
+  // contiguous range
   float4 *rec = nullptr;           // [n_rec] (u, type bits)
   float2 *rec_pair = nullptr;      // [rec_types][rec_types] (r0^2 / h^2, eps)
+  int *rec_cell = nullptr;         // [ncells + 1] first atom of each cell
   int n_rec = 0, rec_types = 0;
   float rec_cut2 = 0.f, rec_cap = 0.f, rec_rmin2 = 0.f;  // cutoff^2 / h^2, cap, rmin^2 / h^2
+  int rec_nc[3] = {1, 1, 1};       // cells per axis (at most 16)
+  float rec_lo[3] = {0, 0, 0};     // cell grid origin, grid units
+  float rec_inv[3] = {0, 0, 0};    // 1 / cell width
 };
 
 // Receptor term of the exact rescoring, device view.
 struct RecParams {
   const float4 *rec;
   const float2 *pair;
+  const int *cell;          // [ncx ncy ncz + 1] first atom of each cell
   int n_rec, n_types;
   float cut2, cap, rmin2;
   float ox, oy, oz, inv_h;  // Angstrom -> grid units, for poses given as states
+  int ncx, ncy, ncz;
+  float lox, loy, loz, icx, icy, icz;
 };
 
 // Poses given as continuous states (ligate_pose_state at base + i * stride);

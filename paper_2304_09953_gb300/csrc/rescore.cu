@@ -18,9 +18,12 @@ namespace ligate {
 // receptor term is the maps' pair potential evaluated at each atom:
 // min(cap, sum_j eps_tj ((r0/r)^12 - 2 (r0/r)^6)) over receptor atoms within
 // the cutoff, r floored at rmin (grid units throughout); the clash term is
-// the docking score's.  The CTA stages all receptor atoms in shared memory;
-// each warp takes poses, builds the pose, and for every ligand atom its
-// lanes split the receptor atoms (conflict-free consecutive reads).
+// the docking score's.  The CTA stages all receptor atoms (sorted by cell of
+// a grid whose cells are at least the cutoff wide) and the cells' start
+// offsets in shared memory; each warp takes poses, builds the pose, and for
+// every ligand atom its lanes split the atoms of the 9 rows of 3 cells
+// around it (conflict-free consecutive reads); atoms farther away are
+// beyond the cutoff.
 __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const RecParams r, int n_poses,
                                                      const int32_t *__restrict__ lig_idx,
                                                      const int32_t *__restrict__ start_id,
@@ -30,11 +33,14 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
                                                      const StateSrc ss,
                                                      ligate_rescored *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ncells = r.ncx * r.ncy * r.ncz;
   float4 *rec = reinterpret_cast<float4 *>(smem_raw);
   float2 *pair = reinterpret_cast<float2 *>(rec + r.n_rec);
-  unsigned char *slots = reinterpret_cast<unsigned char *>(pair + ((r.n_types * r.n_types + 1) & ~1));
+  int *cell = reinterpret_cast<int *>(pair + ((r.n_types * r.n_types + 1) & ~1));
+  unsigned char *slots = reinterpret_cast<unsigned char *>(cell + ((ncells + 1 + 3) & ~3));
   for (int j = threadIdx.x; j < r.n_rec; j += blockDim.x) rec[j] = r.rec[j];
   for (int j = threadIdx.x; j < r.n_types * r.n_types; j += blockDim.x) pair[j] = r.pair[j];
+  for (int j = threadIdx.x; j <= ncells; j += blockDim.x) cell[j] = r.cell[j];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const WarpSmem w = warp_smem(slots + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0), p.nmax, 1);
@@ -119,29 +125,45 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
       const float4 u = w.pose[i];
       const int t = __float_as_int(w.ref[i].w);
       const float2 *prow = pair + t * r.n_types;
-      // four receptor atoms per lane per iteration, separate accumulators:
+      // the 3 x 3 x 3 cells around the atom (clamped to the grid; the index
+      // is clamped in floating point first, so far or non-finite coordinates
+      // give an empty neighbourhood or edge cells)
+      const int cx = (int)floorf(fminf(fmaxf((u.x - r.lox) * r.icx, -2.f), (float)r.ncx + 1.f));
+      const int cy = (int)floorf(fminf(fmaxf((u.y - r.loy) * r.icy, -2.f), (float)r.ncy + 1.f));
+      const int cz = (int)floorf(fminf(fmaxf((u.z - r.loz) * r.icz, -2.f), (float)r.ncz + 1.f));
+      const int x0 = max(cx - 1, 0), x1 = min(cx + 1, r.ncx - 1);
+      const int y0 = max(cy - 1, 0), y1 = min(cy + 1, r.ncy - 1);
+      const int z0 = max(cz - 1, 0), z1 = min(cz + 1, r.ncz - 1);
+      // two receptor atoms per lane per iteration, separate accumulators:
       // the per-pair chain (distance, ratio, sixth and twelfth powers) is
       // long, so independent pairs keep the pipes busy
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int j0 = lane; j0 < r.n_rec; j0 += 128) {
+      float acc[2] = {0.f, 0.f};
+      if (x0 <= x1) {
+        for (int z = z0; z <= z1; ++z)
+          for (int y = y0; y <= y1; ++y) {
+            const int row = (z * r.ncy + y) * r.ncx;
+            const int j_hi = cell[row + x1 + 1];
+            for (int j0 = cell[row + x0] + lane; j0 < j_hi; j0 += 64) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = j0 + 32 * q;
-          if (j < r.n_rec) {
-            const float4 a = rec[j];
-            const float dx = u.x - a.x, dy = u.y - a.y, dz = u.z - a.z;
-            float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (d2 <= r.cut2) {
-              d2 = fmaxf(d2, r.rmin2);
-              const float2 pp = prow[__float_as_int(a.w)];
-              const float q2 = __fdividef(pp.x, d2);
-              const float q6 = q2 * q2 * q2;
-              acc[q] = fmaf(pp.y, fmaf(q6, q6, -2.f * q6), acc[q]);
+              for (int q = 0; q < 2; ++q) {
+                const int j = j0 + 32 * q;
+                if (j < j_hi) {
+                  const float4 a = rec[j];
+                  const float dx = u.x - a.x, dy = u.y - a.y, dz = u.z - a.z;
+                  float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                  if (d2 <= r.cut2) {
+                    d2 = fmaxf(d2, r.rmin2);
+                    const float2 pp = prow[__float_as_int(a.w)];
+                    const float q2 = __fdividef(pp.x, d2);
+                    const float q6 = q2 * q2 * q2;
+                    acc[q] = fmaf(pp.y, fmaf(q6, q6, -2.f * q6), acc[q]);
+                  }
+                }
+              }
             }
           }
-        }
       }
-      float accs = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+      float accs = warp_sum(acc[0] + acc[1]);
       if (accs >= r.cap) { accs = r.cap; ++ncap; }
       e_inter += accs;
       nout += !((u.x >= 0.f) & (u.x <= p.g.fx1) & (u.y >= 0.f) & (u.y <= p.g.fy1) & (u.z >= 0.f) &
@@ -307,8 +329,9 @@ cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t
 }
 
 size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps) {
+  const int ncells = r.ncx * r.ncy * r.ncz;
   return (size_t)r.n_rec * 16 + (size_t)((r.n_types * r.n_types + 1) & ~1) * 8 +
-         (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
+         (size_t)((ncells + 1 + 3) & ~3) * 4 + (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
 }
 
 cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,

@@ -446,6 +446,54 @@ extern "C" ligate_status ligate_surrogate_rank(const ligate_surrogate *s, const 
   return r;
 }
 
+namespace {
+__global__ void axpy_kernel(float *__restrict__ acc, const float *__restrict__ x, int n, float a, int first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) acc[i] = first ? a * x[i] : fmaf(a, x[i], acc[i]);
+}
+}  // namespace
+
+extern "C" ligate_status ligate_surrogate_rank_ensemble(const ligate_surrogate *const *nets, int n_nets,
+                                                        const float *desc, int n, double keep_frac,
+                                                        int32_t *idx_out, float *pred_out, void *stream) {
+  NvtxRange nvtx_("ligate:surrogate_rank_ensemble");
+  if (!nets || n_nets < 1 || n < 0 || !(keep_frac >= 0.0 && keep_frac <= 1.0) || (n > 0 && (!desc || !idx_out))) {
+    set_error("surrogate_rank_ensemble: bad argument");
+    return LIGATE_ERR_INVALID;
+  }
+  for (int m = 0; m < n_nets; ++m)
+    if (!nets[m]) { set_error("surrogate_rank_ensemble: network %d is NULL", m); return LIGATE_ERR_INVALID; }
+  if (n == 0) return LIGATE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int k = (int)ceil((double)n * keep_frac - 1e-9);
+  int n2 = 2048;
+  while (n2 < n) n2 <<= 1;
+  float *mean = pred_out, *one = nullptr;
+  unsigned long long *keys = nullptr;
+  cudaError_t e = cudaSuccess;
+  ligate_status r = LIGATE_OK;
+  if ((!pred_out && (e = cudaMalloc(&mean, (size_t)n * 4))) || (e = cudaMalloc(&one, (size_t)n * 4)) ||
+      (e = cudaMalloc(&keys, (size_t)n2 * 8))) {
+    r = cuda_fail(e, "surrogate_rank_ensemble");
+  }
+  // mean = sum_m (1 / n_nets) pred_m, accumulated in network order
+  for (int m = 0; m < n_nets && r == LIGATE_OK; ++m) {
+    r = ligate_surrogate_predict(nets[m], desc, n, one, stream);
+    if (r != LIGATE_OK) break;
+    axpy_kernel<<<(n + 255) / 256, 256, 0, st>>>(mean, one, n, 1.f / (float)n_nets, m == 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) r = cuda_fail(e, "surrogate_rank_ensemble");
+  }
+  if (r == LIGATE_OK) {
+    e = mlp::sort_select(mean, n, k, keys, n2, idx_out, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) r = cuda_fail(e, "surrogate_rank_ensemble");
+  }
+  cudaFree(keys);
+  cudaFree(one);
+  if (!pred_out) cudaFree(mean);
+  return r;
+}
+
 extern "C" ligate_status ligate_surrogate_get_weights(const ligate_surrogate *s, float *out) {
   if (!s || !out) { set_error("surrogate_get_weights: NULL argument"); return LIGATE_ERR_INVALID; }
   cudaError_t e = cudaMemcpy(out, s->w, NPAR * 4, cudaMemcpyDeviceToHost);

@@ -110,6 +110,8 @@ _SIGS = {
                                               ctypes.c_float, ctypes.c_uint64, P, P]),
     "ligate_surrogate_predict": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
     "ligate_surrogate_rank": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_double, P, P, P]),
+    "ligate_surrogate_rank_ensemble": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_double, P, P,
+                                                      P]),
     "ligate_surrogate_grad": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P]),
     "ligate_surrogate_get_weights": (ctypes.c_int, [P, P]),
     "ligate_surrogate_engine": (ctypes.c_int, [P]),
@@ -413,6 +415,13 @@ def ligate_surrogate_predict(h, desc, n, pred, stream=None):
 def ligate_surrogate_rank(h, desc, n, keep_frac, idx_out, pred_out=None, stream=None):
     check(load().ligate_surrogate_rank(h, _ptr(desc), int(n), float(keep_frac), _ptr(idx_out),
                                        _ptr(pred_out), stream), "ligate_surrogate_rank")
+
+
+def ligate_surrogate_rank_ensemble(hs, desc, n, keep_frac, idx_out, pred_out=None, stream=None):
+    arr = (ctypes.c_void_p * len(hs))(*hs)
+    check(load().ligate_surrogate_rank_ensemble(arr, len(hs), _ptr(desc), int(n), float(keep_frac),
+                                                _ptr(idx_out), _ptr(pred_out), stream),
+          "ligate_surrogate_rank_ensemble")
 
 
 def ligate_surrogate_grad(h, x, t, b, grad, stream=None):

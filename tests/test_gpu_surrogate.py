@@ -173,6 +173,37 @@ def test_rank_is_stable_sort_of_predictions():
         N.ligate_surrogate_destroy(s)
 
 
+def test_ensemble_rank_is_the_mean_of_its_networks():
+    rng = np.random.default_rng(9)
+    nets = [N.ligate_surrogate_create(None, 21 + m) for m in range(3)]
+    try:
+        n = 40003
+        desc = torch.from_numpy(rng.normal(size=(n, 256)).astype(np.float32)).cuda()
+        preds = []
+        for h in nets:
+            p = torch.zeros(n, dtype=torch.float32, device="cuda")
+            N.ligate_surrogate_predict(h, desc, n, p)
+            preds.append(p.cpu().numpy())
+        k = int(np.ceil(n * 0.1))
+        idx = torch.zeros(k, dtype=torch.int32, device="cuda")
+        mean = torch.zeros(n, dtype=torch.float32, device="cuda")
+        N.ligate_surrogate_rank_ensemble(nets, desc, n, 0.1, idx, mean)
+        m = mean.cpu().numpy()
+        np.testing.assert_allclose(m, np.mean(preds, axis=0), rtol=2e-6, atol=2e-6 * np.abs(m).max())
+        np.testing.assert_array_equal(idx.cpu().numpy(), np.lexsort((np.arange(n), m))[:k])
+        # one network: the plain ranking, bit for bit
+        idx1 = torch.zeros(k, dtype=torch.int32, device="cuda")
+        idx2 = torch.zeros(k, dtype=torch.int32, device="cuda")
+        N.ligate_surrogate_rank_ensemble(nets[:1], desc, n, 0.1, idx1)
+        N.ligate_surrogate_rank(nets[0], desc, n, 0.1, idx2)
+        assert torch.equal(idx1, idx2)
+        with pytest.raises(N.LigateError):
+            N.ligate_surrogate_rank_ensemble([], desc, n, 0.1, idx1)
+    finally:
+        for h in nets:
+            N.ligate_surrogate_destroy(h)
+
+
 def test_triage_beats_the_method_without_it():
     """Dock 24,000 ligands of the batched library with the FP32 kernel,
     train on 20,000 best scores, rank the 4,000 held out: recall of their
