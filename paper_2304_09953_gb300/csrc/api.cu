@@ -285,17 +285,25 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     snprintf(err, errlen, "ligand %d: %d bonds for %d atoms (a tree needs n-1)", li, nb, n);
     return LIGATE_ERR_INVALID;
   }
-  std::vector<std::vector<int>> adj(n);
+  // adjacency as CSR (atom a's neighbours at nbr[off[a] .. off[a + 1]), ascending)
+  std::vector<int> off(n + 1, 0), nbr(2 * (size_t)nb), fill;
   for (int b = b0; b < b1; ++b) {
     const int x = L->bonds[2 * b], y = L->bonds[2 * b + 1];
     if (x < 0 || y < 0 || x >= n || y >= n || x == y) {
       snprintf(err, errlen, "ligand %d: bond %d has bad atom index", li, b - b0);
       return LIGATE_ERR_INVALID;
     }
-    adj[x].push_back(y);
-    adj[y].push_back(x);
+    ++off[x + 1];
+    ++off[y + 1];
   }
-  for (auto &v : adj) std::sort(v.begin(), v.end());
+  for (int a = 0; a < n; ++a) off[a + 1] += off[a];
+  fill.assign(off.begin(), off.end() - 1);
+  for (int b = b0; b < b1; ++b) {
+    const int x = L->bonds[2 * b], y = L->bonds[2 * b + 1];
+    nbr[fill[x]++] = y;
+    nbr[fill[y]++] = x;
+  }
+  for (int a = 0; a < n; ++a) std::sort(nbr.begin() + off[a], nbr.begin() + off[a + 1]);
   std::vector<int> pos(n, -1), order, parent(n, -1), size(n, 1), stack;
   order.reserve(n);
   stack.push_back(0);
@@ -307,8 +315,8 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     stack.pop_back();
     pos[a] = (int)order.size();
     order.push_back(a);
-    for (int q = (int)adj[a].size() - 1; q >= 0; --q) {  // push descending: pop ascending
-      const int c = adj[a][q];
+    for (int q = off[a + 1] - 1; q >= off[a]; --q) {  // push descending: pop ascending
+      const int c = nbr[q];
       if (c == parent[a]) continue;
       if (seen[c]) { snprintf(err, errlen, "ligand %d: bonds contain a cycle", li); return LIGATE_ERR_INVALID; }
       seen[c] = 1;
@@ -362,24 +370,27 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   }
   std::sort(br.begin(), br.end(), [](const BondRec &a, const BondRec &b) { return a.v < b.v; });
   P.n_rot = (int)br.size();
-  // topological distances in DFS numbering (BFS from every atom)
-  std::vector<std::vector<int>> adjp(n);
-  for (int a = 0; a < n; ++a)
-    for (int c : adj[a]) adjp[pos[a]].push_back(pos[c]);
+  // clash-eligible pairs in DFS numbering: topological distance >= 4, i.e.
+  // every atom but those within 3 bonds (a depth-3 walk on the tree, which
+  // only has to skip the atom it came from)
   P.elig.assign((size_t)n * P.words, 0u);
-  std::vector<int> dist(n), q(n);
-  for (int s = 0; s < n; ++s) {
-    std::fill(dist.begin(), dist.end(), -1);
-    int h = 0, t = 0;
-    q[t++] = s;
-    dist[s] = 0;
-    while (h < t) {
-      const int a = q[h++];
-      for (int c : adjp[a])
-        if (dist[c] < 0) { dist[c] = dist[a] + 1; q[t++] = c; }
+  for (int s0 = 0; s0 < n; ++s0) {  // walk in input numbering, bits in DFS numbering
+    uint32_t *row = P.elig.data() + (size_t)pos[s0] * P.words;
+    for (int w = 0; w < P.words; ++w) row[w] = ~0u;
+    if (n & 31) row[P.words - 1] = (1u << (n & 31)) - 1u;
+    auto near = [row, &pos](int a) { const int q = pos[a]; row[q >> 5] &= ~(1u << (q & 31)); };
+    near(s0);
+    for (int qa = off[s0]; qa < off[s0 + 1]; ++qa) {
+      const int a = nbr[qa];
+      near(a);
+      for (int qb = off[a]; qb < off[a + 1]; ++qb) {
+        const int b = nbr[qb];
+        if (b == s0) continue;
+        near(b);
+        for (int qc = off[b]; qc < off[b + 1]; ++qc)
+          if (nbr[qc] != a) near(nbr[qc]);
+      }
     }
-    for (int j = 0; j < n; ++j)
-      if (dist[j] >= 4) P.elig[(size_t)s * P.words + (j >> 5)] |= 1u << (j & 31);
   }
   // clash candidates of each bond: moved atom i (v < i < end) x fixed atom j
   // (outside [v, end), j != u), at least 4 bonds apart; ordered by the
@@ -388,7 +399,7 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   // none, then the most frequent single bond e1, then the rest
   P.cand.clear();
   std::vector<uint16_t> one, rest;
-  std::vector<int> sep_by, n_by(br.size());
+  std::vector<int> sep_by, n_by(br.size()), nsep_of(n), last_of(n);
   for (size_t bi = 0; bi < br.size(); ++bi) {
     BondRec &r = br[bi];
     r.cand_off = (int)P.cand.size();
@@ -396,20 +407,32 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     rest.clear();
     sep_by.clear();
     std::fill(n_by.begin(), n_by.end(), 0);
+    // separating earlier bonds of every atom j (count, and the last one)
+    std::fill(nsep_of.begin(), nsep_of.end(), 0);
+    std::fill(last_of.begin(), last_of.end(), -1);
+    for (size_t e = 0; e < bi; ++e) {
+      const bool v_in = r.v >= br[e].v && r.v < br[e].end;
+      for (int j = 0; j < n; ++j)
+        if ((j >= br[e].v && j < br[e].end) != v_in) { ++nsep_of[j]; last_of[j] = (int)e; }
+    }
     for (int i = r.v + 1; i < r.end; ++i)
-      for (int j = 0; j < n; ++j) {
-        if ((j >= r.v && j < r.end) || j == r.u) continue;
-        if (!(P.elig[(size_t)i * P.words + (j >> 5)] >> (j & 31) & 1u)) continue;
-        int nsep = 0, last = -1;
-        for (size_t e = 0; e < bi; ++e)
-          if ((j >= br[e].v && j < br[e].end) != (r.v >= br[e].v && r.v < br[e].end)) { ++nsep; last = (int)e; }
-        const uint16_t c = (uint16_t)(i | (j << 8));
-        if (nsep == 0) {
-          P.cand.push_back(c);
-        } else {
-          one.push_back(c);
-          sep_by.push_back(nsep == 1 ? last : -1);
-          if (nsep == 1) ++n_by[last];
+      for (int wd = 0; wd < P.words; ++wd) {
+        // eligible partners of i in this word, minus the moved range and u
+        uint32_t m = P.elig[(size_t)i * P.words + wd];
+        const int lo = std::max(r.v, 32 * wd), hi = std::min(r.end, 32 * wd + 32);
+        if (lo < hi) m &= ~((hi - lo == 32 ? ~0u : (1u << (hi - lo)) - 1u) << (lo - 32 * wd));
+        if ((r.u >> 5) == wd) m &= ~(1u << (r.u & 31));
+        for (; m; m &= m - 1) {  // ascending j
+          const int j = 32 * wd + __builtin_ctz(m);
+          const int nsep = nsep_of[j], last = last_of[j];
+          const uint16_t c = (uint16_t)(i | (j << 8));
+          if (nsep == 0) {
+            P.cand.push_back(c);
+          } else {
+            one.push_back(c);
+            sep_by.push_back(nsep == 1 ? last : -1);
+            if (nsep == 1) ++n_by[last];
+          }
         }
       }
     r.n_cand0 = (int)P.cand.size() - r.cand_off;
