@@ -139,6 +139,28 @@ typedef struct {
   int64_t total_atoms;
 } ligate_batch_info;
 ligate_status ligate_batch_get_info(const ligate_batch *batch, ligate_batch_info *out);
+
+/* How ligand li of L is packed for the docking kernel, on the host only (no
+ * device work; usable without a GPU).  Paper Sec. 2: the torsion sweep turns
+ * the rotatable bonds one by one; the clash term of a bond's sweep only
+ * involves pairs across it, grouped here by the earlier bonds that separate
+ * them (the kernel memoises the first two groups).
+ *   *n_atoms_out, order_out (host int32[n_atoms], optional): the input index
+ *     of the atom at each DFS pre-order position (children by ascending
+ *     input index).
+ *   *n_rot_out, bonds_out (host int32[n_rot][8], optional), in sweep order:
+ *     u, v, end (DFS positions of the fixed-side atom, the child, and one
+ *     past the child's subtree), n_cand, cand_off, n_cand0 (pairs no earlier
+ *     bond separates), n_cand1 (pairs earlier bond e1 alone separates), e1
+ *     (that bond's index in bits 0-15 and, from bond 2 on, its table slot in
+ *     bits 16-31; -1 when n_cand1 = 0).
+ *   cand_out (host uint16[cand_cap], optional): all candidates, i | j << 8
+ *     in DFS positions, bond after bond; *n_cand_out is their count.
+ * INVALID on bad arguments or cand_cap below the count (query the count
+ * with cand_out NULL); the ligand's own errors as ligate_batch_create. */
+ligate_status ligate_inspect_ligand(const ligate_ligands *L, int li, int *n_atoms_out,
+                                    int32_t *order_out, int *n_rot_out, int32_t *bonds_out,
+                                    uint16_t *cand_out, int cand_cap, int *n_cand_out);
 /* Realised rotatable-bond count per ligand (host int32[n_ligands]). */
 ligate_status ligate_batch_rot_counts(const ligate_batch *batch, int32_t *out);
 

@@ -263,6 +263,7 @@ namespace {
 struct LigPack {
   int n = 0, n_rot = 0, words = 0;
   int max_type = 0;
+  std::vector<int> order;  // input index of the atom at each DFS position
   std::vector<float4> atoms;
   std::vector<BondRec> bonds;
   std::vector<uint32_t> elig;
@@ -330,6 +331,7 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   }
   for (int p = n - 1; p > 0; --p) size[parent[order[p]]] += size[order[p]];
   P.n = n;
+  P.order = order;
   P.words = (n + 31) / 32;
   P.atoms.resize(n);
   P.types.resize(n);
@@ -452,6 +454,43 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
 }
 
 }  // namespace
+
+extern "C" ligate_status ligate_inspect_ligand(const ligate_ligands *L, int li, int *n_atoms_out,
+                                              int32_t *order_out, int *n_rot_out, int32_t *bonds_out,
+                                              uint16_t *cand_out, int cand_cap, int *n_cand_out) {
+  if (!L || li < 0 || li >= L->n_ligands || !L->atom_offset || !L->xyz || !L->type || !L->bond_offset ||
+      !L->bonds || !L->rotatable || !n_atoms_out || !n_rot_out || !n_cand_out || cand_cap < 0) {
+    set_error("inspect_ligand: bad argument");
+    return LIGATE_ERR_INVALID;
+  }
+  if (L->atom_offset[li + 1] < L->atom_offset[li] || L->bond_offset[li + 1] < L->bond_offset[li]) {
+    set_error("inspect_ligand: offsets not ascending at ligand %d", li);
+    return LIGATE_ERR_INVALID;
+  }
+  LigPack P;
+  char buf[256];
+  buf[0] = 0;
+  const ligate_status st = pack_one(L, li, P, buf, sizeof(buf));
+  if (st != LIGATE_OK) { set_error("inspect_ligand: %s", buf); return st; }
+  *n_atoms_out = P.n;
+  *n_rot_out = P.n_rot;
+  *n_cand_out = (int)P.cand.size();
+  if (order_out) std::copy(P.order.begin(), P.order.end(), order_out);
+  if (bonds_out)
+    for (int b = 0; b < P.n_rot; ++b) {
+      const BondRec &r = P.bonds[b];
+      const int32_t row[8] = {r.u, r.v, r.end, r.n_cand, r.cand_off, r.n_cand0, r.n_cand1, r.e1};
+      std::copy(row, row + 8, bonds_out + 8 * (size_t)b);
+    }
+  if (cand_out) {
+    if (cand_cap < (int)P.cand.size()) {
+      set_error("inspect_ligand: %zu candidates, cand_cap %d", P.cand.size(), cand_cap);
+      return LIGATE_ERR_INVALID;
+    }
+    std::copy(P.cand.begin(), P.cand.end(), cand_out);
+  }
+  return LIGATE_OK;
+}
 
 extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_batch **out) {
   NvtxRange nvtx_("ligate:batch_create");

@@ -109,6 +109,7 @@ _SIGS = {
     "ligate_surrogate_train": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_float, ctypes.c_uint64, P, P]),
     "ligate_surrogate_predict": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
+    "ligate_inspect_ligand": (ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P, ctypes.c_int, P]),
     "ligate_surrogate_rank": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_double, P, P, P]),
     "ligate_surrogate_rank_ensemble": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_double, P, P,
                                                       P]),
@@ -222,6 +223,22 @@ def ligate_batch_create(lig):
 
 def ligate_batch_destroy(h):
     load().ligate_batch_destroy(h)
+
+
+def ligate_inspect_ligand(lig, li):
+    """Host-only packing of ligand li: (order, bonds [n_rot][8], candidates)."""
+    lib = load()
+    s = make_ligands_struct(lig)
+    na, nr, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    order = np.zeros(LIGATE_MAX_ATOMS, np.int32)
+    bonds = np.zeros((LIGATE_MAX_ROT, 8), np.int32)
+    check(lib.ligate_inspect_ligand(ctypes.byref(s), int(li), ctypes.byref(na), order.ctypes.data,
+                                    ctypes.byref(nr), bonds.ctypes.data, None, 0, ctypes.byref(nc)),
+          "ligate_inspect_ligand")
+    cand = np.zeros(max(nc.value, 1), np.uint16)
+    check(lib.ligate_inspect_ligand(ctypes.byref(s), int(li), ctypes.byref(na), None, ctypes.byref(nr), None,
+                                    cand.ctypes.data, len(cand), ctypes.byref(nc)), "ligate_inspect_ligand")
+    return order[:na.value].copy(), bonds[:nr.value].copy(), cand[:nc.value].copy()
 
 
 def ligate_batch_get_info(h):
