@@ -230,18 +230,20 @@ __host__ __device__ inline int memo_floats(int S, int rmax) {
   return S <= 0 ? 0 : (memo_row0(S) + memo_rows(S, rmax) * S + 3) / 4 * 4;
 }
 
-__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int S, int G, int rmax) {
-  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)PAIR_WARP * 16 +
+// `list` pair-list entries (PAIR_WARP for kernels that sweep clash pairs or
+// keep a histogram there, 0 for those that need neither).
+__host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int S, int G, int rmax, int list = PAIR_WARP) {
+  return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)list * 16 +
          (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)memo_floats(S, rmax) * 4;
 }
 
 
-__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int G) {
+__device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int G, int list = PAIR_WARP) {
   WarpSmem w;
   w.ref = reinterpret_cast<float4 *>(base);
   w.pose = w.ref + nmax;
   w.list = w.pose + (size_t)G * (nmax + 1);
-  w.cab = reinterpret_cast<float2 *>(w.list + PAIR_WARP);
+  w.cab = reinterpret_cast<float2 *>(w.list + list);
   w.bonds = reinterpret_cast<BondRec *>(w.cab + (size_t)G * nmax);
   w.memo = reinterpret_cast<float *>(w.bonds + LIGATE_MAX_ROT);
   return w;

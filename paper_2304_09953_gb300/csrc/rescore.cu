@@ -24,7 +24,7 @@ namespace ligate {
 // every ligand atom its lanes split the atoms of the 9 rows of 3 cells
 // around it (conflict-free consecutive reads); atoms farther away are
 // beyond the cutoff.
-__global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const RecParams r, int n_poses,
+__global__ void __launch_bounds__(256) rescore_kernel(const DockParams p, const RecParams r, int n_poses,
                                                      const int32_t *__restrict__ lig_idx,
                                                      const int32_t *__restrict__ start_id,
                                                      const uint8_t *__restrict__ tors,
@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(128) rescore_kernel(const DockParams p, const 
   for (int j = threadIdx.x; j <= ncells; j += blockDim.x) cell[j] = r.cell[j];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const WarpSmem w = warp_smem(slots + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0), p.nmax, 1);
+  // warp slots without a pair list: more warps per CTA share the staged receptor
+  const WarpSmem w = warp_smem(slots + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0, 0), p.nmax, 1, 0);
   int cur = -1;
   LigDesc d;
   for (int pi = blockIdx.x * W + warp; pi < n_poses; pi += gridDim.x * W) {
@@ -331,7 +332,7 @@ cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t
 size_t rescore_smem_bytes(const DockParams &p, const RecParams &r, int warps) {
   const int ncells = r.ncx * r.ncy * r.ncz;
   return (size_t)r.n_rec * 16 + (size_t)((r.n_types * r.n_types + 1) & ~1) * 8 +
-         (size_t)((ncells + 1 + 3) & ~3) * 4 + (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
+         (size_t)((ncells + 1 + 3) & ~3) * 4 + (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0, 0);
 }
 
 cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses, const int32_t *lig_idx,
@@ -339,7 +340,7 @@ cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses,
                            const int32_t *row_lig, const StateSrc *states, ligate_rescored *out,
                            cudaStream_t s) {
   if (n_poses <= 0) return cudaSuccess;
-  int warps = 4;
+  int warps = 8;
   while (warps > 1 && rescore_smem_bytes(p, r, warps) > 227 * 1024) --warps;
   const size_t smem = rescore_smem_bytes(p, r, warps);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
