@@ -225,7 +225,8 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
                                                   "ranked by the mean of the 5 fold networks",
            "calibration_hit_rate": round(cal_target, 5),
            "train_epochs": 20,
-           "final_train_loss": loss, "label_docking_s": round(t_label, 2), "train_s": round(t_train, 2),
+           "final_train_loss_mean_of_folds": loss, "label_docking_s": round(t_label, 2),
+           "train_s_5_folds": round(t_train, 2),
            "form": "descriptors + MLP ensemble rank (bf16 tensor cores) + dock kept fraction (bf16 maps, fp32 "
                    "rescore)"}
     if keep_cal < 1.0:
