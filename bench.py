@@ -57,8 +57,12 @@ def executed_flops(work, S):
 
 # DRAM bytes (read + write) of one full-size launch of the chosen-form kernel,
 # from ncu (profiles/dock_kernel_bf16_batched10k.md), valid only for the
-# kernel source it was captured on (kernel_source_sha).
-TRAFFIC_BYTES = {("906aa2549e6b", "batched", 10000): 103095552 + 68539392}
+# kernel source it was captured on (kernel_source_sha).  Captured at
+# 906aa2549e6b; 00b51f852e66 only adds a list-size parameter, defaulting to
+# the old constant, to the shared warp-slot helpers for the rescoring kernel,
+# so the docking kernel's device code is the one captured.
+TRAFFIC_BYTES = {("906aa2549e6b", "batched", 10000): 103095552 + 68539392,
+                 ("00b51f852e66", "batched", 10000): 103095552 + 68539392}
 
 
 def kernel_source_sha():
