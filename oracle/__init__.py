@@ -84,6 +84,7 @@ def _load():
         lib.or_refine.argtypes = [P, P, P, I, P, I, D, P, D, P, P, P, P, P, P]
         lib.or_rescore_coords.argtypes = [P, P, P, P, I, P, P, P, P, P, P]
         lib.or_pose_features.argtypes = [P, P, P, I, P, P]
+        lib.or_rescore_atoms.argtypes = [P, P, P, I, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -393,6 +394,29 @@ def rescore_coords(lig, pocket, sampling, receptor, coords):
                              ec.ctypes.data, no.ctypes.data, nc.ctypes.data, sc.ctypes.data):
         raise ValueError("ligand bonds do not form a tree")
     return {"e_inter": ei, "e_clash": ec, "n_outside": no, "n_capped": nc, "scale": sc}
+
+
+def rescore_atoms(lig, pocket, receptor, coords):
+    """Per atom of coordinate sets [n_poses, n_atoms, 3]: the uncapped
+    receptor sum, the sum of its pair-term magnitudes and the signed
+    distance (grid units) to the map box faces, each [n_poses, n_atoms]."""
+    lib = _load()
+    k = _Keep()
+    L = _lig(k, *lig)
+    P = _pock(k, pocket)
+    rx = _c(receptor["xyz"], np.float32)
+    rt = _c(receptor["type"], np.int32)
+    rr = _c(receptor["radius"], np.float64)
+    re = _c(receptor["eps"], np.float64)
+    R = _Rec(len(rx), k.ptr(rx), k.ptr(rt), len(rr), k.ptr(rr), k.ptr(re), float(receptor["cutoff"]),
+             float(receptor["cap"]), float(receptor["rmin"]))
+    x = _c(coords, np.float64)
+    n, na = x.shape[0], x.shape[1]
+    s, m, f = np.zeros((n, na)), np.zeros((n, na)), np.zeros((n, na))
+    if lib.or_rescore_atoms(_ref(L), _ref(P), _ref(R), n, x.ctypes.data, s.ctypes.data, m.ctypes.data,
+                            f.ctypes.data):
+        raise ValueError("ligand bonds do not form a tree")
+    return s, m, f
 
 
 def pose_features(lig, pocket, sampling, coords) -> np.ndarray:

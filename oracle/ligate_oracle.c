@@ -855,6 +855,65 @@ typedef struct {
   double cutoff, cap, rmin;
 } or_receptor_in;
 
+/* Receptor sum at ligand atom x of type t (uncapped, FP64) and the sum of
+ * the magnitudes of its pair terms. */
+static void receptor_sum(const or_receptor_in *rc, int t, const double x[3], double *acc_out, double *mag_out) {
+  const double c2 = rc->cutoff * rc->cutoff;
+  double acc = 0.0, am = 0.0;
+  for (int j = 0; j < rc->n; ++j) {
+    double dx = (double)rc->xyz[3 * j] - x[0], dy = (double)rc->xyz[3 * j + 1] - x[1],
+           dz = (double)rc->xyz[3 * j + 2] - x[2];
+    double d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 > c2) continue;
+    double r = sqrt(d2);
+    if (r < rc->rmin) r = rc->rmin;
+    int tau = rc->type[j];
+    double q = (rc->radius[t] + rc->radius[tau]) / r;
+    double q2 = q * q, q6 = q2 * q2 * q2;
+    double v = sqrt(rc->eps[t] * rc->eps[tau]) * (q6 * q6 - 2.0 * q6);
+    acc += v;
+    am += fabs(v);
+  }
+  *acc_out = acc;
+  *mag_out = am;
+}
+
+/* Signed distance (grid units) of x to the nearest face of the map box
+ * [0, n-1]^3: positive inside, negative outside. */
+static double face_distance(const or_pocket_in *pi, const double x[3]) {
+  const int dims[3] = {pi->nx, pi->ny, pi->nz};
+  double in = 1e300, out = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double u = (x[d] - pi->origin[d]) / pi->h, hi = (double)(dims[d] - 1);
+    double m = u < hi - u ? u : hi - u;
+    if (m < in) in = m;
+    if (m < 0.0 && -m > out) out = -m;
+  }
+  return in >= 0.0 ? in : -out;
+}
+
+/* Per atom of n_poses coordinate sets: the uncapped receptor sum, the sum
+ * of its pair-term magnitudes and the signed distance to the box faces
+ * (outputs [n_poses][n]).  The filter's per-atom inputs, for checks of the
+ * decisions near their thresholds. */
+OR_EXPORT int or_rescore_atoms(const or_ligand_in *li, const or_pocket_in *pi, const or_receptor_in *rc,
+                               int n_poses, const double *coords, double *atom_sum, double *atom_mag,
+                               double *atom_face) {
+  or_lig L;
+  if (lig_init(&L, li->n_atoms, li->xyz, li->type, li->n_bonds, li->bonds, li->rot)) { lig_free(&L); return -1; }
+  const int n = L.n;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int p = 0; p < n_poses; ++p) {
+    const double (*x)[3] = (const double(*)[3])(coords + (size_t)p * n * 3);
+    for (int i = 0; i < n; ++i) {
+      receptor_sum(rc, L.type[i], x[i], atom_sum + (size_t)p * n + i, atom_mag + (size_t)p * n + i);
+      atom_face[(size_t)p * n + i] = face_distance(pi, x[i]);
+    }
+  }
+  lig_free(&L);
+  return 0;
+}
+
 /* For n_poses coordinate sets [n_poses][n][3]: e_inter, e_clash, n_outside,
  * n_capped and scale (sum of absolute values of the per-atom and clash terms,
  * each per-atom term itself counted by the sum of its pair magnitudes when
@@ -868,7 +927,6 @@ OR_EXPORT int or_rescore_coords(const or_ligand_in *li, const or_pocket_in *pi, 
   or_clash C = {sp->clash_w, sp->clash_dc, sp->clash_min_sep};
   const int n = L.n;
   const int dims[3] = {pi->nx, pi->ny, pi->nz};
-  const double c2 = rc->cutoff * rc->cutoff;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int p = 0; p < n_poses; ++p) {
     const double (*x)[3] = (const double(*)[3])(coords + (size_t)p * n * 3);
@@ -881,22 +939,8 @@ OR_EXPORT int or_rescore_coords(const or_ligand_in *li, const or_pocket_in *pi, 
         if (!(u >= 0.0 && u <= (double)(dims[d] - 1))) outside = 1;
       }
       nout += outside;
-      const int t = L.type[i];
-      double acc = 0.0, am = 0.0;
-      for (int j = 0; j < rc->n; ++j) {
-        double dx = (double)rc->xyz[3 * j] - x[i][0], dy = (double)rc->xyz[3 * j + 1] - x[i][1],
-               dz = (double)rc->xyz[3 * j + 2] - x[i][2];
-        double d2 = dx * dx + dy * dy + dz * dz;
-        if (d2 > c2) continue;
-        double r = sqrt(d2);
-        if (r < rc->rmin) r = rc->rmin;
-        int tau = rc->type[j];
-        double q = (rc->radius[t] + rc->radius[tau]) / r;
-        double q2 = q * q, q6 = q2 * q2 * q2;
-        double v = sqrt(rc->eps[t] * rc->eps[tau]) * (q6 * q6 - 2.0 * q6);
-        acc += v;
-        am += fabs(v);
-      }
+      double acc, am;
+      receptor_sum(rc, L.type[i], x[i], &acc, &am);
       if (acc >= rc->cap) { acc = rc->cap; am = rc->cap; ++ncap; }
       ei += acc;
       mag += am;

@@ -75,3 +75,43 @@ def test_clash_part_is_the_docking_clash_term_and_flags(tiny):
     far = x[:1] + 100.0
     rf = oracle.rescore_coords(lig, w.pocket, w.sampling, w.pocket.receptor(), far)
     assert rf["n_outside"][0] == x.shape[1] and rf["e_inter"][0] == 0.0
+
+
+def test_per_atom_inputs_reproduce_the_filter_and_closed_forms(tiny):
+    """rescore_atoms: its per-atom sums, capped and summed, are e_inter; the
+    atoms at or above the cap are n_capped and those with a negative face
+    distance n_outside; one receptor atom at r0 gives -eps with magnitude
+    eps; the face distance is the closed form for points placed by hand."""
+    w = tiny
+    P = w.pocket
+    lig = w.ligands.ligand(0)
+    rec = P.receptor()
+    rng = np.random.default_rng(8)
+    R_n = int(np.sum(lig[3] != 0))
+    starts = rng.integers(0, w.sampling.n_starts, size=40)
+    tors = rng.integers(0, w.sampling.torsion_steps, size=(40, R_n))
+    x = oracle.pose_coords(lig, P.anchors, w.sampling, starts, tors)
+    x[:3] += 30.0 * rng.normal(size=(3, 1, 3))  # some poses leave the box
+    r = oracle.rescore_coords(lig, P, w.sampling, rec, x)
+    s, m, f = oracle.rescore_atoms(lig, P, rec, x)
+    np.testing.assert_allclose(np.minimum(s, P.cap).sum(axis=1), r["e_inter"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal((s >= P.cap).sum(axis=1), r["n_capped"])
+    np.testing.assert_array_equal((f < 0).sum(axis=1), r["n_outside"])
+    assert np.all(m >= np.abs(s) - 1e-12)
+    assert r["n_outside"][:3].sum() > 0 and np.any(r["n_capped"] > 0)
+    # closed forms: one receptor atom; faces of the box
+    radius, eps = np.array([1.6, 1.9]), np.array([0.15, 0.25])
+    one = {"xyz": np.zeros((1, 3), np.float32) + 5.0, "type": np.array([1], np.int32),
+           "radius": radius, "eps": eps, "cutoff": 8.0, "cap": 10.0, "rmin": 0.5}
+    r0 = radius[0] + radius[1]
+    p = np.array([5.0 + r0, 5.0, 5.0])
+    s1, m1, f1 = oracle.rescore_atoms(one_atom(p, 0), P, one, p[None, None, :])
+    np.testing.assert_allclose(s1[0, 0], -np.sqrt(eps[0] * eps[1]), rtol=1e-12)
+    np.testing.assert_allclose(m1[0, 0], np.sqrt(eps[0] * eps[1]), rtol=1e-12)
+    nx, ny, nz = P.dims
+    o, h = np.asarray(P.origin), P.spacing
+    for u, want in (([0.25, 5.0, 7.0], 0.25), ([3.0, ny - 1.5, 9.0], 0.5), ([-0.75, 4.0, 4.0], -0.75),
+                    ([4.0, 4.0, nz - 1 + 2.0], -2.0)):
+        q = o + h * np.array(u)
+        _, _, fq = oracle.rescore_atoms(one_atom(q, 0), P, one, q[None, None, :])
+        np.testing.assert_allclose(fq[0, 0], want, atol=1e-12)
