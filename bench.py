@@ -329,11 +329,11 @@ def run_pose_selector(args, w, ph, chosen, tile, stream, sh, fail_label=30.0):  
     N.ligate_plan_rescore(tp.h, rs, sh)
     torch.cuda.synchronize()
     r = rs.cpu().numpy().view(N.RESCORED_DTYPE)
-    lab = SEL.labels(r, fail_label)
+    lab = SEL.labels(rs, fail_label)
     live = np.isfinite(r["energy"])
     idx = torch.from_numpy(np.nonzero(live)[0]).cuda()
     x_tr = feat[idx].contiguous()
-    y_tr = torch.from_numpy(lab[live]).cuda()
+    y_tr = lab[idx].contiguous()
     sel_net = N.ligate_surrogate_create(None, 77)
     t0 = time.perf_counter()
     N.ligate_surrogate_train(sel_net, x_tr, y_tr, len(idx), 10, 1024, 1e-3, 77, sh)
@@ -364,7 +364,7 @@ def run_pose_selector(args, w, ph, chosen, tile, stream, sh, fail_label=30.0):  
     torch.cuda.synchronize()
     ex = rbuf.cpu().numpy().view(N.RESCORED_DTYPE).reshape(n, K)
     N.ligate_surrogate_destroy(sel_net)
-    best_idx, best_e = D.best_passing(ex)
+    best_idx, best_e = chosen.best_passing(rbuf)
     has = best_idx >= 0
     p_ = np.where(np.isfinite(ex["energy"]), p_, np.inf)
     pick = np.argmin(p_, axis=1)
@@ -379,7 +379,7 @@ def run_pose_selector(args, w, ph, chosen, tile, stream, sh, fail_label=30.0):  
 
     # the selector's rule: the best-docked pose predicted to pass, else the
     # lowest prediction
-    first_ok = SEL.select(p_, np.isfinite(ex["energy"]), fail_label)
+    first_ok = SEL.select(pred.view(n, K), chosen.device_output(), fail_label)
     t = statistics.mean(ms)
     return {"value": n_poses / (t / 1000), "unit": "poses selected/s", "ms_per_step": t,
             "train_ligands": tw.ligands.n, "train_poses": int(live.sum()), "train_s": round(t_train, 2),
@@ -625,8 +625,8 @@ def main():
             torch.cuda.synchronize()
             r0 = b0.cpu().numpy().view(N.RESCORED_DTYPE).reshape(n_lig, K)
             r1 = b1.cpu().numpy().view(N.RESCORED_DTYPE).reshape(n_lig, K)
-            i0, e0 = D.best_passing(r0)
-            i1, e1 = D.best_passing(r1)
+            i0, e0 = chosen.best_passing(b0)
+            i1, e1 = chosen.best_passing(b1)
             both = (i0 >= 0) & (i1 >= 0)
             after = {"pass_frac_docked": float(np.mean(r0["pass"] == 1)),
                      "pass_frac_refined": float(np.mean(r1["pass"] == 1)),
@@ -666,7 +666,7 @@ def main():
             b.synchronize()
             sms.append(a.elapsed_time(b))
         rs = sbuf.cpu().numpy().view(N.RESCORED_DTYPE).reshape(n_lig, K)
-        bidx, _ = D.best_passing(rs)
+        bidx, _ = chosen.best_passing(sbuf)
         smean = statistics.mean(sms)
         n_rec = int(len(w.pocket.receptor_type))
         rescore = {"value": ws * n_poses / (smean / 1000), "unit": "poses rescored/s", "ms_per_step": smean,

@@ -281,18 +281,26 @@ ligate_status ligate_dock_batch(const ligate_pocket *pocket, const ligate_ligand
  * LIGATE_NOALLOC_SCRATCH_BYTES inside the library, so the call allocates
  * nothing on the device or the host heap.  pocket and batch are inputs the
  * caller created earlier; out is DEVICE ligate_pose[n_ligands][top_k].
- * The call only enqueues work on `stream`.
- *  - Every GPU that loads the library holds the array until the process
- *    exits.  The first call on a device looks up the array's device
- *    address (once per device, with that device current); make that first
- *    call before any stream capture.
+ * The call only enqueues work on `stream`; the orientations travel inside
+ * the kernel launches' parameters, so no host buffer must outlive it.
+ *  - The array is reserved on a device when the library's device code for
+ *    this entry point is loaded there.  With CUDA's default lazy module
+ *    loading that happens during the first call on the device (which looks
+ *    up the array's address, once per device, with that device current):
+ *    make that first call before reserving the rest of the device for a
+ *    pool, and before any stream capture, or run with
+ *    CUDA_MODULE_LOADING=EAGER.  Later calls allocate nothing; the array
+ *    stays until the process exits.
  *  - All calls share the array, which keeps the previous call's contents;
  *    each call clears the counters that must start at zero.  Calls whose
  *    GPU work overlaps (other streams, other host threads) race on it.
- *  - Limits: n_orient <= 1024, n_anchor <= 1024, and the run's scratch
- *    (about n_ligands * ceil(starts / 1024) * (16 + 24 * top_k) bytes) must
- *    fit the array; larger requests return LIGATE_ERR_UNSUPPORTED with the
- *    sizes in ligate_last_error(). */
+ *  - Limits: n_orient <= 1024, n_anchor <= 1024, and the run's scratch must
+ *    fit the array: 49,152 B of start frames plus, per ligand,
+ *    12 + ceil(n_orient * n_anchor / C) * (32 + 24 * top_k) B, where C is
+ *    1024 starts rounded down to a multiple of the start group
+ *    (32 / pow2ceil(torsion_steps)), plus up to 1,536 B of alignment.
+ *    Larger requests return LIGATE_ERR_UNSUPPORTED with the sizes in
+ *    ligate_last_error(). */
 #define LIGATE_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 ligate_status ligate_dock_noalloc(const ligate_pocket *pocket, const ligate_batch *batch,
                                   const ligate_sampling *sampling, ligate_pose *out, void *stream);
@@ -305,6 +313,21 @@ ligate_status ligate_score_poses(const ligate_pocket *pocket, const ligate_batch
                                  const ligate_sampling *sampling, int n_poses,
                                  const int32_t *lig_idx, const int32_t *start_id,
                                  const uint8_t *tors, float *out, void *stream);
+
+/* Coordinates of explicit poses, built exactly as the docking, rescoring and
+ * feature kernels build them (paper Sec. 2: a docked pose is the ligand
+ * placed by its rigid start and turned by its torsion steps; this is the
+ * geometry a user writes out for the next stage).  Pose p is ligand
+ * lig_idx[p] at start start_id[p] with steps tors[p][LIGATE_MAX_ROT]; all
+ * four arrays are DEVICE memory.  out: DEVICE FP32
+ * [n_poses][LIGATE_MAX_ATOMS][3] in grid units u = (x - origin) / spacing
+ * (the frame the kernels score in; x = origin + spacing * u in Angstrom),
+ * atoms in the ligand's INPUT order; rows past the ligand's atom count are
+ * not written.  A pose whose ligand or start index is out of range gets NaN
+ * in every row.  Synchronises stream.  Errors as ligate_score_poses. */
+ligate_status ligate_pose_coords(const ligate_pocket *pocket, const ligate_batch *batch,
+                                 const ligate_sampling *sampling, int n_poses, const int32_t *lig_idx,
+                                 const int32_t *start_id, const uint8_t *tors, float *out, void *stream);
 
 /* ------------------------------------------------------------------------
  * Pose refinement by gradient descent (paper Sec. 2: the docking search is a
@@ -413,6 +436,17 @@ ligate_status ligate_rescore_states(const ligate_pocket *pocket, const ligate_ba
 ligate_status ligate_plan_rescore_refined(const ligate_plan *plan, const ligate_refined *refined,
                                           ligate_rescored *out, void *stream);
 
+/* A ligand's result after the filter (paper Sec. 2: the generated poses are
+ * rescored and filtered; a ligand scores as its best pose): for every row r
+ * of the plan's output, the slot k of the lowest energy among the rescored
+ * poses of row r that pass the filter (ties: the smaller k), or -1 when none
+ * passes.  rescored: DEVICE [n_ligands][top_k] as written by
+ * ligate_plan_rescore or ligate_plan_rescore_refined for this plan; idx_out
+ * DEVICE int32 [n_ligands]; energy_out (DEVICE FP32 [n_ligands], optional)
+ * receives that energy (+inf when none passes).  Enqueues on stream. */
+ligate_status ligate_plan_best_passing(const ligate_plan *plan, const ligate_rescored *rescored,
+                                       int32_t *idx_out, float *energy_out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Per-pose selector features (paper Sec. 3.5: a high-throughput pose
  * selector trading a little accuracy for throughput; a learned model on
@@ -431,6 +465,22 @@ ligate_status ligate_pose_features(const ligate_pocket *pocket, const ligate_bat
                                    const ligate_sampling *sampling, int n, const int32_t *lig_idx,
                                    const int32_t *start_id, const uint8_t *tors, float *out, void *stream);
 ligate_status ligate_plan_pose_features(const ligate_plan *plan, float *out, void *stream);
+/* The selector's decision rule (paper Sec. 3.5: keep one pose per ligand
+ * from a learned prediction instead of rescoring every pose).  Per row r of
+ * n rows of k poses in docking order (poses: DEVICE ligate_pose[n][k], a
+ * slot with start_id < 0 is empty; pred: DEVICE FP32 [n][k], the network's
+ * predicted label of each pose): the first non-empty slot whose prediction
+ * is below pass_below (predicted to pass the filter); else the non-empty
+ * slot with the lowest prediction (ties: the smaller slot); -1 for a row
+ * without a pose.  idx_out: DEVICE int32 [n].  Enqueues on stream. */
+ligate_status ligate_select_poses(const float *pred, const ligate_pose *poses, int n, int k,
+                                  float pass_below, int32_t *idx_out, void *stream);
+/* Training label of each rescored pose for the selector network: the exact
+ * energy of a pose that passes the filter, clipped to fail_label, and
+ * fail_label for a pose that fails or an empty slot.  rescored DEVICE [n],
+ * out DEVICE FP32 [n].  Enqueues on stream. */
+ligate_status ligate_selector_labels(const ligate_rescored *rescored, int64_t n, float fail_label,
+                                     float *out, void *stream);
 
 /* ------------------------------------------------------------------------
  * Autotuner (paper Sec. 3.3: per-size batch tuning).  Times the six CTA

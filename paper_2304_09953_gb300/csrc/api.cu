@@ -575,8 +575,10 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   d.h_elig.resize(ne);
   d.h_types.resize(na);
   d.h_cand.resize(nc);
+  d.h_order.resize(na);
   for (int i = 0; i < n; ++i) {
     const LigDesc &ld = d.h_lig[i];
+    for (int q = 0; q < ld.n_atoms; ++q) d.h_order[ld.atom_base + q] = (uint8_t)packs[i].order[q];
     std::copy(packs[i].atoms.begin(), packs[i].atoms.end(), atoms.begin() + ld.atom_base);
     std::copy(packs[i].types.begin(), packs[i].types.end(), d.h_types.begin() + ld.atom_base);
     std::copy(packs[i].bonds.begin(), packs[i].bonds.end(), d.h_bonds.begin() + ld.bond_base);
@@ -586,7 +588,7 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   cudaError_t e;
   if ((e = dmalloc(&d.lig, n)) != cudaSuccess || (e = dmalloc(&d.atoms, na)) != cudaSuccess ||
       (e = dmalloc(&d.bonds, nb)) != cudaSuccess || (e = dmalloc(&d.elig, ne)) != cudaSuccess ||
-      (e = dmalloc(&d.cand, nc)) != cudaSuccess) {
+      (e = dmalloc(&d.cand, nc)) != cudaSuccess || (e = dmalloc(&d.order, na)) != cudaSuccess) {
     ligate_batch_destroy(B);
     return cuda_fail(e, "batch allocation");
   }
@@ -594,7 +596,8 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
       (na && (e = cudaMemcpy(d.atoms, atoms.data(), sizeof(float4) * na, cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (nb && (e = cudaMemcpy(d.bonds, d.h_bonds.data(), sizeof(BondRec) * nb, cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (ne && (e = cudaMemcpy(d.elig, d.h_elig.data(), 4 * ne, cudaMemcpyHostToDevice)) != cudaSuccess) ||
-      (nc && (e = cudaMemcpy(d.cand, d.h_cand.data(), 2 * nc, cudaMemcpyHostToDevice)) != cudaSuccess)) {
+      (nc && (e = cudaMemcpy(d.cand, d.h_cand.data(), 2 * nc, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (na && (e = cudaMemcpy(d.order, d.h_order.data(), na, cudaMemcpyHostToDevice)) != cudaSuccess)) {
     ligate_batch_destroy(B);
     return cuda_fail(e, "batch upload");
   }
@@ -609,6 +612,7 @@ extern "C" void ligate_batch_destroy(ligate_batch *b) {
   cudaFree(b->d.bonds);
   cudaFree(b->d.elig);
   cudaFree(b->d.cand);
+  cudaFree(b->d.order);
   delete b;
 }
 
@@ -743,6 +747,9 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   CK(dmalloc(anc, 3 * (size_t)s->n_anchor), "start frames");
   CK(launch_start_frames(nullptr, *quat, s->n_orient, d.anchors, s->n_anchor, d.origin, d.spacing,
                          *rot, *anc, 0), "start frames");
+  // the frames are read by kernels on the caller's stream, which need not
+  // be ordered after the legacy default stream
+  CK(cudaStreamSynchronize(0), "start frames");
   p.rot = *rot;
   p.anc = *anc;
   return LIGATE_OK;
@@ -1135,6 +1142,32 @@ extern "C" ligate_status ligate_score_poses(const ligate_pocket *P, const ligate
   return LIGATE_OK;
 }
 
+extern "C" ligate_status ligate_pose_coords(const ligate_pocket *P, const ligate_batch *B,
+                                            const ligate_sampling *s, int n_poses, const int32_t *lig_idx,
+                                            const int32_t *start_id, const uint8_t *tors, float *out,
+                                            void *stream) {
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  if (n_poses < 0 || (n_poses > 0 && (!lig_idx || !start_id || !tors || !out))) {
+    set_error("pose_coords: bad pose arrays");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n_poses == 0) return LIGATE_OK;
+  DockParams p;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  st = base_params(P, B, s, mode, p, &rot, &anc, &quat);
+  cudaError_t e = cudaSuccess;
+  if (st == LIGATE_OK) {
+    e = launch_pose_coords(p, B->d.order, n_poses, lig_idx, start_id, tors, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  cudaFree(rot); cudaFree(anc); cudaFree(quat);
+  if (st != LIGATE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "pose_coords");
+  return LIGATE_OK;
+}
+
 __global__ void best_scores_kernel(const PoseOut *__restrict__ poses, int n, int K, float *__restrict__ out,
                                    int stride, int column) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1400,6 +1433,39 @@ extern "C" ligate_status ligate_plan_pose_features(const ligate_plan *pl, float 
   return LIGATE_OK;
 }
 
+extern "C" ligate_status ligate_plan_best_passing(const ligate_plan *pl, const ligate_rescored *rescored,
+                                                  int32_t *idx_out, float *energy_out, void *stream) {
+  if (!pl || ((!rescored || !idx_out) && pl->n_ligands > 0)) {
+    set_error("plan_best_passing: NULL argument");
+    return LIGATE_ERR_INVALID;
+  }
+  cudaError_t e = launch_best_passing(rescored, pl->n_ligands, pl->p.K, idx_out, energy_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "plan_best_passing");
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_select_poses(const float *pred, const ligate_pose *poses, int n, int k,
+                                             float pass_below, int32_t *idx_out, void *stream) {
+  if (n < 0 || k < 1 || (n > 0 && (!pred || !poses || !idx_out)) || !isfinite(pass_below)) {
+    set_error("select_poses: bad arguments");
+    return LIGATE_ERR_INVALID;
+  }
+  cudaError_t e = launch_select_poses(pred, poses, n, k, pass_below, idx_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "select_poses");
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_selector_labels(const ligate_rescored *rescored, int64_t n, float fail_label,
+                                                float *out, void *stream) {
+  if (n < 0 || (n > 0 && (!rescored || !out)) || !isfinite(fail_label)) {
+    set_error("selector_labels: bad arguments");
+    return LIGATE_ERR_INVALID;
+  }
+  cudaError_t e = launch_selector_labels(rescored, (long long)n, fail_label, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "selector_labels");
+  return LIGATE_OK;
+}
+
 // ===========================================================================
 // Autotuner: times the CTA shapes and register caps on a sample of the
 // batch; chunk sizes per size bucket come from the work model when a plan is
@@ -1492,6 +1558,7 @@ static ligate_status sub_batch(const ligate_batch *B, const std::vector<int> &id
     for (int a = 0; a < o.n_atoms; ++a) {
       atoms.push_back(all_atoms[o.atom_base + a]);
       d.h_types.push_back(src.h_types[o.atom_base + a]);
+      d.h_order.push_back(src.h_order[o.atom_base + a]);
     }
     for (int b = 0; b < o.n_rot; ++b) d.h_bonds.push_back(src.h_bonds[o.bond_base + b]);
     for (int w = 0; w < o.n_atoms * o.n_words; ++w) d.h_elig.push_back(src.h_elig[o.elig_base + w]);
@@ -1507,10 +1574,12 @@ static ligate_status sub_batch(const ligate_batch *B, const std::vector<int> &id
       (e = dmalloc(&d.atoms, atoms.size())) != cudaSuccess ||
       (e = dmalloc(&d.bonds, d.h_bonds.size())) != cudaSuccess ||
       (e = dmalloc(&d.elig, d.h_elig.size())) != cudaSuccess ||
-      (e = dmalloc(&d.cand, d.h_cand.size())) != cudaSuccess) {
+      (e = dmalloc(&d.cand, d.h_cand.size())) != cudaSuccess ||
+      (e = dmalloc(&d.order, d.h_order.size())) != cudaSuccess) {
     ligate_batch_destroy(S);
     return cuda_fail(e, "autotune sample");
   }
+  if (!d.h_order.empty()) cudaMemcpy(d.order, d.h_order.data(), d.h_order.size(), cudaMemcpyHostToDevice);
   if (!d.h_cand.empty()) cudaMemcpy(d.cand, d.h_cand.data(), 2 * d.h_cand.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d.lig, d.h_lig.data(), sizeof(LigDesc) * d.h_lig.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d.atoms, atoms.data(), sizeof(float4) * atoms.size(), cudaMemcpyHostToDevice);

@@ -524,6 +524,53 @@ __global__ void __launch_bounds__(256) score_poses_kernel(const DockParams p, in
 }
 
 // ---------------------------------------------------------------------------
+// Explicit poses' coordinates as every kernel builds them: one warp per pose,
+// grid units, atoms written back in the ligand's input order.
+__global__ void __launch_bounds__(256) pose_coords_kernel(const DockParams p, const uint8_t *__restrict__ order,
+                                                          int n_poses, const int32_t *__restrict__ lig_idx,
+                                                          const int32_t *__restrict__ start_id,
+                                                          const uint8_t *__restrict__ tors,
+                                                          float *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0), p.nmax, 1);
+  const int pi = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (pi >= n_poses) return;
+  float *o = out + (size_t)pi * LIGATE_MAX_ATOMS * 3;
+  const int li = lig_idx[pi], sid = start_id[pi];
+  if (li < 0 || li >= p.n_ligands || sid < 0 || sid >= p.n_starts) {  // caller's device data
+    for (int q = lane; q < LIGATE_MAX_ATOMS * 3; q += 32) o[q] = __int_as_float(0x7fc00000);
+    return;
+  }
+  LigDesc d;
+  (void)load_ligand(p, w, li, d, lane);
+  uint32_t tt[4];
+  for (int q = 0; q < 4; ++q) {
+    const uint8_t *t = tors + (size_t)pi * LIGATE_MAX_ROT + 4 * q;
+    tt[q] = (uint32_t)t[0] | ((uint32_t)t[1] << 8) | ((uint32_t)t[2] << 16) | ((uint32_t)t[3] << 24);
+  }
+  build_pose<MODE_F32_PLAIN>(p, w, w.pose, d, sid, tt, lane);
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 x = w.pose[i];
+    float *a = o + 3 * (int)order[d.atom_base + i];
+    a[0] = x.x; a[1] = x.y; a[2] = x.z;
+  }
+}
+
+cudaError_t launch_pose_coords(const DockParams &p, const uint8_t *order, int n_poses, const int32_t *lig_idx,
+                               const int32_t *start_id, const uint8_t *tors, float *out, cudaStream_t s) {
+  if (n_poses <= 0) return cudaSuccess;
+  const int warps = 4;
+  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
+  cudaError_t e = cudaFuncSetAttribute(pose_coords_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e != cudaSuccess) return e;
+  pose_coords_kernel<<<(n_poses + warps - 1) / warps, 32 * warps, smem, s>>>(p, order, n_poses, lig_idx,
+                                                                            start_id, tors, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Start frames: rotation of each orientation quaternion (normalised, rows
 // re-orthonormalised by Gram-Schmidt in FP32) scaled by 1/h, and anchors in
 // grid units.
@@ -532,26 +579,7 @@ __global__ void start_frames_kernel(const float4 *__restrict__ quat, int n_orien
                                     float oy, float oz, float inv_h, float *__restrict__ rot,
                                     float *__restrict__ anc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_orient) {
-    float4 q = quat[i];
-    const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
-    float r0[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)};
-    float r1[3] = {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)};
-    float n0 = rsqrtf(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
-    for (int a = 0; a < 3; ++a) r0[a] *= n0;
-    const float dp = r0[0] * r1[0] + r0[1] * r1[1] + r0[2] * r1[2];
-    for (int a = 0; a < 3; ++a) r1[a] -= dp * r0[a];
-    const float n1 = rsqrtf(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
-    for (int a = 0; a < 3; ++a) r1[a] *= n1;
-    const float r2[3] = {r0[1] * r1[2] - r0[2] * r1[1], r0[2] * r1[0] - r0[0] * r1[2],
-                         r0[0] * r1[1] - r0[1] * r1[0]};
-    for (int a = 0; a < 3; ++a) {
-      rot[9 * i + a] = r0[a] * inv_h;
-      rot[9 * i + 3 + a] = r1[a] * inv_h;
-      rot[9 * i + 6 + a] = r2[a] * inv_h;
-    }
-  }
+  if (i < n_orient) quat_frame(quat[i], inv_h, rot + 9 * i);
   if (i < n_anchor) {
     anc[3 * i] = (anchors[3 * i] - ox) * inv_h;
     anc[3 * i + 1] = (anchors[3 * i + 1] - oy) * inv_h;

@@ -309,6 +309,29 @@ __device__ __forceinline__ void start_frame(const DockParams &p, int sid, float 
   for (int q = 0; q < 3; ++q) T[q] = __ldg(p.anc + 3 * a + q);
 }
 
+// Start frame of one orientation: quaternion (w, x, y, z) normalised, the
+// rows of its rotation re-orthonormalised by Gram-Schmidt in FP32, scaled by
+// 1/h (row-major into rot[9]).
+__device__ __forceinline__ void quat_frame(float4 q, float inv_h, float *__restrict__ rot) {
+  const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  float r0[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)};
+  float r1[3] = {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)};
+  float n0 = rsqrtf(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+  for (int a = 0; a < 3; ++a) r0[a] *= n0;
+  const float dp = r0[0] * r1[0] + r0[1] * r1[1] + r0[2] * r1[2];
+  for (int a = 0; a < 3; ++a) r1[a] -= dp * r0[a];
+  const float n1 = rsqrtf(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+  for (int a = 0; a < 3; ++a) r1[a] *= n1;
+  const float r2[3] = {r0[1] * r1[2] - r0[2] * r1[1], r0[2] * r1[0] - r0[0] * r1[2],
+                       r0[0] * r1[1] - r0[1] * r1[0]};
+  for (int a = 0; a < 3; ++a) {
+    rot[a] = r0[a] * inv_h;
+    rot[3 + a] = r1[a] * inv_h;
+    rot[6 + a] = r2[a] * inv_h;
+  }
+}
+
 // cos/sin of 2 pi k / S from the run's table (FP64 on the host, rounded).
 __device__ __forceinline__ void step_cs(const DockParams &p, int k, float &c, float &s) {
   c = p.cs_tab[2 * k];

@@ -61,6 +61,7 @@ struct BatchDev {
   BondRec *bonds = nullptr;  // [total_rot]
   uint32_t *elig = nullptr;  // clash-pair masks (topological distance >= 4)
   uint16_t *cand = nullptr;  // per-bond clash candidates (see BondRec)
+  uint8_t *order = nullptr;  // [total_atoms] input index of the atom at each DFS position
   // host copies used for planning
   std::vector<LigDesc> h_lig;
   std::vector<BondRec> h_bonds;
@@ -68,6 +69,7 @@ struct BatchDev {
   std::vector<uint16_t> h_cand;
   std::vector<uint8_t> h_types;   // per atom, DFS order
   std::vector<int32_t> h_rot;     // realised rotatable count per ligand
+  std::vector<uint8_t> h_order;   // per atom, DFS order: input index within its ligand
 };
 
 // ---------------------------------------------------------------------------
@@ -218,6 +220,14 @@ cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t
                                  const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
                                  const int32_t *row_lig, float *out, cudaStream_t s);
 
+// Per-ligand selection after rescoring (rescore.cu).
+cudaError_t launch_best_passing(const ligate_rescored *rec, int n, int K, int32_t *idx, float *energy,
+                                cudaStream_t s);
+cudaError_t launch_select_poses(const float *pred, const ligate_pose *poses, int n, int K, float pass_below,
+                                int32_t *idx, cudaStream_t s);
+cudaError_t launch_selector_labels(const ligate_rescored *rec, long long n, float fail_label, float *out,
+                                   cudaStream_t s);
+
 // Pose refinement (refine.cu): mode 0 energy + gradient of explicit
 // states, 1 refine explicit states, 2 refine a plan's poses.
 size_t refine_smem_bytes(int nmax);
@@ -240,6 +250,10 @@ cudaError_t launch_start_frames(const double *quat_unused, const float *quat_f32
 cudaError_t launch_score_poses(int mode, const DockParams &p, int n_poses, const int32_t *lig_idx,
                                const int32_t *start_id, const uint8_t *tors, float *out,
                                cudaStream_t s);
+// Grid-unit coordinates of explicit poses, [n_poses][LIGATE_MAX_ATOMS][3],
+// atoms in input order (order: the batch's DFS-to-input map).
+cudaError_t launch_pose_coords(const DockParams &p, const uint8_t *order, int n_poses, const int32_t *lig_idx,
+                               const int32_t *start_id, const uint8_t *tors, float *out, cudaStream_t s);
 int dock_kernel_max_ctas_per_sm(int mode, int reg_cap, int block, size_t smem);
 // Local (spill) memory per thread of a kernel instance, in bytes.
 size_t dock_kernel_local_bytes(int mode, int reg_cap);

@@ -9,11 +9,16 @@
 // nothing on the device or on the host heap.  The pocket, the batch and the
 // output buffer are the caller's.
 //
-// The array lives on every GPU that loads the library until the process
-// exits.  All calls share it and it keeps the previous call's contents; the
-// counters that must start at zero are cleared at the start of each call, and
-// two calls whose GPU work overlaps (different streams, or different host
-// threads on one device) race on it.
+// The array is reserved on a device when this file's device code is loaded
+// there: under CUDA's default lazy module loading that is the first call of
+// this entry point on the device (its address look-up), so a caller that
+// reserves the rest of the device for its own pool makes one call first (or
+// runs with CUDA_MODULE_LOADING=EAGER).  From then on it stays until the
+// process exits.  All calls share it and it keeps the previous call's
+// contents; the counters that must start at zero are cleared at the start of
+// each call, and two calls whose GPU work overlaps (different streams, or
+// different host threads on one device) race on it.  The orientations reach
+// the device inside the launches' parameters, not through a host buffer.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -21,7 +26,7 @@
 #include <algorithm>
 #include <mutex>
 
-#include "ligate_internal.h"
+#include "dock_device.cuh"
 
 namespace ligate {
 namespace {
@@ -30,6 +35,7 @@ constexpr size_t kScratchBytes = (size_t)8 << 20;  // LIGATE_NOALLOC_SCRATCH_BYT
 constexpr int kMaxOrient = 1024, kMaxAnchor = 1024;
 constexpr int kChunk = 1024;   // starts per work item
 constexpr int kMaxDevices = 64;
+constexpr int kQuatBlock = 240;  // quaternions per launch: the parameters stay under 4 KB
 
 static_assert(kScratchBytes == LIGATE_NOALLOC_SCRATCH_BYTES, "scratch size");
 
@@ -41,6 +47,27 @@ unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Orientations passed by value (copied into the launch's parameters, so no
+// host buffer has to outlive the call): start frames of orientations
+// first .. first + count - 1 (the same arithmetic as the planned path), and
+// with first == 0 the anchors in grid units.
+struct QuatBlock {
+  float4 q[kQuatBlock];
+};
+
+__global__ void noalloc_frames_kernel(const QuatBlock blk, int first, int count, const float *__restrict__ anchors,
+                                      int n_anchor, float ox, float oy, float oz, float inv_h,
+                                      float *__restrict__ rot, float *__restrict__ anc) {
+  const int i = threadIdx.x;
+  if (i < count) quat_frame(blk.q[i], inv_h, rot + 9 * (first + i));
+  if (first == 0)
+    for (int a = i; a < n_anchor; a += blockDim.x) {
+      anc[3 * a] = (anchors[3 * a] - ox) * inv_h;
+      anc[3 * a + 1] = (anchors[3 * a + 1] - oy) * inv_h;
+      anc[3 * a + 2] = (anchors[3 * a + 2] - oz) * inv_h;
+    }
+}
 
 // Work items (ligand, start range, partial-list slot), computed in place.
 __global__ void noalloc_items_kernel(Item *__restrict__ items, int *__restrict__ lig_items,
@@ -114,12 +141,9 @@ extern "C" ligate_status ligate_dock_noalloc(const ligate_pocket *P, const ligat
     set_error("dock_noalloc: the pocket was created without this map precision/layout");
     return LIGATE_ERR_UNSUPPORTED;
   }
-  // float quaternions on the stack; checked before any device work
-  float qf[4 * kMaxOrient];
-  for (int i = 0; i < 4 * s->n_orient; ++i) {
+  // quaternions checked before any device work
+  for (int i = 0; i < 4 * s->n_orient; ++i)
     if (!isfinite(s->orientations[i])) { set_error("dock_noalloc: non-finite quaternion"); return LIGATE_ERR_INVALID; }
-    qf[i] = (float)s->orientations[i];
-  }
   const int n = bt.n_ligands;
   if (n == 0) return LIGATE_OK;
 
@@ -131,7 +155,6 @@ extern "C" ligate_status ligate_dock_noalloc(const ligate_pocket *P, const ligat
   const long long n_items = (long long)n * per_lig;
   const int K = s->top_k;
   size_t off = 0;
-  const size_t o_quat = off; off = align256(off + sizeof(float) * 4 * kMaxOrient);
   const size_t o_rot = off;  off = align256(off + sizeof(float) * 9 * kMaxOrient);
   const size_t o_anc = off;  off = align256(off + sizeof(float) * 3 * kMaxAnchor);
   const size_t o_cnt = off;  off = align256(off + sizeof(int) * ((size_t)n + 1));
@@ -208,10 +231,19 @@ extern "C" ligate_status ligate_dock_noalloc(const ligate_pocket *P, const ligat
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return cuda_fail(e, "dock_noalloc");
 
-  if ((e = cudaMemcpyAsync(base + o_quat, qf, sizeof(float) * 4 * s->n_orient, cudaMemcpyHostToDevice, st)) ||
-      (e = launch_start_frames(nullptr, (const float *)(base + o_quat), s->n_orient, pk.anchors, s->n_anchor,
-                               pk.origin, pk.spacing, (float *)(base + o_rot), (float *)(base + o_anc), st)) ||
-      (e = cudaMemsetAsync(base + o_cnt, 0, sizeof(int) * ((size_t)n + 1), st)))
+  for (int first = 0; first < s->n_orient; first += kQuatBlock) {
+    QuatBlock blk;
+    const int count = std::min(kQuatBlock, s->n_orient - first);
+    for (int q = 0; q < count; ++q) {
+      const double *o = s->orientations + 4 * (size_t)(first + q);
+      blk.q[q] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)o[3]);
+    }
+    noalloc_frames_kernel<<<1, 256, 0, st>>>(blk, first, count, pk.anchors, s->n_anchor, (float)pk.origin[0],
+                                              (float)pk.origin[1], (float)pk.origin[2], (float)(1.0 / pk.spacing),
+                                              (float *)(base + o_rot), (float *)(base + o_anc));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "dock_noalloc: start frames");
+  }
+  if ((e = cudaMemsetAsync(base + o_cnt, 0, sizeof(int) * ((size_t)n + 1), st)) != cudaSuccess)
     return cuda_fail(e, "dock_noalloc: set-up");
   const long long threads = std::max<long long>(n_items, n);
   noalloc_items_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(

@@ -360,4 +360,76 @@ cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Per-ligand result after the filter (paper Sec. 2: docking, then rescoring
+// and a filter; a ligand scores as its best surviving pose): one thread per
+// row of K rescored poses, the lowest energy among those that pass (ties:
+// the smaller slot), or -1 and +inf when none passes.
+__global__ void best_passing_kernel(const ligate_rescored *__restrict__ rec, int n, int K,
+                                    int32_t *__restrict__ idx, float *__restrict__ energy) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int best = -1;
+  float be = __int_as_float(0x7f800000);
+  for (int k = 0; k < K; ++k) {
+    const ligate_rescored q = rec[(size_t)r * K + k];
+    if (q.pass == 1 && (best < 0 || q.energy < be)) { best = k; be = q.energy; }
+  }
+  idx[r] = best;
+  if (energy) energy[r] = be;
+}
+
+// Learned pose selector's rule (paper Sec. 3.5: a pose selector that keeps
+// one pose per ligand without rescoring them all): per row of K poses in
+// docking order, the first live pose (start id >= 0) whose predicted label
+// is below pass_below; else the live pose with the lowest prediction (ties:
+// the smaller slot); -1 for a row without a live pose.
+__global__ void select_poses_kernel(const float *__restrict__ pred, const PoseOut *__restrict__ poses, int n,
+                                    int K, float pass_below, int32_t *__restrict__ idx) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int first = -1, low = -1;
+  float lp = 0.f;
+  for (int k = 0; k < K; ++k) {
+    if (poses[(size_t)r * K + k].start_id < 0) continue;
+    const float v = pred[(size_t)r * K + k];
+    if (first < 0 && v < pass_below) first = k;
+    if (low < 0 || v < lp) { low = k; lp = v; }
+  }
+  idx[r] = first >= 0 ? first : low;
+}
+
+// Selector training label of a rescored pose: its energy clipped to
+// fail_label when it passes the filter, fail_label when it fails (an empty
+// slot too).
+__global__ void selector_labels_kernel(const ligate_rescored *__restrict__ rec, long long n, float fail_label,
+                                       float *__restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ligate_rescored q = rec[i];
+  out[i] = q.pass == 1 ? fminf(q.energy, fail_label) : fail_label;
+}
+
+cudaError_t launch_best_passing(const ligate_rescored *rec, int n, int K, int32_t *idx, float *energy,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  best_passing_kernel<<<(n + 127) / 128, 128, 0, s>>>(rec, n, K, idx, energy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select_poses(const float *pred, const ligate_pose *poses, int n, int K, float pass_below,
+                                int32_t *idx, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  select_poses_kernel<<<(n + 127) / 128, 128, 0, s>>>(pred, reinterpret_cast<const PoseOut *>(poses), n, K,
+                                                      pass_below, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selector_labels(const ligate_rescored *rec, long long n, float fail_label, float *out,
+                                   cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  selector_labels_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec, n, fail_label, out);
+  return cudaGetLastError();
+}
+
 }  // namespace ligate

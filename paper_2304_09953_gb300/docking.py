@@ -1,5 +1,6 @@
 """Convenience layer over the C ABI: RAII wrappers for pockets, batches and
-plans, returning numpy structured arrays of poses.  No computation here."""
+plans, returning numpy structured arrays of poses.  No computation here:
+every selection and score comes from the library's kernels."""
 from __future__ import annotations
 
 import numpy as np
@@ -87,6 +88,19 @@ class Plan:
         torch.cuda.synchronize()
         return buf.cpu().numpy().view(N.RESCORED_DTYPE).reshape(self.n, self.k)
 
+    def best_passing(self, rescored, stream=None):
+        """Per ligand the slot of its lowest-energy pose that passes the
+        filter (-1 if none) and that energy (+inf if none), from rescored
+        records of this plan's poses (RESCORED_DTYPE [n, K], host array or a
+        CUDA byte tensor), by ligate_plan_best_passing."""
+        import torch
+        buf = _device_bytes(rescored)
+        idx = torch.empty(max(self.n, 1), dtype=torch.int32, device="cuda")
+        en = torch.empty(max(self.n, 1), dtype=torch.float32, device="cuda")
+        N.ligate_plan_best_passing(self.h, buf, idx, en, stream)
+        torch.cuda.synchronize()
+        return idx[:self.n].cpu().numpy(), en[:self.n].cpu().numpy()
+
     def device_output(self) -> int:
         """Device address of the last run's ligate_pose[n][K] result."""
         return N.ligate_plan_output(self.h)
@@ -118,11 +132,9 @@ def dock(pocket, ligands, sampling, mode="fp32", rescore=None, tile=None, top_k=
         ph.close()
 
 
-def best_passing(rescored: np.ndarray):
-    """Per ligand (row) the index of the lowest-energy pose that passes the
-    filter, or -1 when none passes; and that energy (+inf when none)."""
-    e = np.where(rescored["pass"] == 1, rescored["energy"], np.inf)
-    idx = np.argmin(e, axis=1)
-    best = e[np.arange(len(e)), idx]
-    return np.where(np.isfinite(best), idx, -1), best
-
+def _device_bytes(a):
+    """A CUDA byte view of a structured host array (copied) or a CUDA tensor."""
+    import torch
+    if isinstance(a, np.ndarray):
+        return torch.from_numpy(np.ascontiguousarray(a).reshape(-1).view(np.uint8)).cuda()
+    return a

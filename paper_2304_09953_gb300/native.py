@@ -101,6 +101,7 @@ _SIGS = {
     "ligate_dock_batch": (ctypes.c_int, [P, P, P, P, P]),
     "ligate_dock_noalloc": (ctypes.c_int, [P, P, P, P, P]),
     "ligate_score_poses": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
+    "ligate_pose_coords": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_autotune": (ctypes.c_int, [P, P, P, ctypes.c_double, P]),
     "ligate_model_tile": (ctypes.c_int, [P, P, P, P]),
     "ligate_descriptors": (ctypes.c_int, [P, P, P]),
@@ -130,6 +131,9 @@ _SIGS = {
     "ligate_plan_rescore_refined": (ctypes.c_int, [P, P, P, P]),
     "ligate_pose_features": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_plan_pose_features": (ctypes.c_int, [P, P, P]),
+    "ligate_plan_best_passing": (ctypes.c_int, [P, P, P, P, P]),
+    "ligate_select_poses": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_float, P, P]),
+    "ligate_selector_labels": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_float, P, P]),
 }
 
 _lib = None
@@ -326,6 +330,12 @@ def ligate_score_poses(pocket, batch, sampling_struct, n, lig_idx, start_id, tor
                                     _ptr(start_id), _ptr(tors), _ptr(out), stream), "ligate_score_poses")
 
 
+def ligate_pose_coords(pocket, batch, sampling_struct, n, lig_idx, start_id, tors, out, stream=None):
+    """out: DEVICE float32 [n][LIGATE_MAX_ATOMS][3], grid units, input atom order."""
+    check(load().ligate_pose_coords(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
+                                    _ptr(start_id), _ptr(tors), _ptr(out), stream), "ligate_pose_coords")
+
+
 def ligate_pose_gradient(pocket, batch, sampling_struct, n, lig_idx, states, energy, grad, stream=None):
     """states: DEVICE ligate_pose_state[n] (e.g. a uint8 tensor of n * 112 bytes)."""
     check(load().ligate_pose_gradient(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
@@ -473,3 +483,20 @@ def ligate_surrogate_load(path):
     check(load().ligate_surrogate_load(str(path).encode(), ctypes.byref(h)), "ligate_surrogate_load")
     return h
 
+
+def ligate_plan_best_passing(plan, rescored, idx_out, energy_out=None, stream=None):
+    """rescored: DEVICE RESCORED_DTYPE [n][K]; idx_out DEVICE int32 [n]; energy_out DEVICE float32 [n]."""
+    check(load().ligate_plan_best_passing(plan, _ptr(rescored), _ptr(idx_out), _ptr(energy_out), stream),
+          "ligate_plan_best_passing")
+
+
+def ligate_select_poses(pred, poses, n, k, pass_below, idx_out, stream=None):
+    """pred DEVICE float32 [n][k]; poses DEVICE POSE_DTYPE [n][k]; idx_out DEVICE int32 [n]."""
+    check(load().ligate_select_poses(_ptr(pred), _ptr(poses), int(n), int(k), float(pass_below), _ptr(idx_out),
+                                     stream), "ligate_select_poses")
+
+
+def ligate_selector_labels(rescored, n, fail_label, out, stream=None):
+    """rescored DEVICE RESCORED_DTYPE [n]; out DEVICE float32 [n]."""
+    check(load().ligate_selector_labels(_ptr(rescored), int(n), float(fail_label), _ptr(out), stream),
+          "ligate_selector_labels")

@@ -1,17 +1,20 @@
 """Exact rescoring and the pose filter on the GPU vs the FP64 oracle.
 
 Explicit poses (seeded starts and torsion steps): receptor and clash terms
-within 1e-4 of the sum of absolute term values; the filter counts equal the
-oracle's for at least 98% of poses (an atom on the box face or a sum at the
-cap may fall either way in FP32).  The plan path gives the same values as
-the explicit path for the plan's own poses, and the per-ligand choice of the
-best passing pose follows from them."""
+by the docking score's parity rules (strict 1e-4 relative, else exact at the
+GPU's own coordinates with the coordinates inside the FP32 envelope); the
+filter counts equal the oracle's at the GPU's coordinates except for an atom
+on its threshold (a receptor sum within the bar of the cap, a coordinate on
+a box face).  The plan path gives the same values as the explicit path for
+the plan's own poses, and the per-ligand choice of the best passing pose
+follows from them."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2304_09953_gb300 import docking as D
 from paper_2304_09953_gb300 import native as N
+from tests.parity import (REL, U32, Geometry, Stats, coord_envelope, features_check, rescore_check)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -43,23 +46,19 @@ def test_rescore_matches_oracle(name, request):
     N.ligate_rescore_poses(ph.h, bh.h, s, n, torch.from_numpy(lig).cuda(), torch.from_numpy(sid).cuda(),
                            torch.from_numpy(tors).cuda(), out)
     r = out.cpu().numpy().view(N.RESCORED_DTYPE)
-    rec = w.pocket.receptor()
-    same_flags = 0
+    geo = Geometry(w.pocket)
+    st = Stats()
+    diff_exact = diff_gpu = 0
     for li in np.unique(lig):
         sel = np.nonzero(lig == li)[0]
         R_n = int(w.ligands.n_rot[li])
-        L = w.ligands.ligand(li)
-        x = oracle.pose_coords(L, w.pocket.anchors, w.sampling, sid[sel], tors[sel, :R_n].astype(np.int32))
-        o = oracle.rescore_coords(L, w.pocket, w.sampling, rec, x)
-        for m, k in enumerate(sel):
-            tol = 1e-4 * max(o["scale"][m], 1.0)
-            assert abs(r[k]["e_inter"] - o["e_inter"][m]) <= tol, (li, k, r[k]["e_inter"], o["e_inter"][m])
-            assert abs(r[k]["e_clash"] - o["e_clash"][m]) <= tol
-            assert abs(r[k]["energy"] - (o["e_inter"][m] + o["e_clash"][m])) <= tol
-            ok = r[k]["n_outside"] == o["n_outside"][m] and r[k]["n_capped"] == o["n_capped"][m]
-            same_flags += ok
-            assert r[k]["pass"] == (r[k]["n_outside"] == 0 and r[k]["n_capped"] == 0)
-    assert same_flags >= 0.98 * n, (same_flags, n)
+        info = rescore_check(geo, w.ligands.ligand(li), w.pocket, w.sampling, sid[sel], tors[sel, :R_n],
+                             r[sel], st)
+        diff_exact += info["flag_diff_vs_exact"]
+        diff_gpu += info["flag_diff_vs_gpu_coords"]
+        assert np.allclose(r[sel]["energy"], r[sel]["e_inter"] + r[sel]["e_clash"], rtol=1e-6, atol=1e-5)
+    print(f"{st.line()}; filter counts differing from the oracle at the exact poses {diff_exact}, "
+          f"at the GPU's coordinates {diff_gpu} (all on a threshold) of {n}")
     assert np.any(r["n_capped"] > 0)  # random poses hit the receptor
 
 
@@ -82,7 +81,7 @@ def test_plan_rescore_equals_explicit_and_selects_best(batched_small):
     flat = rs.reshape(-1)
     np.testing.assert_array_equal(flat[live], ex)
     assert np.all(np.isinf(flat[~live]["energy"]))
-    idx, best = D.best_passing(rs)
+    idx, best = pl.best_passing(rs)
     # the interpolated maps smooth the steep wall of the pair potential, so
     # many docked poses touch it (a capped atom); a good share still passes
     assert np.mean(idx >= 0) > 0.25
@@ -111,9 +110,10 @@ def test_rescore_needs_a_receptor(tiny):
 
 @pytest.mark.parametrize("name", ["tiny", "batched_small"])
 def test_pose_features_match_oracle(name, request):
-    """Histogram counts equal the oracle's (FP32 bin decisions on both sides)
-    for at least 99% of poses; means, score and clash entries within 1e-4 of
-    their term scale; the plan path equals the explicit path."""
+    """Histogram counts equal the oracle's at the GPU's coordinates (FP32 bin
+    decisions on both sides) except for an atom whose value sits on a bin
+    edge; means, score and clash entries by the score rules; the plan path
+    equals the explicit path (test_empty_slots and the selector test)."""
     w = request.getfixturevalue(name)
     lig, sid, tors = explicit(w, 128 if name == "tiny" else 8, 11)
     ph = D.PocketHandle(w.pocket)
@@ -124,28 +124,14 @@ def test_pose_features_match_oracle(name, request):
     N.ligate_pose_features(ph.h, bh.h, s, n, torch.from_numpy(lig).cuda(), torch.from_numpy(sid).cuda(),
                            torch.from_numpy(tors).cuda(), out)
     f = out.cpu().numpy().astype(np.float64)
-    same_hist = 0
+    geo = Geometry(w.pocket)
+    moved = 0
     for li in np.unique(lig):
         sel = np.nonzero(lig == li)[0]
         R_n = int(w.ligands.n_rot[li])
-        L = w.ligands.ligand(li)
-        x = oracle.pose_coords(L, w.pocket.anchors, w.sampling, sid[sel], tors[sel, :R_n].astype(np.int32))
-        o = oracle.pose_features(L, w.pocket, w.sampling, x)
-        _, scale = oracle.score_poses(L, w.pocket, w.sampling, sid[sel], tors[sel, :R_n].astype(np.int32),
-                                      with_scale=True)
-        n_at = len(L[1])
-        for m, k in enumerate(sel):
-            same = np.array_equal(np.round(np.expm1(f[k, :64])), np.round(np.expm1(o[m, :64])))
-            same_hist += same
-            if same:
-                np.testing.assert_allclose(f[k, :64], o[m, :64], rtol=2e-6, atol=2e-6)
-            tol = 1e-4 * max(scale[m], 1.0)
-            assert abs(f[k, 72] - o[m, 72]) * n_at <= tol
-            assert abs(f[k, 73] - o[m, 73]) <= tol
-            np.testing.assert_allclose(f[k, 64:72], o[m, 64:72], atol=tol)
-            np.testing.assert_allclose(f[k, 74:77], o[m, 74:77], rtol=1e-6)
-            assert np.all(f[k, 77:] == 0)
-    assert same_hist >= 0.99 * n, (same_hist, n)
+        moved += features_check(geo, w.ligands.ligand(li), w.pocket, w.sampling, sid[sel], tors[sel, :R_n],
+                                f[sel])
+    print(f"histograms differing from the oracle at the GPU's coordinates: {moved} of {n} (bin-edge atoms)")
 
 
 def test_learned_selector_beats_docking_rank(workload_factory):
@@ -163,36 +149,35 @@ def test_learned_selector_beats_docking_rank(workload_factory):
     def features_and_truth(lig_w):
         bh = D.BatchHandle(lig_w.ligands)
         pl = D.Plan(ph, bh, lig_w.sampling, mode="bf16")
-        pl.run()
+        poses = pl.result()
         n = lig_w.ligands.n * K
         f = torch.empty((n, 256), dtype=torch.float32, device="cuda")
         N.ligate_plan_pose_features(pl.h, f)
         r = torch.empty(n * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         N.ligate_plan_rescore(pl.h, r)
-        torch.cuda.synchronize()
-        out = f, r.cpu().numpy().view(N.RESCORED_DTYPE)
+        best_idx, _ = pl.best_passing(r)
+        out = f, r.cpu().numpy().view(N.RESCORED_DTYPE), poses, best_idx
         pl.close()
         bh.close()
         return out
 
-    ftr, rtr = features_and_truth(tw)
+    ftr, rtr, _, _ = features_and_truth(tw)
     live = np.isfinite(rtr["energy"])
     idx = torch.from_numpy(np.nonzero(live)[0]).cuda()
     net = N.ligate_surrogate_create(None, 5)
     try:
-        N.ligate_surrogate_train(net, ftr[idx].contiguous(), torch.from_numpy(SEL.labels(rtr[live])).cuda(),
+        N.ligate_surrogate_train(net, ftr[idx].contiguous(), SEL.labels(rtr[live]).contiguous(),
                                  len(idx), 10, 1024, 1e-3, 5)
-        f, r = features_and_truth(w)
+        f, r, poses, best_idx = features_and_truth(w)
         pred = torch.empty(f.shape[0], dtype=torch.float32, device="cuda")
         N.ligate_surrogate_predict(net, f, f.shape[0], pred)
         p = pred.cpu().numpy().reshape(-1, K)
     finally:
         N.ligate_surrogate_destroy(net)
     ex = r.reshape(-1, K)
-    best_idx, _ = D.best_passing(ex)
     has = best_idx >= 0
     rows = np.arange(len(ex))
-    pick = SEL.select(p, np.isfinite(ex["energy"]))
+    pick = SEL.select(p, poses)
     rank0 = np.zeros(len(ex), np.int64)
     pass_sel = np.mean(ex["pass"][rows, pick][has] == 1)
     pass_r0 = np.mean(ex["pass"][rows, rank0][has] == 1)
@@ -219,17 +204,44 @@ def test_rescore_states_matches_oracle_and_refined_plan_path(batched_small):
     N.ligate_rescore_states(ph.h, bh.h, s, n, torch.from_numpy(lig).cuda(), to_dev(rec), out)
     r = out.cpu().numpy().view(N.RESCORED_DTYPE)
     same = 0
+    org, h = np.asarray(w.pocket.origin), w.pocket.spacing
+    rcp = w.pocket.receptor()
     for li in np.unique(lig):
         sel = np.nonzero(lig == li)[0]
         L = w.ligands.ligand(li)
+        R_n = int(np.sum(L[3] != 0))
         x = oracle.state_coords(L, np.array([st64[k] for k in sel]))
-        o = oracle.rescore_coords(L, w.pocket, w.sampling, w.pocket.receptor(), x)
+        o = oracle.rescore_coords(L, w.pocket, w.sampling, rcp, x)
         for m, k in enumerate(sel):
             tol = 1e-4 * max(o["scale"][m], 1.0)
             assert abs(r[k]["e_inter"] - o["e_inter"][m]) <= tol
             assert abs(r[k]["e_clash"] - o["e_clash"][m]) <= tol
-            same += r[k]["n_outside"] == o["n_outside"][m] and r[k]["n_capped"] == o["n_capped"][m]
-    assert same >= 0.98 * n
+            ok = r[k]["n_outside"] == o["n_outside"][m] and r[k]["n_capped"] == o["n_capped"][m]
+            same += ok
+            if not ok:
+                # without the GPU's coordinates of a state, a flag difference
+                # must come from an atom that the coordinate envelope can move
+                # across its threshold: the face distance within the envelope,
+                # or the receptor sum crossing the cap somewhere in the box of
+                # that half-width around the atom (a corner of it, first order)
+                env = coord_envelope((x[m] - org) / h, R_n)
+                s0, mg, fc = oracle.rescore_atoms(L, w.pocket, rcp, x[m:m + 1])
+                near = np.abs(fc[0]) <= env
+                d = env * h
+                lo, hi = s0[0].copy(), s0[0].copy()
+                for ax in range(3):
+                    for sg in (-1.0, 1.0):
+                        xp = x[m:m + 1].copy()
+                        xp[0, :, ax] += sg * d
+                        sp, _, _ = oracle.rescore_atoms(L, w.pocket, rcp, xp)
+                        lo = np.minimum(lo, s0[0] - 3 * np.abs(sp[0] - s0[0]))
+                        hi = np.maximum(hi, s0[0] + 3 * np.abs(sp[0] - s0[0]))
+                cross = (lo - REL * np.maximum(mg[0], 1) <= w.pocket.cap) & \
+                        (hi + REL * np.maximum(mg[0], 1) >= w.pocket.cap)
+                dcap = abs(int(r[k]["n_capped"]) - int(o["n_capped"][m]))
+                dout = abs(int(r[k]["n_outside"]) - int(o["n_outside"][m]))
+                assert dcap <= int(cross.sum()) and dout <= int(near.sum()), (k, dcap, dout)
+    print(f"states with filter counts equal to the oracle's: {same} of {n}")
     # refined plan records vs their states through the explicit path
     pl = D.Plan(ph, bh, w.sampling, mode="bf16")
     pl.run()

@@ -5,8 +5,10 @@ memory is all reserved by its own pool, or a loop that cannot afford
 cudaMalloc's implicit synchronisation): its scratch lives in a fixed device
 array inside the library.  Checked here through the C ABI: two calls in a
 row give the same poses as the allocating plan path (same starts and
-torsion steps, scores within the docking tolerance), and requests larger
-than the array are refused with an error.  This file is named to be
+torsion steps, scores within the docking tolerance), the second call leaves
+the device's free memory unchanged (the first may load the library's device
+code, and with it the array), and requests larger than the array are
+refused with an error.  This file is named to be
 collected last; it also passes alone in a fresh process."""
 import numpy as np
 import pytest
@@ -31,10 +33,18 @@ def test_noalloc_matches_plan_path_twice(mode):
     prec, layout = D.MODES[mode]
     s = N.make_sampling(w.sampling, prec, layout, rescore=prec != N.LIGATE_FP32)
     K = w.sampling.top_k
+    outs = [torch.full((w.ligands.n * K * 24,), 0xAB, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
     for call in range(2):
-        out = torch.full((w.ligands.n * K * 24,), 0xAB, dtype=torch.uint8, device="cuda")
+        if call == 1:  # the first call may have loaded the array; the second allocates nothing
+            free0 = torch.cuda.mem_get_info()[0]
+            held0 = torch.cuda.memory_reserved()
+        out = outs[call]
         N.ligate_dock_noalloc(ph.h, bh.h, s, out)
         torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0, "the second call changed the free device memory"
+            assert torch.cuda.memory_reserved() == held0
         got = out.cpu().numpy().view(N.POSE_DTYPE).reshape(w.ligands.n, K)
         np.testing.assert_array_equal(got["start_id"], want["start_id"])
         np.testing.assert_array_equal(got["tors"], want["tors"])
