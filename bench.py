@@ -39,11 +39,20 @@ WORKLOAD = ("batched: 10000 ligands (N~U{15..60}, R~U{0..12}), 8x64^3 maps @0.37
 WORKLOADS = {"batched": WORKLOAD,
              "combined": ("combined: 1000000 ligands (N log-uniform {10..80}, R~U{0..15}), "
                           "8x96^3 maps @0.375 A, 256 orient x 32 anchors x S=16, top-16")}
-# FP32 operations (FMA = 2) per unit of executed work:
-#   atom interpolation: 9 FMA rotation + 3 fraction subs + 7 lerps (sub + FMA) + 1 add = 43
-#   clash candidate test (once per bond): 2 subs + mul + FMA against the circle bound = 5
-#   surviving pair set-up (once per bond): P, Q, D0 and the scaled coefficients = 33
-#   surviving pair, per torsion step: 2 FMA (d^2 in closed form) + 1 FMA (t^2) = 6
+# Roofline of the docking kernel, two FLOP counts (FMA = 2):
+#  * algorithmic (the method's own count, per unique pose): every atom
+#    evaluation of a unique pose (N per start, moved atoms x (S - 1) per bond)
+#    costs 50 FLOP (rotation 9 FMA, rigid move 9 FMA, grid coordinate 3 FMA,
+#    7 lerps as sub + FMA, floor/sub 3), every crossing clash pair of a unique
+#    trial (candidates x (S - 1) per bond) 12 FLOP;
+#  * executed (what the kernel actually computes after pruning and the clash
+#    memo), from the device counters of the run:
+#      atom interpolation: 9 FMA rotation + 3 fraction subs + 7 lerps + 1 add = 43
+#      clash candidate test (once per bond): 2 subs + mul + FMA against the bound = 5
+#      surviving pair set-up (once per bond): P, Q, D0 and the scaled coefficients = 33
+#      surviving pair, per torsion step: 2 FMA (d^2 in closed form) + 1 FMA (t^2) = 6
+FLOP_ALG_ATOM = 50.0
+FLOP_ALG_PAIR = 12.0
 FLOP_PER_ATOM_EVAL = 43.0
 FLOP_PER_PAIR_TEST = 5.0
 FLOP_PER_PAIR_SETUP = 33.0
@@ -55,14 +64,21 @@ def executed_flops(work, S):
             + work.done_pair_survivors * (FLOP_PER_PAIR_SETUP + S * FLOP_PER_PAIR_STEP))
 
 
-# DRAM bytes (read + write) of one full-size launch of the chosen-form kernel,
-# from ncu (profiles/dock_kernel_bf16_batched10k.md), valid only for the
-# kernel source it was captured on (kernel_source_sha).  Captured at
-# 906aa2549e6b; 00b51f852e66 only adds a list-size parameter, defaulting to
-# the old constant, to the shared warp-slot helpers for the rescoring kernel,
-# so the docking kernel's device code is the one captured.
-TRAFFIC_BYTES = {("906aa2549e6b", "batched", 10000): 103095552 + 68539392,
-                 ("00b51f852e66", "batched", 10000): 103095552 + 68539392}
+def algorithmic_flops(work, S, n_starts, total_atoms):
+    """Unique-pose count: the plan's atom and pair counts include the k = 0
+    trial of every bond, which repeats the current pose."""
+    rigid = float(n_starts) * float(total_atoms)
+    atoms = rigid + (work.atom_evals - rigid) * (S - 1) / S
+    pairs = work.pair_evals * (S - 1) / S
+    return FLOP_ALG_ATOM * atoms + FLOP_ALG_PAIR * pairs, atoms, pairs
+
+
+# DRAM bytes (read + write) of one full-size launch of the chosen-form
+# kernel, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
+# valid only for the kernel revision it was captured on (sha1 prefix of
+# dock.cu + dock_device.cuh); any other revision reports null until it is
+# captured again.
+TRAFFIC_BYTES = {}
 
 
 def kernel_source_sha():
@@ -78,7 +94,8 @@ def kernel_traffic(workload, n_ligands):
     return TRAFFIC_BYTES.get((kernel_source_sha(), workload, n_ligands))
 
 
-def fp32_peak_tflops(sms=152, lanes=128, mhz=2070.0):
+def fp32_peak_tflops(sms, mhz, lanes=128):
+    """FP32 FMA peak of the device: SMs x 128 FP32 lanes x 2 FLOP x clock."""
     return sms * lanes * 2 * mhz * 1e6 / 1e12
 
 
@@ -559,11 +576,25 @@ def main():
     poses_s = ws * work.poses * args.steps / t_chosen
     mean_ms = t_chosen * 1000 / args.steps
     S = w.sampling.torsion_steps
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    mhz = clock_info["sm_mhz"] or clock_info["sm_max_mhz"] or 2070.0
+    peak = fp32_peak_tflops(n_sm, mhz)
+    total_atoms = int(np.sum(np.diff(w.ligands.atom_offset)))
+    alg, alg_atoms, alg_pairs = algorithmic_flops(work, S, w.sampling.n_starts, total_atoms)
     flops = executed_flops(work, S)
-    achieved = flops / (mean_ms / 1000) / 1e12
-    peak = fp32_peak_tflops()
+    achieved = alg / (mean_ms / 1000) / 1e12
+    achieved_exec = flops / (mean_ms / 1000) / 1e12
     plain_ms = sum(ms_plain) / len(ms_plain)
     plain_flops = executed_flops(work_plain, S)
+    plain_alg, _, _ = algorithmic_flops(work_plain, S, w.sampling.n_starts, total_atoms)
+    # gather half: 16-byte corner-cell reads of the sweep against the measured
+    # ceiling of random corner-cell gathers over the same maps
+    gather_peak = N.ligate_probe_gather(ph.h, N.LIGATE_BF16)
+    gather_peak_f32 = N.ligate_probe_gather(ph.h, N.LIGATE_FP32)
+    gather_bytes = work.done_atom_evals * 16.0
+    gather_gbs = gather_bytes / (mean_ms / 1000) / 1e9
+    plain_gather_gbs = work_plain.done_atom_evals * 32.0 / (plain_ms / 1000) / 1e9
 
     # end to end through the host-array C-ABI call
     e2e = None
@@ -710,13 +741,30 @@ def main():
         "plain": {"value": ws * n_lig / (plain_ms / 1000), "unit": "ligands/s",
                   "poses_per_s": ws * work_plain.poses / (plain_ms / 1000), "ms_per_step": plain_ms,
                   "form": "fp32 plain maps, default tile, no rescore",
-                  "roofline_frac": plain_flops / (plain_ms / 1000) / 1e12 / peak},
+                  "roofline_frac": plain_alg / (plain_ms / 1000) / 1e12 / peak,
+                  "roofline_frac_executed": plain_flops / (plain_ms / 1000) / 1e12 / peak,
+                  "gather": {"achieved": plain_gather_gbs, "peak": gather_peak_f32, "unit": "GB/s",
+                             "frac": plain_gather_gbs / gather_peak_f32,
+                             "note": "32 B per interpolation (eight FP32 corners); peak measured on the "
+                                     "FP32 corner layout"}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": kernel_traffic(args.workload, n_lig),
-                     "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                     "frac": achieved / peak,
+                     "count": "algorithmic: 50 FLOP per atom evaluation of a unique pose + 12 FLOP per "
+                              "crossing clash pair of a unique trial",
+                     "achieved_executed": achieved_exec, "frac_executed": achieved_exec / peak,
+                     "traffic": kernel_traffic(args.workload, n_lig),
+                     "traffic_unit": "bytes per launch (ncu dram read + write of this kernel revision; "
+                                     "null until captured for it)",
+                     "peak_note": f"FP32 FMA peak derived: {n_sm} SMs x 128 lanes x 2 x {mhz:.0f} MHz "
+                                  "(median SM clock sampled during the timed region)",
                      "kernel": "dock_kernel<BF16_CORNER>",
-                     "work_per_launch": {"atom_evals": work.done_atom_evals,
+                     "gather": {"achieved": gather_gbs, "peak": gather_peak, "unit": "GB/s",
+                                "frac": gather_gbs / gather_peak, "bytes_per_launch": gather_bytes,
+                                "peak_note": "measured: ligate_probe_gather, random 16 B corner-cell "
+                                             "gathers over the whole BF16 map, all SMs (L2-served)"},
+                     "work_per_launch": {"atom_evals_unique": alg_atoms, "pair_trials_unique": alg_pairs,
+                                         "algorithmic_flop": alg, "executed_flop": flops,
+                                         "atom_evals": work.done_atom_evals,
                                          "pair_tests": work.done_pair_tests,
                                          "pair_survivors": work.done_pair_survivors,
                                          "pair_candidates_x_S": work.pair_evals, "poses": work.poses}},

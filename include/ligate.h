@@ -105,6 +105,16 @@ ligate_status ligate_pocket_create(const float *maps, int n_types, int nx, int n
                                    int n_anchors, unsigned precision_mask, ligate_pocket **out);
 void ligate_pocket_destroy(ligate_pocket *pocket);
 
+/* Measured ceiling of the docking kernel's map reads on this device (the
+ * gather half of its roofline; the paper's Sec. 3.1 compares devices by
+ * docking throughput): uniformly random corner-cell gathers over the whole
+ * corner-packed map of `precision` (16 B per cell for BF16/FP16, 32 B for
+ * FP32), four independent loads in flight per thread, all SMs, after one
+ * warm-up pass; *gbs_out = bytes gathered / best time of three passes
+ * (CUDA events), in GB/s.  Synchronous, on the legacy default stream.
+ * Errors: INVALID, UNSUPPORTED (no such map in the pocket), CUDA. */
+ligate_status ligate_probe_gather(const ligate_pocket *pocket, ligate_precision precision, double *gbs_out);
+
 /* ------------------------------------------------------------------------
  * Ligand library (paper Sec. 2: ligands after 3D preparation; Sec. 3.3:
  * processed as a batch).  All host arrays, concatenated over ligands:

@@ -139,6 +139,27 @@ extern "C" ligate_status ligate_pocket_create(const float *maps, int n_types, in
   return LIGATE_OK;
 }
 
+extern "C" ligate_status ligate_probe_gather(const ligate_pocket *P, ligate_precision precision,
+                                             double *gbs_out) {
+  if (!P || !gbs_out) { set_error("probe_gather: NULL argument"); return LIGATE_ERR_INVALID; }
+  const PocketDev &d = P->d;
+  const void *cells = precision == LIGATE_FP32 ? (const void *)d.map_f32c
+                    : precision == LIGATE_BF16 ? (const void *)d.map_bf16c : (const void *)d.map_f16c;
+  if (!cells) {
+    set_error("probe_gather: the pocket has no corner-packed map of this precision");
+    return LIGATE_ERR_UNSUPPORTED;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_gather");
+  double ms = 0, bytes = 0;
+  e = probe_gather(cells, d.n_cells() * (size_t)d.n_types, precision == LIGATE_FP32 ? 2 : 1, sms, &ms, &bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "probe_gather");
+  *gbs_out = bytes / (ms * 1e-3) / 1e9;
+  return LIGATE_OK;
+}
+
 extern "C" void ligate_pocket_destroy(ligate_pocket *p) {
   if (!p) return;
   cudaFree(p->d.map_f32);
@@ -724,6 +745,7 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   p.g.nx = d.nx; p.g.ny = d.ny; p.g.nz = d.nz;
   p.g.fx1 = (float)(d.nx - 1); p.g.fy1 = (float)(d.ny - 1); p.g.fz1 = (float)(d.nz - 1);
   p.g.penalty = s->penalty;
+  p.g.cx = 8388608.f + (float)(d.nx - 2); p.g.cy = 8388608.f + (float)(d.ny - 2); p.g.cz = 8388608.f + (float)(d.nz - 2);
   p.n_anchor = s->n_anchor;
   p.n_starts = s->n_orient * s->n_anchor;
   p.S = s->torsion_steps;

@@ -377,14 +377,15 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
           if (br.n_cand0 > 0 && k < S) ac += w.memo[memo_row0(S) + (b - memo_bonds(S)) * S + k];
           ac += c1;
         }
-        const float V = (k < S) ? fmaf(p.clash_w, ac, ag) : INF;
-        float best = V;
-        int bk = k;
-        for (int o = L >> 1; o > 0; o >>= 1) {
-          const float ob = __shfl_xor_sync(FULL, best, o);
-          const int okk = __shfl_xor_sync(FULL, bk, o);
-          if (ob < best || (ob == best && okk < bk)) { best = ob; bk = okk; }
-        }
+        const float V = (k < S) ? fmaf(p.clash_w, ac, ag) + 0.f : INF;  // + 0: -0 becomes +0
+        // argmin over the group's lanes (ties: smaller k) by one min-reduction
+        // of an order-preserving integer key and one ballot
+        const unsigned vb = __float_as_uint(V);
+        const unsigned key = vb ^ ((unsigned)((int)vb >> 31) | 0x80000000u);
+        const unsigned gmask = L == 32 ? FULL : (((1u << L) - 1u) << glead);
+        const unsigned kmin = __reduce_min_sync(gmask, key);
+        const int bk = __ffs(__ballot_sync(FULL, key == kmin) & gmask) - 1 - glead;
+        const float best = __uint_as_float((kmin & 0x80000000u) ? (kmin ^ 0x80000000u) : ~kmin);
         const float V0 = __shfl_sync(FULL, V, glead);
         const float cb = __shfl_sync(FULL, ck, glead + bk);
         const float sb = __shfl_sync(FULL, sk, glead + bk);
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         switch (b >> 2) { case 0: t0 |= bits; break; case 1: t1 |= bits; break;
                           case 2: t2 |= bits; break; default: t3 |= bits; }
         __syncwarp();
-        if (bk != 0) {
+        if (__any_sync(FULL, bk != 0)) {  // a group whose step is 0 applies the identity exactly
           Rot rb;
           rb.make(cb, sb, nx, ny, nz, pv.x, pv.y, pv.z);
           for (int i = br.v + 1 + k; i < br.end; i += L) {

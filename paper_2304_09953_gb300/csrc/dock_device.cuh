@@ -22,14 +22,25 @@ constexpr int EMPTY_SID = 0x7fffffff;   // start id of an empty top-K slot
 // first element (plain) or cell (corner layouts) is at `toff`.  Outside
 // [0, n-1] on any axis the atom scores the penalty.  Cell = min(floor, n-2),
 // then successive linear interpolation along x, y, z.
+//
+// The cell index is taken without float/integer conversions (a slow pipe):
+// for 0 <= u < 2^22, u + 2^23 rounded toward minus infinity is exactly
+// 2^23 + floor(u) (FP32 spacing is 1 there), so its bit pattern minus that
+// of 2^23 is floor(u), and (u + 2^23) - 2^23 is floor(u) as a float; the
+// clamp to n - 2 is an FP32 min against 2^23 + n - 2 (GridConst cx, cy, cz).
+// Inside the box the cell and the fraction equal those of (int)u exactly.
 template <int MODE>
 __device__ __forceinline__ float grid_eval(const void *__restrict__ maps, int toff, float ux,
                                            float uy, float uz, const GridConst &g) {
   if (!((ux >= 0.f) & (ux <= g.fx1) & (uy >= 0.f) & (uy <= g.fy1) & (uz >= 0.f) &
         (uz <= g.fz1)))
     return g.penalty;
-  const int ix = min((int)ux, g.nx - 2), iy = min((int)uy, g.ny - 2), iz = min((int)uz, g.nz - 2);
-  const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+  const float M23 = 8388608.f;
+  const float tx = fminf(__fadd_rd(ux, M23), g.cx), ty = fminf(__fadd_rd(uy, M23), g.cy),
+              tz = fminf(__fadd_rd(uz, M23), g.cz);
+  const int ix = __float_as_int(tx) - 0x4B000000, iy = __float_as_int(ty) - 0x4B000000,
+            iz = __float_as_int(tz) - 0x4B000000;
+  const float fx = ux - (tx - M23), fy = uy - (ty - M23), fz = uz - (tz - M23);
   float v0, v1, v2, v3, v4, v5, v6, v7;
   if (MODE == MODE_F32_PLAIN) {
     const float *m = (const float *)maps + toff + (iz * g.ny + iy) * g.nx + ix;
@@ -109,13 +120,19 @@ __device__ __forceinline__ float2 grid_eval2(const void *__restrict__ maps, int 
                                              int toffb, float bx, float by, float bz, const GridConst &g) {
   const bool ina = (ax >= 0.f) & (ax <= g.fx1) & (ay >= 0.f) & (ay <= g.fy1) & (az >= 0.f) & (az <= g.fz1);
   const bool inb = (bx >= 0.f) & (bx <= g.fx1) & (by >= 0.f) & (by <= g.fy1) & (bz >= 0.f) & (bz <= g.fz1);
-  const int ixa = ina ? min((int)ax, g.nx - 2) : 0, iya = ina ? min((int)ay, g.ny - 2) : 0,
-            iza = ina ? min((int)az, g.nz - 2) : 0;
-  const int ixb = inb ? min((int)bx, g.nx - 2) : 0, iyb = inb ? min((int)by, g.ny - 2) : 0,
-            izb = inb ? min((int)bz, g.nz - 2) : 0;
-  const float2 fx = sub2(make_float2(ax, bx), make_float2((float)ixa, (float)ixb));
-  const float2 fy = sub2(make_float2(ay, by), make_float2((float)iya, (float)iyb));
-  const float2 fz = sub2(make_float2(az, bz), make_float2((float)iza, (float)izb));
+  const float M23 = 8388608.f;
+  const float txa = fminf(__fadd_rd(ax, M23), g.cx), tya = fminf(__fadd_rd(ay, M23), g.cy),
+              tza = fminf(__fadd_rd(az, M23), g.cz);
+  const float txb = fminf(__fadd_rd(bx, M23), g.cx), tyb = fminf(__fadd_rd(by, M23), g.cy),
+              tzb = fminf(__fadd_rd(bz, M23), g.cz);
+  const int ixa = ina ? __float_as_int(txa) - 0x4B000000 : 0, iya = ina ? __float_as_int(tya) - 0x4B000000 : 0,
+            iza = ina ? __float_as_int(tza) - 0x4B000000 : 0;
+  const int ixb = inb ? __float_as_int(txb) - 0x4B000000 : 0, iyb = inb ? __float_as_int(tyb) - 0x4B000000 : 0,
+            izb = inb ? __float_as_int(tzb) - 0x4B000000 : 0;
+  const float2 m23 = make_float2(M23, M23);
+  const float2 fx = sub2(make_float2(ax, bx), sub2(make_float2(txa, txb), m23));
+  const float2 fy = sub2(make_float2(ay, by), sub2(make_float2(tya, tyb), m23));
+  const float2 fz = sub2(make_float2(az, bz), sub2(make_float2(tza, tzb), m23));
   float va[8], vb[8];
   load_corners<MODE>(maps, ina ? toffa : 0, ixa, iya, iza, g, va);
   load_corners<MODE>(maps, inb ? toffb : 0, ixb, iyb, izb, g, vb);

@@ -131,6 +131,7 @@ struct GridConst {
   int nx, ny, nz;
   float fx1, fy1, fz1;  // n - 1 as float (inclusive upper bound)
   float penalty;
+  float cx, cy, cz;     // 2^23 + n - 2: the largest cell index in FP32 floor form
 };
 
 // One result slot in device memory (same bytes as ligate_pose).
@@ -261,6 +262,12 @@ size_t dock_kernel_local_bytes(int mode, int reg_cap);
 // Pocket kernels (pocket.cu).
 cudaError_t launch_corner_pack(const float *plain, int n_types, int nx, int ny, int nz,
                                int out_kind, void *out, cudaStream_t s);
+
+// Random corner-cell gathers over a whole corner-packed map (words = 16-byte
+// loads per cell): best time of three timed passes after a warm-up, and the
+// bytes one pass reads (pocket.cu).
+cudaError_t probe_gather(const void *cells, size_t n_cells, int words, int sms, double *ms_out,
+                         double *bytes_out);
 
 // Descriptor + surrogate kernels (surrogate.cu): declared there.
 

@@ -57,4 +57,63 @@ cudaError_t launch_corner_pack(const float *plain, int n_types, int nx, int ny, 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Ceiling of the docking kernel's map reads: every thread gathers corner
+// cells at pseudo-random positions (a 32-bit LCG per thread, scaled to the
+// cell count) of the whole corner-packed map, four independent loads in
+// flight, 16 B per gather (two loads of one 32 B cell for FP32).  The
+// exclusive-or of the loaded words is stored only if it equals a constant,
+// so the loads cannot be dropped and nothing is written in practice.
+template <int WORDS>  // 16-byte words per cell: 1 (BF16/FP16) or 2 (FP32)
+__global__ void __launch_bounds__(256) gather_probe_kernel(const uint4 *__restrict__ cells, unsigned n_cells,
+                                                           int per_thread, unsigned *__restrict__ sink) {
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned x = tid * 2654435761u + 0x9e3779b9u;
+  unsigned acc = 0;
+  for (int i = 0; i < per_thread; i += 4) {
+    uint4 v[4 * WORDS];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x = x * 1664525u + 1013904223u;
+      const unsigned c = (unsigned)(((unsigned long long)x * n_cells) >> 32);  // < n_cells
+#pragma unroll
+      for (int q = 0; q < WORDS; ++q) v[u * WORDS + q] = __ldg(cells + (size_t)c * WORDS + q);
+    }
+#pragma unroll
+    for (int u = 0; u < 4 * WORDS; ++u) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+  }
+  if (acc == 0x5bd1e995u) sink[tid & 255] = acc;
+}
+
+cudaError_t probe_gather(const void *cells, size_t n_cells, int words, int sms, double *ms_out,
+                         double *bytes_out) {
+  unsigned *sink = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaMalloc((void **)&sink, 256 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const int block = 256, grid = sms * 8, per_thread = 256;
+  const double gathers = (double)grid * block * per_thread;
+  double best = 1e30;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // rep 0 warms L2
+    e = cudaEventRecord(a, 0);
+    if (e != cudaSuccess) break;
+    if (words == 1)
+      gather_probe_kernel<1><<<grid, block>>>((const uint4 *)cells, (unsigned)n_cells, per_thread, sink);
+    else
+      gather_probe_kernel<2><<<grid, block>>>((const uint4 *)cells, (unsigned)n_cells, per_thread, sink);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaEventRecord(b, 0)) != cudaSuccess || (e = cudaEventSynchronize(b)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) break;
+    if (rep > 0) best = ms < best ? ms : best;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(sink);
+  *ms_out = best;
+  *bytes_out = gathers * 16.0 * words;
+  return e;
+}
+
 }  // namespace ligate

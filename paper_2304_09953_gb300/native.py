@@ -86,6 +86,7 @@ _SIGS = {
     "ligate_pocket_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                             ctypes.c_double, P, ctypes.c_int, ctypes.c_uint, P]),
     "ligate_pocket_destroy": (None, [P]),
+    "ligate_probe_gather": (ctypes.c_int, [P, ctypes.c_int, P]),
     "ligate_batch_create": (ctypes.c_int, [P, P]),
     "ligate_batch_destroy": (None, [P]),
     "ligate_batch_get_info": (ctypes.c_int, [P, P]),
@@ -500,3 +501,10 @@ def ligate_selector_labels(rescored, n, fail_label, out, stream=None):
     """rescored DEVICE RESCORED_DTYPE [n]; out DEVICE float32 [n]."""
     check(load().ligate_selector_labels(_ptr(rescored), int(n), float(fail_label), _ptr(out), stream),
           "ligate_selector_labels")
+
+
+def ligate_probe_gather(pocket, precision):
+    """Measured GB/s of random corner-cell gathers over the pocket's maps."""
+    v = ctypes.c_double()
+    check(load().ligate_probe_gather(pocket, int(precision), ctypes.byref(v)), "ligate_probe_gather")
+    return v.value
