@@ -204,29 +204,37 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     n = w.ligands.n
     desc = torch.empty((n, 256), dtype=torch.float32, device="cuda")
     pred_all = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def time_steps(step, k, idx_dev):
+        """2 warm-up steps, then --steps steps timed with CUDA events on the
+        stream (everything a step does is enqueued there); the kept indices
+        of the last step."""
+        for _ in range(2):
+            step()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(max(1, args.steps)):
+            step()
+        b.record(stream)
+        b.synchronize()
+        return k, idx_dev[:k].cpu().numpy(), a.elapsed_time(b) / 1000.0 / max(1, args.steps)
 
     def timed(keep):
+        """One triage step on the device, no host round trip: descriptors,
+        ensemble ranking into idx_dev, docking of those rows through the
+        chosen plan (ligate_plan_run_subset)."""
         k = int(np.ceil(n * keep - 1e-9))
         idx_dev = torch.empty(max(k, 1), dtype=torch.int32, device="cuda")
 
         def step():
             N.ligate_descriptors(bh.h, desc, sh)
             N.ligate_surrogate_rank_ensemble(sur, desc, n, keep, idx_dev, None, sh)
-            sel = idx_dev[:k].cpu().numpy()
-            pl = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile, subset=sel)
-            pl.result(sh)
-            pl.close()
-            return sel
+            N.ligate_plan_run_subset(chosen.h, idx_dev, k, None, sh)
 
-        for _ in range(2):
-            step()
-        times = []
-        for _ in range(max(1, args.steps)):
-            torch.cuda.synchronize()
-            a = time.perf_counter()
-            sel = step()
-            times.append(time.perf_counter() - a)
-        return k, sel, statistics.mean(times)
+        return time_steps(step, k, idx_dev)
 
     k, sel, t = timed(args.keep_frac)
     truth_scores = plain.result(sh)["score"][:, 0]
@@ -278,21 +286,9 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
             N.ligate_plan_run(cplan.h, None, sh)
             N.ligate_plan_best_scores(cplan.h, desc, 256, 233, sh)
             N.ligate_surrogate_rank_ensemble(sur_c, desc, n, keep, idx_dev, pred_all, sh)
-            sel = idx_dev[:k].cpu().numpy()
-            pl = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=tile, subset=sel)
-            pl.result(sh)
-            pl.close()
-            return sel
+            N.ligate_plan_run_subset(chosen.h, idx_dev, k, None, sh)
 
-        for _ in range(2):
-            step()
-        times = []
-        for _ in range(max(1, args.steps)):
-            torch.cuda.synchronize()
-            a = time.perf_counter()
-            sel = step()
-            times.append(time.perf_counter() - a)
-        return k, sel, statistics.mean(times)
+        return time_steps(step, k, idx_dev)
 
     kc5, selc5, tc5 = timed_c(args.keep_frac)
     pred_c = pred_all.cpu().numpy()

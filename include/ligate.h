@@ -248,6 +248,21 @@ ligate_status ligate_plan_create_subset(const ligate_pocket *pocket, const ligat
  * (host or device pointer) and, for host memory, the stream is
  * synchronised. */
 ligate_status ligate_plan_run(ligate_plan *plan, ligate_pose *out, void *stream);
+/* Enqueue one docking run of a SELECTION of the plan's ligands (paper
+ * Sec. 3.5: only the ligands a cheaper predictor ranks best are docked),
+ * chosen on the device: ligands is a DEVICE int32 array of n_sel batch
+ * indices (0 <= n_sel <= the plan's ligand count), e.g. the index output of
+ * ligate_surrogate_rank; output row r holds the poses of ligands[r], the
+ * same poses a full run gives that ligand.  The selected ligands' work
+ * items are taken, in the plan's largest-first order, from the plan's own
+ * item list on the device, so nothing waits for the host and no memory is
+ * allocated after the first call.  A repeated or out-of-range index gives an
+ * empty row (start ids -1).  The plan must have been created over the whole
+ * batch (ligate_plan_create); `out` as for ligate_plan_run, n_sel rows.
+ * After a subset run the post-docking stages below (refine, rescore,
+ * features, best scores, best passing) act on its n_sel rows. */
+ligate_status ligate_plan_run_subset(ligate_plan *plan, const int32_t *ligands, int n_sel, ligate_pose *out,
+                                     void *stream);
 ligate_status ligate_plan_output(const ligate_plan *plan, const ligate_pose **device_ptr);
 /* Best score (the first pose) of every output row r of the plan's last run
  * into DEVICE out[r * stride + column] (FP32; +inf for a row without a

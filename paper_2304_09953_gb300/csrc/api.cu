@@ -807,10 +807,29 @@ struct ligate_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ligate_work work;
+  bool is_subset = false;          // created over a subset (ligate_plan_create_subset)
+  // rows of the last run and their batch indices (the whole plan, or a
+  // ligate_plan_run_subset selection): what the post-docking stages read
+  int rows = 0;
+  const int32_t *cur_row_lig = nullptr;
+  // subset runs (ligate_plan_run_subset): the work model's inputs for the
+  // whole batch, the ligands in descending per-start cost and their size
+  // buckets (device, built on the first subset run), and the run's buffers
+  double model_W = 0.0, model_cb[LIGATE_N_BUCKETS] = {0};
+  int32_t *lig_by_cost = nullptr;
+  uint8_t *lig_bucket = nullptr;
+  size_t sub_cap = 0;              // capacity of sub_items (items) and sub_partial (items x K poses)
+  Item *sub_items = nullptr;
+  PoseOut *sub_partial = nullptr;
+  int *sub_count = nullptr, *sub_lig_items = nullptr, *sub_slot0 = nullptr;
+  int32_t *rowmap = nullptr, *sub_row_lig = nullptr;
 };
 
 static void free_plan(ligate_plan *pl) {
   if (!pl) return;
+  cudaFree(pl->sub_items); cudaFree(pl->sub_partial); cudaFree(pl->sub_count); cudaFree(pl->sub_lig_items);
+  cudaFree(pl->sub_slot0); cudaFree(pl->rowmap); cudaFree(pl->sub_row_lig); cudaFree(pl->lig_by_cost);
+  cudaFree(pl->lig_bucket);
   cudaFree(pl->p.memo1);
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
@@ -880,6 +899,7 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   ligate_plan *pl = new ligate_plan();
   pl->mode = mode;
   pl->n_ligands = sel ? n_sel : B->d.n_ligands;
+  pl->is_subset = sel != nullptr;
   for (int d = 0; d < 3; ++d) pl->origin[d] = P->d.origin[d];
   pl->h = P->d.spacing;
   pl->pocket = P;
@@ -1028,6 +1048,9 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   p.stats = pl->stats;
   p.partial = pl->partial;
   p.out = pl->out;
+  p.n_items_dev = nullptr;
+  pl->rows = n;
+  pl->cur_row_lig = pl->row_lig;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan setup"); }
   *out = pl;
   return LIGATE_OK;
@@ -1079,9 +1102,211 @@ extern "C" ligate_status ligate_plan_run(ligate_plan *pl, ligate_pose *out, void
   if (st != LIGATE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaGraphLaunch(pl->exec, s), "graph launch");
+  pl->rows = pl->n_ligands;
+  pl->cur_row_lig = pl->row_lig;
   if (out) {
     const size_t bytes = sizeof(PoseOut) * (size_t)pl->n_ligands * pl->p.K;
     if (bytes) CK(cudaMemcpyAsync(out, pl->out, bytes, cudaMemcpyDefault, s), "result copy");
+    if (is_host_ptr(out)) CK(cudaStreamSynchronize(s), "stream synchronize");
+  }
+  return LIGATE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Subset runs on the device: the selected ligands' work items are built on
+// the GPU, in the plan's descending per-start cost order and with chunk
+// sizes from the work model for the selection's size, so a selection
+// produced on the GPU (a triage ranking) is docked without a round trip to
+// the host.
+__global__ void subset_rows_kernel(const int32_t *__restrict__ ligands, int n_sel, int n_batch,
+                                   int32_t *__restrict__ rowmap) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_sel) return;
+  const int l = ligands[r];
+  if (l >= 0 && l < n_batch) rowmap[l] = r;  // a repeated ligand keeps one of its rows
+}
+
+// Rows whose index is out of range or repeated (rowmap holds another row
+// for it) get no items: their output is written empty here.  sub_row_lig is
+// the batch index of each row for the post-docking stages.
+__global__ void subset_meta_kernel(const int32_t *__restrict__ ligands, int n_sel, int n_batch,
+                                   const int32_t *__restrict__ rowmap, int32_t *__restrict__ sub_row_lig,
+                                   PoseOut *__restrict__ out, int K) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_sel) return;
+  const int l = ligands[r];
+  const bool ok = l >= 0 && l < n_batch && rowmap[l] == r;
+  sub_row_lig[r] = ok ? l : 0;
+  if (!ok)
+    for (int k = 0; k < K; ++k) {
+      PoseOut o;
+      o.score = __int_as_float(0x7f800000);
+      o.start_id = -1;
+      o.tors[0] = o.tors[1] = o.tors[2] = o.tors[3] = 0;
+      out[(size_t)r * K + k] = o;
+    }
+}
+
+struct SubsetChunks {
+  int c[LIGATE_N_BUCKETS];  // starts per work item of each size bucket
+};
+
+// Work items of the selected ligands (rowmap[l] >= 0), built by one CTA in
+// the plan's descending per-start cost order: a ligand's items are its
+// starts in chunks of its bucket's size, consecutive, with slots equal to
+// their positions; the block scan gives each selected ligand its first slot.
+__global__ void __launch_bounds__(1024) subset_build_kernel(const int32_t *__restrict__ lig_by_cost, int n,
+                                                            const int32_t *__restrict__ rowmap,
+                                                            const uint8_t *__restrict__ lig_bucket,
+                                                            const SubsetChunks ch, int n_starts,
+                                                            Item *__restrict__ items, int *__restrict__ lig_items,
+                                                            int *__restrict__ lig_slot0, int *__restrict__ count) {
+  __shared__ int wsum[32];
+  __shared__ int base, chunk_total;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+    const int i = c0 + threadIdx.x;
+    const int l = i < n ? lig_by_cost[i] : -1;
+    const int row = l >= 0 ? rowmap[l] : -1;
+    int chunk = 1, c = 0;
+    if (row >= 0) {
+      chunk = ch.c[lig_bucket[l]];
+      c = (n_starts + chunk - 1) / chunk;
+    }
+    int incl = c;  // inclusive scan of the item counts within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {  // exclusive prefix of the warp totals, and the chunk's total
+      const int v = lane < nw ? wsum[lane] : 0;
+      int w_incl = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, w_incl, o);
+        if (lane >= o) w_incl += t;
+      }
+      if (lane < nw) wsum[lane] = w_incl - v;
+      if (lane == 31) chunk_total = w_incl;
+    }
+    __syncthreads();
+    if (row >= 0) {
+      const int off = base + wsum[wid] + incl - c;
+      lig_items[row] = c;
+      lig_slot0[row] = off;
+      for (int q = 0; q < c; ++q) {
+        Item it;
+        it.ligand = l;
+        it.row = row;
+        it.s0 = q * chunk;
+        it.s1 = min(n_starts, (q + 1) * chunk);
+        it.slot = off + q;
+        it.pad[0] = it.pad[1] = it.pad[2] = 0;
+        items[off + q] = it;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += chunk_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+extern "C" ligate_status ligate_plan_run_subset(ligate_plan *pl, const int32_t *ligands, int n_sel,
+                                                ligate_pose *out, void *stream) {
+  NvtxRange nvtx_("ligate:plan_run_subset");
+  if (!pl) { set_error("plan_run_subset: NULL plan"); return LIGATE_ERR_INVALID; }
+  if (pl->is_subset) {
+    set_error("plan_run_subset: the plan was created over a subset; create it over the whole batch");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n_sel < 0 || n_sel > pl->n_ligands || (n_sel > 0 && !ligands)) {
+    set_error("plan_run_subset: need 0 <= n_sel <= %d ligands and a device index array", pl->n_ligands);
+    return LIGATE_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = pl->n_ligands;
+  const DockParams &p = pl->p;
+  const BatchDev &B = pl->batch->d;
+  cudaError_t e;
+  if (!pl->lig_by_cost) {  // once: cost order, buckets and the work model of the whole batch
+    std::vector<double> cost(n);
+    std::vector<int32_t> order(n);
+    std::vector<uint8_t> bucket(n);
+    double nb[LIGATE_N_BUCKETS] = {0};
+    for (int i = 0; i < n; ++i) {
+      double a, q;
+      start_work(B, i, p.S, a, q);
+      cost[i] = a + 0.35 * q + 40.0;
+      bucket[i] = (uint8_t)bucket_of(B.h_lig[i]);
+      pl->model_W += cost[i] * p.n_starts;
+      pl->model_cb[bucket[i]] += cost[i];
+      nb[bucket[i]] += 1.0;
+      order[i] = i;
+    }
+    for (int b = 0; b < LIGATE_N_BUCKETS; ++b) pl->model_cb[b] = nb[b] > 0 ? pl->model_cb[b] / nb[b] : 0.0;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    if ((e = dmalloc(&pl->lig_by_cost, n)) != cudaSuccess || (e = dmalloc(&pl->lig_bucket, n)) != cudaSuccess ||
+        (e = dmalloc(&pl->sub_count, 1)) != cudaSuccess || (e = dmalloc(&pl->sub_lig_items, n)) != cudaSuccess ||
+        (e = dmalloc(&pl->sub_slot0, n)) != cudaSuccess || (e = dmalloc(&pl->rowmap, n)) != cudaSuccess ||
+        (e = dmalloc(&pl->sub_row_lig, n)) != cudaSuccess ||
+        (n && (e = cudaMemcpy(pl->lig_by_cost, order.data(), 4 * (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (n && (e = cudaMemcpy(pl->lig_bucket, bucket.data(), (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess))
+      return cuda_fail(e, "plan_run_subset: set-up");
+  }
+  // chunks from the work model for a selection of n_sel average ligands
+  SubsetChunks ch;
+  int cmin = 2048;
+  const double P_warps = std::max(1.0, (double)pl->grid * pl->tile.warps_per_cta);
+  for (int b = 0; b < LIGATE_N_BUCKETS; ++b) {
+    double chunk = 512.0;
+    if (pl->model_cb[b] > 0) chunk = pl->model_W * ((double)n_sel / std::max(n, 1)) / (8.0 * P_warps * pl->model_cb[b]);
+    chunk = std::min(2048.0, std::max(128.0, chunk));
+    ch.c[b] = std::max(p.G, (int)chunk / p.G * p.G);
+    cmin = std::min(cmin, ch.c[b]);
+  }
+  const size_t need = (size_t)n_sel * (size_t)((p.n_starts + cmin - 1) / cmin);
+  if (need > pl->sub_cap) {  // grows only
+    cudaFree(pl->sub_items);
+    cudaFree(pl->sub_partial);
+    pl->sub_items = nullptr;
+    pl->sub_partial = nullptr;
+    pl->sub_cap = 0;
+    if ((e = dmalloc(&pl->sub_items, need)) != cudaSuccess || (e = dmalloc(&pl->sub_partial, need * p.K)) != cudaSuccess)
+      return cuda_fail(e, "plan_run_subset: allocation");
+    pl->sub_cap = need;
+  }
+  pl->rows = n_sel;
+  pl->cur_row_lig = pl->sub_row_lig;
+  if (n_sel > 0) {
+    if ((e = cudaMemsetAsync(pl->rowmap, 0xff, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess)
+      return cuda_fail(e, "plan_run_subset");
+    const int blocks = (n_sel + 255) / 256;
+    subset_rows_kernel<<<blocks, 256, 0, s>>>(ligands, n_sel, B.n_ligands, pl->rowmap);
+    subset_build_kernel<<<1, 1024, 0, s>>>(pl->lig_by_cost, n, pl->rowmap, pl->lig_bucket, ch, p.n_starts,
+                                           pl->sub_items, pl->sub_lig_items, pl->sub_slot0, pl->sub_count);
+    subset_meta_kernel<<<blocks, 256, 0, s>>>(ligands, n_sel, B.n_ligands, pl->rowmap, pl->sub_row_lig, pl->out,
+                                              p.K);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "plan_run_subset: selection");
+    if ((e = cudaMemsetAsync(pl->counters, 0, sizeof(int) * ((size_t)n_sel + 1), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(pl->stats, 0, 3 * sizeof(unsigned long long), s)) != cudaSuccess)
+      return cuda_fail(e, "plan_run_subset");
+    DockParams q = p;
+    q.items = pl->sub_items;
+    q.n_items = 0;
+    q.n_items_dev = pl->sub_count;
+    q.lig_items = pl->sub_lig_items;
+    q.lig_slot0 = pl->sub_slot0;
+    q.partial = pl->sub_partial;
+    if ((e = launch_dock(pl->mode, pl->tile.reg_cap, q, pl->grid, pl->block, pl->smem, s)) != cudaSuccess)
+      return cuda_fail(e, "plan_run_subset: docking kernel");
+  }
+  if (out && n_sel > 0) {
+    const size_t bytes = sizeof(PoseOut) * (size_t)n_sel * p.K;
+    CK(cudaMemcpyAsync(out, pl->out, bytes, cudaMemcpyDefault, s), "result copy");
     if (is_host_ptr(out)) CK(cudaStreamSynchronize(s), "stream synchronize");
   }
   return LIGATE_OK;
@@ -1202,7 +1427,7 @@ extern "C" ligate_status ligate_plan_best_scores(const ligate_plan *pl, float *o
     set_error("plan_best_scores: bad arguments");
     return LIGATE_ERR_INVALID;
   }
-  const int n = pl->n_ligands;
+  const int n = pl->rows;
   if (n == 0) return LIGATE_OK;
   best_scores_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(pl->out, n, pl->p.K, out, stride, column);
   cudaError_t e = cudaGetLastError();
@@ -1272,14 +1497,14 @@ extern "C" ligate_status ligate_plan_refine(const ligate_plan *pl, int iteration
     set_error("plan_refine: iterations must be 0..%d and eta0 finite and > 0", LIGATE_REFINE_MAX_ITERS);
     return LIGATE_ERR_INVALID;
   }
-  const int n = pl->n_ligands * pl->p.K;
+  const int n = pl->rows * pl->p.K;
   if (n == 0) return LIGATE_OK;
   if (refine_smem_bytes(pl->p.nmax) * 4 > 227 * 1024) {
     set_error("plan_refine: ligands too large for the refinement kernel's shared memory");
     return LIGATE_ERR_UNSUPPORTED;
   }
   cudaError_t e = launch_refine(2, pl->p, pl->origin, pl->h, n, nullptr, nullptr,
-                                reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, iterations,
+                                reinterpret_cast<const ligate_pose *>(pl->out), pl->cur_row_lig, iterations,
                                 eta0, out, nullptr, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "plan_refine");
   return LIGATE_OK;
@@ -1342,14 +1567,14 @@ extern "C" ligate_status ligate_plan_rescore(const ligate_plan *pl, ligate_resco
   RecParams r;
   ligate_status st = rec_params(pl->pocket, pl->batch, r, "plan_rescore");
   if (st != LIGATE_OK) return st;
-  const int n = pl->n_ligands * pl->p.K;
+  const int n = pl->rows * pl->p.K;
   if (n == 0) return LIGATE_OK;
   if (rescore_smem_bytes(pl->p, r, 1) > 227 * 1024) {
     set_error("plan_rescore: %d receptor atoms do not fit in shared memory", r.n_rec);
     return LIGATE_ERR_UNSUPPORTED;
   }
   cudaError_t e = launch_rescore(pl->p, r, n, nullptr, nullptr, nullptr,
-                                 reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, nullptr, out,
+                                 reinterpret_cast<const ligate_pose *>(pl->out), pl->cur_row_lig, nullptr, out,
                                  (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "plan_rescore");
   return LIGATE_OK;
@@ -1399,7 +1624,7 @@ extern "C" ligate_status ligate_plan_rescore_refined(const ligate_plan *pl, cons
   RecParams r;
   ligate_status st = rec_params(pl->pocket, pl->batch, r, "plan_rescore_refined");
   if (st != LIGATE_OK) return st;
-  const int n = pl->n_ligands * pl->p.K;
+  const int n = pl->rows * pl->p.K;
   if (n == 0) return LIGATE_OK;
   if (rescore_smem_bytes(pl->p, r, 1) > 227 * 1024) {
     set_error("plan_rescore_refined: %d receptor atoms do not fit in shared memory", r.n_rec);
@@ -1446,10 +1671,10 @@ extern "C" ligate_status ligate_pose_features(const ligate_pocket *P, const liga
 extern "C" ligate_status ligate_plan_pose_features(const ligate_plan *pl, float *out, void *stream) {
   NvtxRange nvtx_("ligate:plan_pose_features");
   if (!pl || !out) { set_error("plan_pose_features: NULL argument"); return LIGATE_ERR_INVALID; }
-  const int n = pl->n_ligands * pl->p.K;
+  const int n = pl->rows * pl->p.K;
   if (n == 0) return LIGATE_OK;
   cudaError_t e = launch_pose_features(pl->p, n, nullptr, nullptr, nullptr,
-                                       reinterpret_cast<const ligate_pose *>(pl->out), pl->row_lig, out,
+                                       reinterpret_cast<const ligate_pose *>(pl->out), pl->cur_row_lig, out,
                                        (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "plan_pose_features");
   return LIGATE_OK;
@@ -1457,11 +1682,11 @@ extern "C" ligate_status ligate_plan_pose_features(const ligate_plan *pl, float 
 
 extern "C" ligate_status ligate_plan_best_passing(const ligate_plan *pl, const ligate_rescored *rescored,
                                                   int32_t *idx_out, float *energy_out, void *stream) {
-  if (!pl || ((!rescored || !idx_out) && pl->n_ligands > 0)) {
+  if (!pl || ((!rescored || !idx_out) && pl->rows > 0)) {
     set_error("plan_best_passing: NULL argument");
     return LIGATE_ERR_INVALID;
   }
-  cudaError_t e = launch_best_passing(rescored, pl->n_ligands, pl->p.K, idx_out, energy_out, (cudaStream_t)stream);
+  cudaError_t e = launch_best_passing(rescored, pl->rows, pl->p.K, idx_out, energy_out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "plan_best_passing");
   return LIGATE_OK;
 }

@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
   float *const m1 = p.memo1 ? p.memo1 + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * p.m1max * S * S
                             : nullptr;
 
+  const int n_items = p.n_items_dev ? __ldcg(p.n_items_dev) : p.n_items;
   int cur = -1, n_memo = 0;
   LigDesc d;
   float clash_ref = 0.f;
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
     int it = 0;
     if (lane == 0) it = atomicAdd(p.queue, 1);
     it = __shfl_sync(FULL, it, 0);
-    if (it >= p.n_items) break;
+    if (it >= n_items) break;
     const Item item = p.items[it];
     if (item.ligand != cur) {
       __syncwarp();

@@ -182,6 +182,7 @@ struct DockParams {
   // work queue
   const Item *items;
   int n_items;
+  const int *n_items_dev;  // optional: the run's item count in device memory (subset runs); else n_items
   const int *lig_items;    // [n_ligands] items per ligand
   const int *lig_slot0;    // [n_ligands] first partial slot of each ligand
   int *queue;              // [1] next item

@@ -61,32 +61,48 @@ class Plan:
         else:
             self.n = len(subset)
             self.h = N.ligate_plan_create_subset(pocket.h, batch.h, self.s, subset, tile)
+        self.rows = self.n  # rows of the last run
 
     def run(self, stream=None):
         N.ligate_plan_run(self.h, None, stream)
+        self.rows = self.n
 
     def result(self, stream=None) -> np.ndarray:
         out = np.zeros((self.n, self.k), N.POSE_DTYPE)
         N.ligate_plan_run(self.h, out, stream)
+        self.rows = self.n
+        return out
+
+    def run_subset(self, ligands, n_sel=None, stream=None, result=False):
+        """Dock a device-chosen selection of this plan's ligands
+        (ligate_plan_run_subset): ligands is a CUDA int32 tensor (or a host
+        array, uploaded); with result=True returns POSE_DTYPE [n_sel, K]."""
+        import torch
+        if isinstance(ligands, np.ndarray):
+            ligands = torch.from_numpy(np.ascontiguousarray(ligands, np.int32)).cuda()
+        n_sel = int(ligands.numel()) if n_sel is None else int(n_sel)
+        out = np.zeros((n_sel, self.k), N.POSE_DTYPE) if result else None
+        N.ligate_plan_run_subset(self.h, ligands, n_sel, out, stream)
+        self.rows = n_sel
         return out
 
     def refine(self, iterations=32, eta0=0.1, stream=None) -> np.ndarray:
         """Gradient-descent refinement of every pose of the last run
         (ligate_plan_refine); returns REFINED_DTYPE [n, K] on the host."""
         import torch
-        buf = torch.empty(self.n * self.k * N.REFINED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        buf = torch.empty(self.rows * self.k * N.REFINED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         N.ligate_plan_refine(self.h, iterations, eta0, buf, stream)
         torch.cuda.synchronize()
-        return buf.cpu().numpy().view(N.REFINED_DTYPE).reshape(self.n, self.k)
+        return buf.cpu().numpy().view(N.REFINED_DTYPE).reshape(self.rows, self.k)
 
     def rescore_exact(self, stream=None) -> np.ndarray:
         """Exact receptor term + clash and the filter flags of every pose of
         the last run (ligate_plan_rescore); RESCORED_DTYPE [n, K] on the host."""
         import torch
-        buf = torch.empty(self.n * self.k * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        buf = torch.empty(self.rows * self.k * N.RESCORED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         N.ligate_plan_rescore(self.h, buf, stream)
         torch.cuda.synchronize()
-        return buf.cpu().numpy().view(N.RESCORED_DTYPE).reshape(self.n, self.k)
+        return buf.cpu().numpy().view(N.RESCORED_DTYPE).reshape(self.rows, self.k)
 
     def best_passing(self, rescored, stream=None):
         """Per ligand the slot of its lowest-energy pose that passes the
@@ -95,11 +111,11 @@ class Plan:
         CUDA byte tensor), by ligate_plan_best_passing."""
         import torch
         buf = _device_bytes(rescored)
-        idx = torch.empty(max(self.n, 1), dtype=torch.int32, device="cuda")
-        en = torch.empty(max(self.n, 1), dtype=torch.float32, device="cuda")
+        idx = torch.empty(max(self.rows, 1), dtype=torch.int32, device="cuda")
+        en = torch.empty(max(self.rows, 1), dtype=torch.float32, device="cuda")
         N.ligate_plan_best_passing(self.h, buf, idx, en, stream)
         torch.cuda.synchronize()
-        return idx[:self.n].cpu().numpy(), en[:self.n].cpu().numpy()
+        return idx[:self.rows].cpu().numpy(), en[:self.rows].cpu().numpy()
 
     def device_output(self) -> int:
         """Device address of the last run's ligate_pose[n][K] result."""

@@ -94,6 +94,7 @@ _SIGS = {
     "ligate_plan_create": (ctypes.c_int, [P, P, P, P, P]),
     "ligate_plan_create_subset": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, P]),
     "ligate_plan_run": (ctypes.c_int, [P, P, P]),
+    "ligate_plan_run_subset": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
     "ligate_plan_output": (ctypes.c_int, [P, P]),
     "ligate_plan_best_scores": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, P]),
     "ligate_plan_get_tile": (ctypes.c_int, [P, P, P]),
@@ -508,3 +509,9 @@ def ligate_probe_gather(pocket, precision):
     v = ctypes.c_double()
     check(load().ligate_probe_gather(pocket, int(precision), ctypes.byref(v)), "ligate_probe_gather")
     return v.value
+
+
+def ligate_plan_run_subset(plan, ligands, n_sel, out=None, stream=None):
+    """ligands: DEVICE int32 [n_sel] batch indices; out: optional host/device POSE_DTYPE [n_sel][K]."""
+    check(load().ligate_plan_run_subset(plan, _ptr(ligands), int(n_sel), _ptr(out), stream),
+          "ligate_plan_run_subset")

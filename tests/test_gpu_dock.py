@@ -309,3 +309,36 @@ def test_pose_coords_are_the_exact_poses_within_the_fp32_envelope(batched_small)
     q = np.quantile(ratios, [0.5, 0.99, 1.0])
     print(f"coordinate error / (u X): median {q[0]:.1f}, 99% {q[1]:.1f}, max {q[2]:.1f}; max by R "
           + ", ".join(f"{k}:{v:.0f}" for k, v in sorted(by_r.items())))
+
+
+def test_device_subset_run_equals_rows_of_full_run(batched_small):
+    """ligate_plan_run_subset: a selection given on the device docks to the
+    same poses as the full run's rows, twice in a row and for a new
+    selection; a repeated ligand keeps one of its rows (the other is empty),
+    an out-of-range index gives an empty row; the post-docking stages then
+    act on the selection's rows."""
+    w = batched_small
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    pl = D.Plan(ph, bh, w.sampling, mode="bf16")
+    full = pl.result()
+    for sel in (np.array([63, 5, 17, 0, 42, 7], np.int32), np.array([63, 5, 17, 0, 42, 7], np.int32),
+                np.arange(64, dtype=np.int32)[::-3]):
+        got = pl.run_subset(sel, result=True)
+        assert np.array_equal(got, full[sel])
+    bad = np.array([4, 4, 999, -1, 6], np.int32)
+    got = pl.run_subset(bad, result=True)
+    empty = got["start_id"][:, 0] == -1
+    assert list(empty[2:]) == [True, True, False]
+    assert empty[0] != empty[1]
+    j = 0 if not empty[0] else 1
+    assert np.array_equal(got[j], full[4]) and np.array_equal(got[4], full[6])
+    assert np.all(np.isinf(got[empty]["score"]))
+    rs = pl.rescore_exact()
+    assert rs.shape == (5, w.sampling.top_k)
+    assert np.all(np.isinf(rs[empty]["energy"])) and np.all(np.isfinite(rs[~empty]["energy"]))
+    pl.result()
+    ref = pl.rescore_exact()
+    np.testing.assert_array_equal(rs[4], ref[6])
+    with pytest.raises(N.LigateError):
+        D.Plan(ph, bh, w.sampling, mode="bf16", subset=np.array([1, 2], np.int32)).run_subset(np.array([0], np.int32))
