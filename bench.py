@@ -520,7 +520,19 @@ def main():
     from paper_2304_09953_gb300 import native as N
     from paper_2304_09953_gb300.workload import make_workload
 
-    w = make_workload(args.workload, n_ligands=args.n_ligands, first_index=rank * args.n_ligands)
+    if ws > 1:
+        # the job's library is ws x n_ligands ligands, split into contiguous
+        # ranges of equal precomputed pose count (weak scaling: per-rank work
+        # stays the same as N grows); no collective on the data path
+        from paper_2304_09953_gb300.distributed import shard
+        from paper_2304_09953_gb300.workload import poses_per_ligand
+        gw = make_workload(args.workload, n_ligands=ws * args.n_ligands)
+        first, count = shard(gw.ligands.n, rank, ws, poses_per_ligand(gw.ligands, gw.sampling))
+        del gw
+        w = make_workload(args.workload, n_ligands=count, first_index=first)
+    else:
+        w = make_workload(args.workload, n_ligands=args.n_ligands)
+    n_job = ws * args.n_ligands  # ligands of the whole job
     tune_path = os.path.join(tempfile.gettempdir(), f"ligate_tune_{os.getpid()}.txt")
     os.environ["LIGATE_TUNE_CACHE"] = tune_path
     ph = D.PocketHandle(w.pocket)
@@ -563,13 +575,13 @@ def main():
     clock_info = clocks.stop()
     ms_plain = timed(plain, args.steps)
     torch.cuda.synchronize()
-    from paper_2304_09953_gb300.distributed import max_over_ranks
+    from paper_2304_09953_gb300.distributed import max_over_ranks, sum_over_ranks
     t_chosen = max_over_ranks(sum(ms_chosen) / 1000.0, device="cuda")  # slowest rank
     work = chosen.work()
     work_plain = plain.work()
-    n_lig = args.n_ligands
-    value = ws * n_lig * args.steps / t_chosen
-    poses_s = ws * work.poses * args.steps / t_chosen
+    n_lig = w.ligands.n  # this rank's ligands
+    value = n_job * args.steps / t_chosen
+    poses_s = sum_over_ranks(work.poses, device="cuda") * args.steps / t_chosen
     mean_ms = t_chosen * 1000 / args.steps
     S = w.sampling.torsion_steps
     props = torch.cuda.get_device_properties(dev)
@@ -606,7 +618,7 @@ def main():
             t0 = time.perf_counter()
             N.ligate_dock_batch(ph.h, lig, s_chosen, out, sh)
             et.append(time.perf_counter() - t0)
-        e2e = {"value": ws * n_lig / statistics.mean(et), "unit": "ligands/s",
+        e2e = {"value": n_job / max_over_ranks(statistics.mean(et)), "unit": "ligands/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes),
                "ms_per_step": 1000 * statistics.mean(et)}
 
@@ -619,8 +631,8 @@ def main():
             N.ligate_plan_run(mplan.h, None, sh)
         mms = statistics.mean(timed(mplan, args.steps))
         mt_, _ = mplan.tile()
-        model = {"value": ws * n_lig / (mms / 1000), "unit": "ligands/s", "ms_per_step": mms,
-                 "vs_autotuned": (ws * n_lig / (mms / 1000)) / value,
+        model = {"value": n_job / (mms / 1000), "unit": "ligands/s", "ms_per_step": mms,
+                 "vs_autotuned": (n_job / (mms / 1000)) / value,
                  "tile": {"warps_per_cta": mt_.warps_per_cta, "ctas_per_sm": mt_.ctas_per_sm,
                           "starts_per_item": list(mt_.starts_per_item), "reg_cap": mt_.reg_cap}}
         mplan.close()
@@ -734,7 +746,7 @@ def main():
                             "starts_per_item": list(t_.starts_per_item), "reg_cap": t_.reg_cap},
                    "autotune_s": round(tune_s, 2), "parallelism": f"replicas x{ws}"},
         "poses_per_s": poses_s,
-        "plain": {"value": ws * n_lig / (plain_ms / 1000), "unit": "ligands/s",
+        "plain": {"value": n_job / (plain_ms / 1000), "unit": "ligands/s",
                   "poses_per_s": ws * work_plain.poses / (plain_ms / 1000), "ms_per_step": plain_ms,
                   "form": "fp32 plain maps, default tile, no rescore",
                   "roofline_frac": plain_alg / (plain_ms / 1000) / 1e12 / peak,
@@ -748,7 +760,7 @@ def main():
                      "count": "algorithmic: 50 FLOP per atom evaluation of a unique pose + 12 FLOP per "
                               "crossing clash pair of a unique trial",
                      "achieved_executed": achieved_exec, "frac_executed": achieved_exec / peak,
-                     "traffic": kernel_traffic(args.workload, n_lig),
+                     "traffic": kernel_traffic(args.workload, n_job),
                      "traffic_unit": "bytes per launch (ncu dram read + write of this kernel revision; "
                                      "null until captured for it)",
                      "peak_note": f"FP32 FMA peak derived: {n_sm} SMs x 128 lanes x 2 x {mhz:.0f} MHz "

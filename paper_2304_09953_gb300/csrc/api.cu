@@ -308,7 +308,12 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     return LIGATE_ERR_INVALID;
   }
   // adjacency as CSR (atom a's neighbours at nbr[off[a] .. off[a + 1]), ascending)
-  std::vector<int> off(n + 1, 0), nbr(2 * (size_t)nb), fill;
+  // per-thread scratch, reused from ligand to ligand (packing runs on many
+  // threads; the allocator would otherwise dominate)
+  thread_local std::vector<int> off, nbr, fill, pos, parent, size, stack;
+  thread_local std::vector<char> seen;
+  off.assign(n + 1, 0);
+  nbr.resize(2 * (size_t)nb);
   for (int b = b0; b < b1; ++b) {
     const int x = L->bonds[2 * b], y = L->bonds[2 * b + 1];
     if (x < 0 || y < 0 || x >= n || y >= n || x == y) {
@@ -326,11 +331,15 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     nbr[fill[y]++] = x;
   }
   for (int a = 0; a < n; ++a) std::sort(nbr.begin() + off[a], nbr.begin() + off[a + 1]);
-  std::vector<int> pos(n, -1), order, parent(n, -1), size(n, 1), stack;
+  pos.assign(n, -1);
+  parent.assign(n, -1);
+  size.assign(n, 1);
+  stack.clear();
+  std::vector<int> order;
   order.reserve(n);
   stack.push_back(0);
   parent[0] = -1;
-  std::vector<char> seen(n, 0);
+  seen.assign(n, 0);
   seen[0] = 1;
   while (!stack.empty()) {
     const int a = stack.back();
@@ -401,7 +410,8 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
     uint32_t *row = P.elig.data() + (size_t)pos[s0] * P.words;
     for (int w = 0; w < P.words; ++w) row[w] = ~0u;
     if (n & 31) row[P.words - 1] = (1u << (n & 31)) - 1u;
-    auto near = [row, &pos](int a) { const int q = pos[a]; row[q >> 5] &= ~(1u << (q & 31)); };
+    const int *pos_of = pos.data();
+    auto near = [row, pos_of](int a) { const int q = pos_of[a]; row[q >> 5] &= ~(1u << (q & 31)); };
     near(s0);
     for (int qa = off[s0]; qa < off[s0 + 1]; ++qa) {
       const int a = nbr[qa];
@@ -421,51 +431,69 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   // separates j when exactly one of j and v lies in e's subtree [v_e, end_e)):
   // none, then the most frequent single bond e1, then the rest
   P.cand.clear();
-  std::vector<uint16_t> one, rest;
-  std::vector<int> sep_by, n_by(br.size()), nsep_of(n), last_of(n);
+  // bitsets over DFS positions (at most LIGATE_MAX_ATOMS bits): for bond bi,
+  // the atoms no earlier bond separates from the moved subtree, those exactly
+  // one separates (and which one), and the rest; a candidate's group is its
+  // fixed atom's
+  constexpr int MW = LIGATE_MAX_ATOMS / 32;
+  auto range_bits = [&](int lo, int hi, uint32_t *bits) {  // bits of [lo, hi)
+    for (int wd = 0; wd < P.words; ++wd) {
+      const int a = std::max(lo, 32 * wd) - 32 * wd, z = std::min(hi, 32 * wd + 32) - 32 * wd;
+      bits[wd] = a >= z ? 0u : ((z - a == 32 ? ~0u : (1u << (z - a)) - 1u) << a);
+    }
+  };
+  thread_local std::vector<uint32_t> sep;  // [bond e][MW]: atoms e separates from the current bond's subtree
+  sep.assign(br.size() * MW, 0u);
   for (size_t bi = 0; bi < br.size(); ++bi) {
     BondRec &r = br[bi];
     r.cand_off = (int)P.cand.size();
-    one.clear();
-    rest.clear();
-    sep_by.clear();
-    std::fill(n_by.begin(), n_by.end(), 0);
-    // separating earlier bonds of every atom j (count, and the last one)
-    std::fill(nsep_of.begin(), nsep_of.end(), 0);
-    std::fill(last_of.begin(), last_of.end(), -1);
+    uint32_t once[MW] = {0}, twice[MW] = {0};
     for (size_t e = 0; e < bi; ++e) {
-      const bool v_in = r.v >= br[e].v && r.v < br[e].end;
-      for (int j = 0; j < n; ++j)
-        if ((j >= br[e].v && j < br[e].end) != v_in) { ++nsep_of[j]; last_of[j] = (int)e; }
-    }
-    for (int i = r.v + 1; i < r.end; ++i)
+      uint32_t *se = &sep[e * MW];
+      range_bits(br[e].v, br[e].end, se);
+      if (r.v >= br[e].v && r.v < br[e].end)
+        for (int wd = 0; wd < P.words; ++wd) se[wd] = ~se[wd];
+      if (n & 31) se[P.words - 1] &= (1u << (n & 31)) - 1u;
       for (int wd = 0; wd < P.words; ++wd) {
-        // eligible partners of i in this word, minus the moved range and u
-        uint32_t m = P.elig[(size_t)i * P.words + wd];
-        const int lo = std::max(r.v, 32 * wd), hi = std::min(r.end, 32 * wd + 32);
-        if (lo < hi) m &= ~((hi - lo == 32 ? ~0u : (1u << (hi - lo)) - 1u) << (lo - 32 * wd));
-        if ((r.u >> 5) == wd) m &= ~(1u << (r.u & 31));
-        for (; m; m &= m - 1) {  // ascending j
-          const int j = 32 * wd + __builtin_ctz(m);
-          const int nsep = nsep_of[j], last = last_of[j];
-          const uint16_t c = (uint16_t)(i | (j << 8));
-          if (nsep == 0) {
-            P.cand.push_back(c);
-          } else {
-            one.push_back(c);
-            sep_by.push_back(nsep == 1 ? last : -1);
-            if (nsep == 1) ++n_by[last];
-          }
-        }
+        twice[wd] |= once[wd] & se[wd];
+        once[wd] |= se[wd];
       }
+    }
+    // eligible partners of moved atom i: clash-eligible, outside the moved
+    // range [v, end) and not u
+    uint32_t keep[MW];
+    range_bits(r.v, r.end, keep);
+    for (int wd = 0; wd < P.words; ++wd) keep[wd] = ~keep[wd];
+    keep[r.u >> 5] &= ~(1u << (r.u & 31));
+    auto partners = [&](int i, int wd) { return P.elig[(size_t)i * P.words + wd] & keep[wd]; };
+    auto emit = [&](const uint32_t *group) {  // i ascending, then j ascending
+      for (int i = r.v + 1; i < r.end; ++i)
+        for (int wd = 0; wd < P.words; ++wd)
+          for (uint32_t m = partners(i, wd) & group[wd]; m; m &= m - 1)
+            P.cand.push_back((uint16_t)(i | ((32 * wd + __builtin_ctz(m)) << 8)));
+    };
+    uint32_t none[MW];
+    for (int wd = 0; wd < P.words; ++wd) none[wd] = ~once[wd];
+    emit(none);
     r.n_cand0 = (int)P.cand.size() - r.cand_off;
+    // e1: the earlier bond that alone separates the most candidates (ties:
+    // the earlier bond)
     r.e1 = -1;
-    for (size_t e = 0; e < bi; ++e)
-      if (n_by[e] > 0 && (r.e1 < 0 || n_by[e] > n_by[r.e1])) r.e1 = (int)e;
-    for (size_t q = 0; q < one.size(); ++q)
-      (sep_by[q] >= 0 && sep_by[q] == r.e1 ? P.cand : rest).push_back(one[q]);
+    int best = 0;
+    for (size_t e = 0; e < bi; ++e) {
+      int cnt = 0;
+      for (int i = r.v + 1; i < r.end; ++i)
+        for (int wd = 0; wd < P.words; ++wd)
+          cnt += __builtin_popcount(partners(i, wd) & sep[e * MW + wd] & ~twice[wd]);
+      if (cnt > best) { best = cnt; r.e1 = (int)e; }
+    }
+    uint32_t g1[MW] = {0}, rest_bits[MW];
+    if (r.e1 >= 0)
+      for (int wd = 0; wd < P.words; ++wd) g1[wd] = sep[r.e1 * MW + wd] & ~twice[wd];
+    for (int wd = 0; wd < P.words; ++wd) rest_bits[wd] = once[wd] & ~g1[wd];
+    emit(g1);
     r.n_cand1 = (int)P.cand.size() - r.cand_off - r.n_cand0;
-    P.cand.insert(P.cand.end(), rest.begin(), rest.end());
+    emit(rest_bits);
     r.n_cand = (int)P.cand.size() - r.cand_off;
   }
   for (size_t bi = 2, slot = 0; bi < br.size(); ++bi)  // table slots of bonds 2, 3, ...
@@ -538,23 +566,27 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   std::vector<std::string> errs(n);
   const unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
   const int nthreads = n < 256 ? 1 : (int)nt;
-  std::atomic<int> next(0);
-  auto worker = [&]() {
-    char buf[256];
-    for (;;) {
-      const int i0 = next.fetch_add(64);
-      if (i0 >= n) break;
-      for (int i = i0; i < std::min(n, i0 + 64); ++i) {
-        buf[0] = 0;
-        st[i] = pack_one(L, i, packs[i], buf, sizeof(buf));
-        if (st[i] != LIGATE_OK) errs[i] = buf;
+  // fn(i) for every ligand, blocks of 64 ligands handed out to the threads
+  auto parallel = [&](auto fn) {
+    std::atomic<int> next(0);
+    auto worker = [&]() {
+      for (;;) {
+        const int i0 = next.fetch_add(64);
+        if (i0 >= n) break;
+        for (int i = i0; i < std::min(n, i0 + 64); ++i) fn(i);
       }
-    }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nthreads; ++t) th.emplace_back(worker);
+    worker();
+    for (auto &t : th) t.join();
   };
-  std::vector<std::thread> th;
-  for (int t = 1; t < nthreads; ++t) th.emplace_back(worker);
-  worker();
-  for (auto &t : th) t.join();
+  parallel([&](int i) {
+    char buf[256];
+    buf[0] = 0;
+    st[i] = pack_one(L, i, packs[i], buf, sizeof(buf));
+    if (st[i] != LIGATE_OK) errs[i] = buf;
+  });
   for (int i = 0; i < n; ++i)
     if (st[i] != LIGATE_OK) {
       set_error("batch_create: %s", errs[i].c_str());
@@ -597,15 +629,17 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   d.h_types.resize(na);
   d.h_cand.resize(nc);
   d.h_order.resize(na);
-  for (int i = 0; i < n; ++i) {
+  parallel([&](int i) {  // each ligand into its place, then release its pieces
     const LigDesc &ld = d.h_lig[i];
-    for (int q = 0; q < ld.n_atoms; ++q) d.h_order[ld.atom_base + q] = (uint8_t)packs[i].order[q];
-    std::copy(packs[i].atoms.begin(), packs[i].atoms.end(), atoms.begin() + ld.atom_base);
-    std::copy(packs[i].types.begin(), packs[i].types.end(), d.h_types.begin() + ld.atom_base);
-    std::copy(packs[i].bonds.begin(), packs[i].bonds.end(), d.h_bonds.begin() + ld.bond_base);
-    std::copy(packs[i].elig.begin(), packs[i].elig.end(), d.h_elig.begin() + ld.elig_base);
-    std::copy(packs[i].cand.begin(), packs[i].cand.end(), d.h_cand.begin() + ld.cand_base);
-  }
+    LigPack &pk = packs[i];
+    for (int q = 0; q < ld.n_atoms; ++q) d.h_order[ld.atom_base + q] = (uint8_t)pk.order[q];
+    std::copy(pk.atoms.begin(), pk.atoms.end(), atoms.begin() + ld.atom_base);
+    std::copy(pk.types.begin(), pk.types.end(), d.h_types.begin() + ld.atom_base);
+    std::copy(pk.bonds.begin(), pk.bonds.end(), d.h_bonds.begin() + ld.bond_base);
+    std::copy(pk.elig.begin(), pk.elig.end(), d.h_elig.begin() + ld.elig_base);
+    std::copy(pk.cand.begin(), pk.cand.end(), d.h_cand.begin() + ld.cand_base);
+    pk = LigPack();
+  });
   cudaError_t e;
   if ((e = dmalloc(&d.lig, n)) != cudaSuccess || (e = dmalloc(&d.atoms, na)) != cudaSuccess ||
       (e = dmalloc(&d.bonds, nb)) != cudaSuccess || (e = dmalloc(&d.elig, ne)) != cudaSuccess ||
@@ -734,7 +768,8 @@ const void *mode_maps(const PocketDev &d, int mode) {
 
 // Start frames + everything of DockParams that does not depend on items.
 ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const ligate_sampling *s,
-                          int mode, DockParams &p, float **rot, float **anc, float **quat) {
+                          int mode, DockParams &p, float **rot, float **anc, float **quat,
+                          const float *rot_in = nullptr, const float *anc_in = nullptr) {
   const PocketDev &d = P->d;
   memset(&p, 0, sizeof(p));
   p.lig = B->d.lig; p.atoms = B->d.atoms; p.bonds = B->d.bonds; p.elig = B->d.elig;
@@ -761,6 +796,12 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   p.nmax = std::max(32, (B->d.max_atoms + 31) / 32 * 32);
   p.wmax = p.nmax / 32;
   p.rmax = B->d.max_rot;
+  if (rot_in && anc_in) {  // frames of the same sampling and pocket, owned by another plan
+    *rot = *anc = *quat = nullptr;
+    p.rot = rot_in;
+    p.anc = anc_in;
+    return LIGATE_OK;
+  }
   std::vector<float> qf(4 * (size_t)s->n_orient);
   for (size_t i = 0; i < qf.size(); ++i) qf[i] = (float)s->orientations[i];
   CK(dmalloc(quat, qf.size()), "quaternions");
@@ -879,9 +920,18 @@ static void model_chunks(const BatchDev &B, const int32_t *sel, int n, int S, in
 
 // Plan over all ligands of B (sel == NULL) or over the ligands sel[0..n_sel),
 // whose results fill output rows 0..n_sel-1 in that order.
+// Options of plans made inside the library: start frames borrowed from a
+// plan of the same pocket and sampling, and no device-wide synchronisation
+// at the end (the caller orders the set-up copies before its launch).
+struct PlanOpts {
+  const float *rot = nullptr, *anc = nullptr;
+  bool no_device_sync = false;
+};
+
 static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch *B,
                                       const ligate_sampling *s, const ligate_tile *tile,
-                                      const int32_t *sel, int n_sel, ligate_plan **out) {
+                                      const int32_t *sel, int n_sel, ligate_plan **out,
+                                      const PlanOpts *opt = nullptr) {
   NvtxRange nvtx_("ligate:plan_create");
   if (!out) { set_error("plan_create: out is NULL"); return LIGATE_ERR_INVALID; }
   *out = nullptr;
@@ -914,7 +964,8 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
       return cuda_fail(e0, "plan allocation");
     }
   }
-  st = base_params(P, B, s, mode, pl->p, &pl->rot, &pl->anc, &pl->quat);
+  st = base_params(P, B, s, mode, pl->p, &pl->rot, &pl->anc, &pl->quat, opt ? opt->rot : nullptr,
+                   opt ? opt->anc : nullptr);
   if (st != LIGATE_OK) { free_plan(pl); return st; }
   DockParams &p = pl->p;
   const int sms = device_sms();
@@ -1051,7 +1102,10 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   p.n_items_dev = nullptr;
   pl->rows = n;
   pl->cur_row_lig = pl->row_lig;
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan setup"); }
+  if (!(opt && opt->no_device_sync) && (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "plan setup");
+  }
   *out = pl;
   return LIGATE_OK;
 }
@@ -1341,26 +1395,112 @@ extern "C" ligate_status ligate_plan_work(const ligate_plan *pl, ligate_work *w)
 
 extern "C" void ligate_plan_destroy(ligate_plan *pl) { free_plan(pl); }
 
+// One docking run of a plan, launched directly on `st` (no graph).
+static cudaError_t plan_launch(ligate_plan *pl, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(pl->counters, 0, pl->counter_bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->stats, 0, 3 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && pl->p.n_items > 0)
+    e = launch_dock(pl->mode, pl->tile.reg_cap, pl->p, pl->grid, pl->block, pl->smem, st);
+  pl->rows = pl->n_ligands;
+  pl->cur_row_lig = pl->row_lig;
+  return e;
+}
+
 extern "C" ligate_status ligate_dock_batch(const ligate_pocket *P, const ligate_ligands *L,
                                            const ligate_sampling *s, ligate_pose *out,
                                            void *stream) {
   NvtxRange nvtx_("ligate:dock_batch");
-  if (!out && L && L->n_ligands > 0) { set_error("dock_batch: out is NULL"); return LIGATE_ERR_INVALID; }
-  ligate_batch *B = nullptr;
-  ligate_status st = ligate_batch_create(L, &B);
-  if (st != LIGATE_OK) return st;
-  ligate_plan *pl = nullptr;
-  st = ligate_plan_create(P, B, s, nullptr, &pl);
-  if (st == LIGATE_OK) {
-    st = ligate_plan_run(pl, out, stream);
+  if (!L) { set_error("dock_batch: ligands is NULL"); return LIGATE_ERR_INVALID; }
+  if (!out && L->n_ligands > 0) { set_error("dock_batch: out is NULL"); return LIGATE_ERR_INVALID; }
+  const int n = L->n_ligands;
+  if (n < 2048 || !L->atom_offset || !L->bond_offset) {  // one batch, one plan
+    ligate_batch *B = nullptr;
+    ligate_status st = ligate_batch_create(L, &B);
+    if (st != LIGATE_OK) return st;
+    ligate_plan *pl = nullptr;
+    st = ligate_plan_create(P, B, s, nullptr, &pl);
     if (st == LIGATE_OK) {
-      cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-      if (e != cudaSuccess) st = cuda_fail(e, "dock_batch");
+      st = ligate_plan_run(pl, out, stream);
+      if (st == LIGATE_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "dock_batch");
+      }
+    }
+    ligate_plan_destroy(pl);
+    ligate_batch_destroy(B);
+    return st;
+  }
+  // Two parts: the first eighth is packed, planned and launched, then the
+  // rest is packed, uploaded and planned on the host while the first part
+  // docks (an eighth of the work is several times the rest's host time),
+  // and its kernel fills the SMs as the first one's CTAs finish (two
+  // library streams).  The same poses as one plan over all ligands.
+  const int first = n / 8;
+  const int32_t a0 = L->atom_offset[first], b0 = L->bond_offset[first];
+  std::vector<int32_t> aoB(n - first + 1), boB(n - first + 1);
+  for (int i = 0; i <= n - first; ++i) {
+    aoB[i] = L->atom_offset[first + i] - a0;
+    boB[i] = L->bond_offset[first + i] - b0;
+  }
+  const ligate_ligands part[2] = {
+      {first, L->atom_offset, L->xyz, L->type, L->bond_offset, L->bonds, L->rotatable},
+      {n - first, aoB.data(), L->xyz ? L->xyz + 3 * (size_t)a0 : nullptr, L->type ? L->type + a0 : nullptr,
+       boB.data(), L->bonds ? L->bonds + 2 * (size_t)b0 : nullptr, L->rotatable ? L->rotatable + b0 : nullptr}};
+  ligate_batch *B[2] = {nullptr, nullptr};
+  ligate_plan *pl[2] = {nullptr, nullptr};
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  ligate_status res = LIGATE_OK;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], (cudaStream_t)stream);  // after the caller's prior work
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(st[q], ev[2], 0);
+  if (e != cudaSuccess) res = cuda_fail(e, "dock_batch: streams");
+  for (int q = 0; q < 2 && res == LIGATE_OK; ++q) {
+    res = ligate_batch_create(&part[q], &B[q]);
+    if (res != LIGATE_OK) {
+      if (q == 1) {  // the message counts ligands from the start of the second part
+        const std::string m = g_err;
+        set_error("%s (ligand numbers counted from ligand %d of the input)", m.c_str(), first);
+      }
+      break;
+    }
+    PlanOpts opt;
+    opt.no_device_sync = true;
+    if (q == 1) {
+      opt.rot = pl[0]->p.rot;
+      opt.anc = pl[0]->p.anc;
+    }
+    res = plan_create_impl(P, B[q], s, nullptr, nullptr, 0, &pl[q], &opt);
+    if (res != LIGATE_OK) break;
+    // the set-up copies ran on the legacy default stream: order them first
+    if ((e = cudaEventRecord(ev[q], 0)) != cudaSuccess || (e = cudaStreamWaitEvent(st[q], ev[q], 0)) != cudaSuccess ||
+        (e = plan_launch(pl[q], st[q])) != cudaSuccess) {
+      res = cuda_fail(e, "dock_batch: launch");
+      break;
     }
   }
-  ligate_plan_destroy(pl);
-  ligate_batch_destroy(B);
-  return st;
+  for (int q = 0; q < 2 && res == LIGATE_OK; ++q) {
+    const size_t bytes = sizeof(PoseOut) * (size_t)pl[q]->n_ligands * pl[q]->p.K;
+    if ((e = cudaMemcpyAsync(out + (q ? (size_t)first * s->top_k : 0), pl[q]->out, bytes, cudaMemcpyDefault, st[q])) !=
+        cudaSuccess)
+      res = cuda_fail(e, "dock_batch: result copy");
+  }
+  for (int q = 0; q < 2; ++q)
+    if (st[q]) {
+      e = cudaStreamSynchronize(st[q]);
+      if (e != cudaSuccess && res == LIGATE_OK) res = cuda_fail(e, "dock_batch");
+    }
+  for (int q = 1; q >= 0; --q) {  // plan 1 borrows plan 0's frames
+    ligate_plan_destroy(pl[q]);
+    ligate_batch_destroy(B[q]);
+  }
+  for (int q = 0; q < 3; ++q)
+    if (ev[q]) cudaEventDestroy(ev[q]);
+  for (int q = 0; q < 2; ++q)
+    if (st[q]) cudaStreamDestroy(st[q]);
+  return res;
 }
 
 extern "C" ligate_status ligate_score_poses(const ligate_pocket *P, const ligate_batch *B,

@@ -13,13 +13,32 @@ from __future__ import annotations
 import numpy as np
 
 
-def shard(n_total: int, rank: int, world: int):
-    """Contiguous balanced shard (first index, count) of rank in [0, world)."""
+def shard(n_total: int, rank: int, world: int, weights=None):
+    """Contiguous shard (first index, count) of rank in [0, world).
+
+    Without weights the ligand counts are balanced (they differ by at most
+    one).  With per-ligand weights (e.g. the precomputed pose count of each
+    ligand, workload.poses_per_ligand) the shards balance the work instead:
+    ligand i goes to rank floor(world * (W_i + w_i / 2) / W), W_i the work
+    before it and W the total, so the ranges are contiguous, ordered, and
+    each rank's work is within one ligand's weight of W / world."""
     if world < 1 or not 0 <= rank < world or n_total < 0:
         raise ValueError("bad shard arguments")
-    base, extra = divmod(n_total, world)
-    first = rank * base + min(rank, extra)
-    return first, base + (1 if rank < extra else 0)
+    if weights is None:
+        base, extra = divmod(n_total, world)
+        first = rank * base + min(rank, extra)
+        return first, base + (1 if rank < extra else 0)
+    w = np.asarray(weights, np.float64)
+    if w.shape != (n_total,) or np.any(w < 0):
+        raise ValueError("weights must be n_total non-negative numbers")
+    total = float(w.sum())
+    if total <= 0.0:
+        return shard(n_total, rank, world)
+    mid = np.cumsum(w) - 0.5 * w
+    owner = np.minimum((world * mid / total).astype(np.int64), world - 1)
+    first = int(np.searchsorted(owner, rank, side="left"))
+    last = int(np.searchsorted(owner, rank, side="right"))
+    return first, last - first
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -33,16 +52,28 @@ def max_over_ranks(value: float, device=None) -> float:
     return float(t.item())
 
 
-def gather_scores(local_best: np.ndarray, n_total: int, device=None) -> np.ndarray:
+def sum_over_ranks(value: float, device=None) -> float:
+    """Sum of a per-rank value over all ranks (e.g. the poses each rank scored)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def gather_scores(local_best: np.ndarray, n_total: int, device=None, weights=None) -> np.ndarray:
     """All ranks' per-ligand best scores in global ligand order (every rank
-    receives the full array).  Rank r must hold the shard given by shard()."""
+    receives the full array).  Rank r must hold the shard given by
+    shard(n_total, r, world, weights)."""
     import torch
     import torch.distributed as dist
     local_best = np.asarray(local_best, np.float32)
     if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
         return local_best.copy()
     world = dist.get_world_size()
-    counts = [shard(n_total, r, world)[1] for r in range(world)]
+    counts = [shard(n_total, r, world, weights)[1] for r in range(world)]
     width = max(counts) if counts else 0
     buf = torch.full((width,), float("inf"), dtype=torch.float32, device=device)
     buf[:len(local_best)] = torch.from_numpy(local_best).to(buf.device)

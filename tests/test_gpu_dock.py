@@ -342,3 +342,24 @@ def test_device_subset_run_equals_rows_of_full_run(batched_small):
     np.testing.assert_array_equal(rs[4], ref[6])
     with pytest.raises(N.LigateError):
         D.Plan(ph, bh, w.sampling, mode="bf16", subset=np.array([1, 2], np.int32)).run_subset(np.array([0], np.int32))
+
+
+def test_host_array_call_in_two_halves_equals_plan_path(full):
+    """ligate_dock_batch on 3,000 ligands packs and docks the library in two
+    parts (the second packed while the first docks, on two streams): the
+    same poses as one plan over all of them; a malformed ligand in the
+    second part is reported with its number in the input."""
+    sub = make_workload("batched", n_ligands=3000, pocket=full.pocket)
+    ph = D.PocketHandle(sub.pocket)
+    bh = D.BatchHandle(sub.ligands)
+    want = D.Plan(ph, bh, sub.sampling, mode="bf16").result()
+    s = N.make_sampling(sub.sampling, N.LIGATE_BF16, N.LIGATE_LAYOUT_CORNER, rescore=True)
+    got = np.zeros_like(want)
+    N.ligate_dock_batch(ph.h, sub.ligands, s, got)
+    assert np.array_equal(got, want)
+    bad = sub.ligands.subset(np.arange(3000))
+    j = int(bad.bond_offset[2500])
+    bad.bonds[j] = bad.bonds[j + 1]  # a repeated edge: no longer a tree
+    with pytest.raises(N.LigateError) as err:
+        N.ligate_dock_batch(ph.h, bad, s, np.zeros_like(want))
+    assert "375" in str(err.value)  # the second part starts at ligand 3000 / 8
