@@ -114,6 +114,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default tile instead of the autotuner")
+    ap.add_argument("--no-model", action="store_true", help="skip timing the analytic launch model's tile")
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--no-triage", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
@@ -210,7 +211,7 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
         """2 warm-up steps, then --steps steps timed with CUDA events on the
         stream (everything a step does is enqueued there); the kept indices
         of the last step."""
-        for _ in range(2):
+        for _ in range(max(1, min(2, args.warmup))):
             step()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -237,7 +238,7 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
         return time_steps(step, k, idx_dev)
 
     k, sel, t = timed(args.keep_frac)
-    truth_scores = plain.result(sh)["score"][:, 0]
+    truth_scores = plain.output()["score"][:, 0]  # the plain form's last (timed) run
     N.ligate_surrogate_rank_ensemble(sur, desc, n, args.keep_frac, torch.empty(max(k, 1), dtype=torch.int32,
                                      device="cuda"), pred_all, sh)
     pred = pred_all.cpu().numpy()
@@ -465,7 +466,7 @@ def cpu_baseline(w, n_sample):
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": len(sub) / dt, "unit": "ligands/s", "poses_per_s": poses / dt, "cores": cores,
-            "kind": "oracle", "sample": f"first {len(sub)} ligands of the batched library, full "
+            "kind": "oracle", "sample": f"first {len(sub)} ligands of the {w.name} library, full "
             f"{w.sampling.n_starts} starts each, FP64 C + OpenMP"}, dt
 
 
@@ -624,7 +625,7 @@ def main():
 
     # analytic launch model (no timing) against the autotuned shape
     model = None
-    if not args.no_tune:
+    if not args.no_tune and not args.no_model:
         mt = N.ligate_model_tile(ph.h, bh.h, s_chosen)
         mplan = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True, tile=mt)
         for _ in range(2):

@@ -73,6 +73,17 @@ class Plan:
         self.rows = self.n
         return out
 
+    def output(self) -> np.ndarray:
+        """The last run's poses (rows of the last run), copied from the
+        plan's device buffer without running again."""
+        import torch
+        out = np.zeros((self.rows, self.k), N.POSE_DTYPE)
+        torch.cuda.synchronize()
+        if out.nbytes:
+            view = torch.as_tensor(_DeviceBytes(self.device_output(), out.nbytes), device="cuda")
+            out.reshape(-1).view(np.uint8)[:] = view.cpu().numpy()
+        return out
+
     def run_subset(self, ligands, n_sel=None, stream=None, result=False):
         """Dock a device-chosen selection of this plan's ligands
         (ligate_plan_run_subset): ligands is a CUDA int32 tensor (or a host
@@ -154,3 +165,12 @@ def _device_bytes(a):
     if isinstance(a, np.ndarray):
         return torch.from_numpy(np.ascontiguousarray(a).reshape(-1).view(np.uint8)).cuda()
     return a
+
+
+class _DeviceBytes:
+    """A device byte range (pointer, size) seen through the CUDA array
+    interface, so torch can copy it without owning it."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}

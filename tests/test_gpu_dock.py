@@ -363,3 +363,17 @@ def test_host_array_call_in_two_halves_equals_plan_path(full):
     with pytest.raises(N.LigateError) as err:
         N.ligate_dock_batch(ph.h, bad, s, np.zeros_like(want))
     assert "375" in str(err.value)  # the second part starts at ligand 3000 / 8
+
+
+def test_plan_output_is_the_last_run(batched_small):
+    """Plan.output() copies the last run's rows from the plan's buffer: the
+    full run's, then a subset run's."""
+    w = batched_small
+    ph = D.PocketHandle(w.pocket)
+    bh = D.BatchHandle(w.ligands)
+    pl = D.Plan(ph, bh, w.sampling, mode="bf16")
+    full = pl.result()
+    assert np.array_equal(pl.output(), full)
+    sel = np.array([9, 3, 60], np.int32)
+    pl.run_subset(sel)
+    assert np.array_equal(pl.output(), full[sel])
