@@ -398,6 +398,15 @@ ligate_status ligate_pose_gradient(const ligate_pocket *pocket, const ligate_bat
                                    const ligate_sampling *sampling, int n, const int32_t *lig_idx,
                                    const ligate_pose_state *states, float *energy, float *grad,
                                    void *stream);
+/* Coordinates of n continuous states as the refinement and the exact
+ * rescoring build them (the geometry of a refined pose; paper Sec. 2: the
+ * refined pose is the ligand's output).  DEVICE lig_idx [n] and states [n];
+ * out DEVICE FP32 [n][LIGATE_MAX_ATOMS][3] in Angstrom, atoms in the
+ * ligand's INPUT order; rows past the atom count are not written; an
+ * out-of-range ligand index gives NaN rows.  Synchronises stream. */
+ligate_status ligate_state_coords(const ligate_pocket *pocket, const ligate_batch *batch,
+                                  const ligate_sampling *sampling, int n, const int32_t *lig_idx,
+                                  const ligate_pose_state *states, float *out, void *stream);
 /* Refine n explicit states (DEVICE arrays; out DEVICE [n]) for
  * `iterations` (0..LIGATE_REFINE_MAX_ITERS) descent iterations with
  * initial step eta0 > 0 (A^2 per score unit).  Synchronises stream. */

@@ -1555,6 +1555,31 @@ extern "C" ligate_status ligate_pose_coords(const ligate_pocket *P, const ligate
   return LIGATE_OK;
 }
 
+extern "C" ligate_status ligate_state_coords(const ligate_pocket *P, const ligate_batch *B,
+                                             const ligate_sampling *s, int n, const int32_t *lig_idx,
+                                             const ligate_pose_state *states, float *out, void *stream) {
+  int mode = 0;
+  ligate_status st = check_sampling(P, B, s, &mode);
+  if (st != LIGATE_OK) return st;
+  if (n < 0 || (n > 0 && (!lig_idx || !states || !out))) {
+    set_error("state_coords: bad state arrays");
+    return LIGATE_ERR_INVALID;
+  }
+  if (n == 0) return LIGATE_OK;
+  DockParams p;
+  float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  st = base_params(P, B, s, mode, p, &rot, &anc, &quat);
+  cudaError_t e = cudaSuccess;
+  if (st == LIGATE_OK) {
+    e = launch_state_coords(p, B->d.order, n, lig_idx, states, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  }
+  cudaFree(rot); cudaFree(anc); cudaFree(quat);
+  if (st != LIGATE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "state_coords");
+  return LIGATE_OK;
+}
+
 __global__ void best_scores_kernel(const PoseOut *__restrict__ poses, int n, int K, float *__restrict__ out,
                                    int stride, int column) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;

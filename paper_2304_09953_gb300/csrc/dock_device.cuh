@@ -396,6 +396,48 @@ __device__ void build_pose(const DockParams &p, const WarpSmem &w, float4 *buf, 
   }
 }
 
+// Angstrom coordinates of continuous state (R, t, phi) of the loaded ligand
+// into buf: starting from its centred input coordinates `ref` (.w kept),
+// each rotatable bond in sweep order turns its subtree by phi_b (radians,
+// skipped when exactly 0) about its current axis u -> v, then x = R y + t.
+// The refinement, the exact rescoring of states and ligate_state_coords all
+// build states with this function, so they see the same FP32 geometry.
+// Warp-cooperative.
+__device__ inline void build_state(const float4 *ref, float4 *buf, const BondRec *bonds, const LigDesc &d,
+                                   const float *R, const float *T, const float *phi, int lane) {
+  for (int i = lane; i < d.n_atoms; i += 32) buf[i] = ref[i];
+  __syncwarp();
+  for (int b = 0; b < d.n_rot; ++b) {
+    const float ang = phi[b];
+    if (ang == 0.f) continue;
+    const BondRec br = bonds[b];
+    float nx, ny, nz;
+    const float4 pv = buf[br.v];
+    bond_axis(buf[br.u], pv, nx, ny, nz);
+    float sn, cs;
+    sincosf(ang, &sn, &cs);
+    Rot rot;
+    rot.make(cs, sn, nx, ny, nz, pv.x, pv.y, pv.z);
+    __syncwarp();
+    for (int i = br.v + 1 + lane; i < br.end; i += 32) {
+      float4 q = buf[i];
+      rot.apply(q.x, q.y, q.z, q.x, q.y, q.z);
+      buf[i] = q;
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 y = buf[i];
+    float4 x;
+    x.x = fmaf(R[0], y.x, fmaf(R[1], y.y, fmaf(R[2], y.z, T[0])));
+    x.y = fmaf(R[3], y.x, fmaf(R[4], y.y, fmaf(R[5], y.z, T[1])));
+    x.z = fmaf(R[6], y.x, fmaf(R[7], y.y, fmaf(R[8], y.z, T[2])));
+    x.w = y.w;
+    buf[i] = x;
+  }
+  __syncwarp();
+}
+
 // Full FP32 score of pose (sid, tors) of the loaded ligand, warp-cooperative,
 // using the map `maps` read in mode MODE (scratch: pose slot `buf`).
 template <int MODE>

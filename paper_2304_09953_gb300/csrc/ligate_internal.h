@@ -222,6 +222,11 @@ cudaError_t launch_pose_features(const DockParams &p, int n_poses, const int32_t
                                  const int32_t *start_id, const uint8_t *tors, const ligate_pose *poses,
                                  const int32_t *row_lig, float *out, cudaStream_t s);
 
+// Angstrom coordinates of continuous states, [n][LIGATE_MAX_ATOMS][3],
+// atoms in input order (rescore.cu).
+cudaError_t launch_state_coords(const DockParams &p, const uint8_t *order, int n, const int32_t *lig_idx,
+                                const ligate_pose_state *states, float *out, cudaStream_t s);
+
 // Per-ligand selection after rescoring (rescore.cu).
 cudaError_t launch_best_passing(const ligate_rescored *rec, int n, int K, int32_t *idx, float *energy,
                                 cudaStream_t s);

@@ -24,7 +24,7 @@
 #include <math.h>
 #include <string.h>
 
-#include "ligate_internal.h"
+#include "dock_device.cuh"
 
 namespace ligate {
 namespace {
@@ -73,18 +73,6 @@ __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLM, v, o);
   return v;
-}
-
-// Rotation by angle (c, s) about unit axis n through point p, applied to v.
-__device__ __forceinline__ void rotate_about(float c, float s, float nx, float ny, float nz, float px,
-                                             float py, float pz, float4 &v) {
-  const float ax = v.x - px, ay = v.y - py, az = v.z - pz;
-  const float kd = nx * ax + ny * ay + nz * az;
-  const float kx = ny * az - nz * ay, ky = nz * ax - nx * az, kz = nx * ay - ny * ax;
-  const float o = (1.f - c) * kd;
-  v.x = px + ax * c + kx * s + nx * o;
-  v.y = py + ay * c + ky * s + ny * o;
-  v.z = pz + az * c + kz * s + nz * o;
 }
 
 __device__ __forceinline__ void unit_axis(const float4 &a, const float4 &b, float &nx, float &ny,
@@ -139,35 +127,7 @@ struct RefineArgs {
 __device__ float eval_state(const RefineArgs &a, const RSmem &w, const LigDesc &d, int s, int lane) {
   const DockParams &p = a.p;
   const State &q = w.q[s];
-  for (int i = lane; i < d.n_atoms; i += 32) w.x[i] = w.ref[i];
-  __syncwarp();
-  for (int b = 0; b < d.n_rot; ++b) {
-    const float phi = q.phi[b];
-    if (phi == 0.f) continue;
-    const BondRec br = w.bonds[b];
-    const float4 pu = w.x[br.u], pv = w.x[br.v];
-    float nx, ny, nz;
-    unit_axis(pu, pv, nx, ny, nz);
-    float sn, cs;
-    sincosf(phi, &sn, &cs);
-    __syncwarp();
-    for (int i = br.v + 1 + lane; i < br.end; i += 32) {
-      float4 v = w.x[i];
-      rotate_about(cs, sn, nx, ny, nz, pv.x, pv.y, pv.z, v);
-      w.x[i] = v;
-    }
-    __syncwarp();
-  }
-  for (int i = lane; i < d.n_atoms; i += 32) {
-    const float4 y = w.x[i];
-    float4 x;
-    x.x = fmaf(q.R[0], y.x, fmaf(q.R[1], y.y, fmaf(q.R[2], y.z, q.t[0])));
-    x.y = fmaf(q.R[3], y.x, fmaf(q.R[4], y.y, fmaf(q.R[5], y.z, q.t[1])));
-    x.z = fmaf(q.R[6], y.x, fmaf(q.R[7], y.y, fmaf(q.R[8], y.z, q.t[2])));
-    x.w = y.w;
-    w.x[i] = x;
-  }
-  __syncwarp();
+  build_state(w.ref, w.x, w.bonds, d, q.R, q.t, q.phi, lane);
   const int ts = p.g.nx * p.g.ny * p.g.nz;
   const float fcl = -4.f * p.clash_w * p.inv_dc2_ang;
   float e = 0.f, cl = 0.f, F0 = 0.f, F1 = 0.f, F2 = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f, IR = 0.f;

@@ -85,35 +85,12 @@ __global__ void __launch_bounds__(256) rescore_kernel(const DockParams p, const 
       // state (R, t, phi): torsions on the centred input coordinates about
       // the current axes, then x = R y + t (A) and u = (x - origin) / h
       const float *R = reinterpret_cast<const float *>(st_rec);
-      const float *T = R + 9, *phi = R + 12;
-      for (int i = lane; i < d.n_atoms; i += 32) w.pose[i] = w.ref[i];
-      __syncwarp();
-      for (int b = 0; b < d.n_rot; ++b) {
-        const float ang = phi[b];
-        if (ang == 0.f) continue;
-        const BondRec br = w.bonds[b];
-        float nx, ny, nz;
-        const float4 pv = w.pose[br.v];
-        bond_axis(w.pose[br.u], pv, nx, ny, nz);
-        float sn, cs;
-        sincosf(ang, &sn, &cs);
-        Rot rot;
-        rot.make(cs, sn, nx, ny, nz, pv.x, pv.y, pv.z);
-        __syncwarp();
-        for (int i = br.v + 1 + lane; i < br.end; i += 32) {
-          float4 q = w.pose[i];
-          rot.apply(q.x, q.y, q.z, q.x, q.y, q.z);
-          w.pose[i] = q;
-        }
-        __syncwarp();
-      }
+      build_state(w.ref, w.pose, w.bonds, d, R, R + 9, R + 12, lane);
       for (int i = lane; i < d.n_atoms; i += 32) {
-        const float4 y = w.pose[i];
-        float4 u;
-        u.x = (fmaf(R[0], y.x, fmaf(R[1], y.y, fmaf(R[2], y.z, T[0]))) - r.ox) * r.inv_h;
-        u.y = (fmaf(R[3], y.x, fmaf(R[4], y.y, fmaf(R[5], y.z, T[1]))) - r.oy) * r.inv_h;
-        u.z = (fmaf(R[6], y.x, fmaf(R[7], y.y, fmaf(R[8], y.z, T[2]))) - r.oz) * r.inv_h;
-        u.w = y.w;
+        float4 u = w.pose[i];
+        u.x = (u.x - r.ox) * r.inv_h;
+        u.y = (u.y - r.oy) * r.inv_h;
+        u.z = (u.z - r.oz) * r.inv_h;
         w.pose[i] = u;
       }
       __syncwarp();
@@ -357,6 +334,48 @@ cudaError_t launch_rescore(const DockParams &p, const RecParams &r, int n_poses,
   if (states) ss = *states;
   rescore_kernel<<<grid, 32 * warps, smem, s>>>(p, r, n_poses, lig_idx, start_id, tors,
                                                 reinterpret_cast<const PoseOut *>(poses), row_lig, ss, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Coordinates of continuous states as the refinement and the exact
+// rescoring build them (build_state): one warp per state, Angstrom, atoms
+// written back in the ligand's input order.
+__global__ void __launch_bounds__(256) state_coords_kernel(const DockParams p, const uint8_t *__restrict__ order,
+                                                           int n, const int32_t *__restrict__ lig_idx,
+                                                           const ligate_pose_state *__restrict__ states,
+                                                           float *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const WarpSmem w = warp_smem(smem_raw + (size_t)warp * smem_bytes_per_warp(p.nmax, 0, 1, 0), p.nmax, 1);
+  const int pi = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (pi >= n) return;
+  float *o = out + (size_t)pi * LIGATE_MAX_ATOMS * 3;
+  const int li = lig_idx[pi];
+  if (li < 0 || li >= p.n_ligands) {  // caller's device data
+    for (int q = lane; q < LIGATE_MAX_ATOMS * 3; q += 32) o[q] = __int_as_float(0x7fc00000);
+    return;
+  }
+  LigDesc d;
+  (void)load_ligand(p, w, li, d, lane);
+  const ligate_pose_state &st = states[pi];
+  build_state(w.ref, w.pose, w.bonds, d, st.rot, st.trans, st.tors, lane);
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    const float4 x = w.pose[i];
+    float *a = o + 3 * (int)order[d.atom_base + i];
+    a[0] = x.x; a[1] = x.y; a[2] = x.z;
+  }
+}
+
+cudaError_t launch_state_coords(const DockParams &p, const uint8_t *order, int n, const int32_t *lig_idx,
+                                const ligate_pose_state *states, float *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int warps = 4;
+  const size_t smem = (size_t)warps * smem_bytes_per_warp(p.nmax, 0, 1, 0);
+  cudaError_t e = cudaFuncSetAttribute(state_coords_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e != cudaSuccess) return e;
+  state_coords_kernel<<<(n + warps - 1) / warps, 32 * warps, smem, s>>>(p, order, n, lig_idx, states, out);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ _SIGS = {
     "ligate_dock_noalloc": (ctypes.c_int, [P, P, P, P, P]),
     "ligate_score_poses": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
     "ligate_pose_coords": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P, P]),
+    "ligate_state_coords": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, P]),
     "ligate_autotune": (ctypes.c_int, [P, P, P, ctypes.c_double, P]),
     "ligate_model_tile": (ctypes.c_int, [P, P, P, P]),
     "ligate_descriptors": (ctypes.c_int, [P, P, P]),
@@ -336,6 +337,12 @@ def ligate_pose_coords(pocket, batch, sampling_struct, n, lig_idx, start_id, tor
     """out: DEVICE float32 [n][LIGATE_MAX_ATOMS][3], grid units, input atom order."""
     check(load().ligate_pose_coords(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
                                     _ptr(start_id), _ptr(tors), _ptr(out), stream), "ligate_pose_coords")
+
+
+def ligate_state_coords(pocket, batch, sampling_struct, n, lig_idx, states, out, stream=None):
+    """states: DEVICE ligate_pose_state[n]; out: DEVICE float32 [n][LIGATE_MAX_ATOMS][3], Angstrom."""
+    check(load().ligate_state_coords(pocket, batch, ctypes.byref(sampling_struct), int(n), _ptr(lig_idx),
+                                     _ptr(states), _ptr(out), stream), "ligate_state_coords")
 
 
 def ligate_pose_gradient(pocket, batch, sampling_struct, n, lig_idx, states, energy, grad, stream=None):

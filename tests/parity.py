@@ -126,6 +126,23 @@ class Geometry:
         bh.close()
         return out.cpu().numpy().reshape(n, 128, 3)[:, :len(lig[0])].astype(np.float64)
 
+    def state_coords(self, lig, sampling, rec):
+        """GPU coordinates [n, n_atoms, 3] in Angstrom (FP32 values) of
+        continuous states (STATE_DTYPE records), as the refinement and the
+        exact rescoring build them."""
+        import torch
+        from paper_2304_09953_gb300 import docking as D
+        from paper_2304_09953_gb300 import native as N
+        rec = np.ascontiguousarray(rec)
+        n = len(rec)
+        bh = D.BatchHandle(_one_ligand(lig))
+        s = N.make_sampling(sampling)
+        out = torch.zeros(n * 128 * 3, dtype=torch.float32, device="cuda")
+        st = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+        N.ligate_state_coords(self.ph.h, bh.h, s, n, torch.zeros(n, dtype=torch.int32, device="cuda"), st, out)
+        bh.close()
+        return out.cpu().numpy().reshape(n, 128, 3)[:, :len(lig[0])].astype(np.float64)
+
     def exact_coords(self, lig, sampling, starts, tors):
         """FP64 coordinates of the same poses, grid units."""
         x = oracle.pose_coords(lig, self.pocket.anchors, sampling, starts, np.asarray(tors, np.int32))
@@ -353,3 +370,38 @@ def features_check(geo, lig, pocket, sampling, starts, tors, feats, stats=None):
     np.testing.assert_allclose(feats[:, 74:77], og[:, 74:77], rtol=1e-6)
     assert np.all(feats[:, 77:] == 0)
     return int((~same).sum())
+
+
+def check_state_energies(geo, lig, pocket, sampling, rec, st64, energies, e64, stats=None, value=None):
+    """Energies of continuous states (docking score, or a rescoring term when
+    `value` maps Angstrom coordinate sets to FP64 values): the strict bar
+    against the FP64 value of the exact state, else the rounding proof with
+    the GPU's own state coordinates (ligate_state_coords)."""
+    R = int(np.sum(np.asarray(lig[3]) != 0))
+    energies = np.asarray(energies, np.float64)
+    e64 = np.asarray(e64, np.float64)
+    ratio = np.abs(energies - e64) / tol(e64)
+    bad = ratio > 1.0
+    if stats is not None:
+        stats.poses += len(ratio)
+        stats.strict += int((~bad).sum())
+        stats.rounding += int(bad.sum())
+        stats.max_strict_ratio = max(stats.max_strict_ratio, float(ratio.max(initial=0.0)))
+    if not bad.any():
+        return
+    idx = np.nonzero(bad)[0]
+    xg = geo.state_coords(lig, sampling, np.asarray(rec)[idx])
+    x64 = oracle.state_coords(lig, np.array([st64[k] for k in idx]))
+    if value is None:
+        e_at = np.array([oracle.score_coords(lig, pocket, sampling, x) for x in xg])
+    else:
+        e_at = value(xg)
+    for m, j in enumerate(idx):
+        ar = abs(energies[j] - e_at[m]) / tol(e_at[m])
+        u64 = (x64[m] - geo.org) / geo.h
+        cr = float(np.max(np.abs(xg[m] - x64[m]))) / geo.h / coord_envelope(u64, R)
+        if stats is not None:
+            stats.max_arith_ratio = max(stats.max_arith_ratio, float(ar))
+            stats.max_coord_ratio = max(stats.max_coord_ratio, cr)
+        assert ar <= 1.0, (j, energies[j], e_at[m], e64[j])
+        assert cr <= 1.0, (j, cr)

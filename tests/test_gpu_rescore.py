@@ -1,8 +1,9 @@
 """Exact rescoring and the pose filter on the GPU vs the FP64 oracle.
 
-Explicit poses (seeded starts and torsion steps): receptor and clash terms
-by the docking score's parity rules (strict 1e-4 relative, else exact at the
-GPU's own coordinates with the coordinates inside the FP32 envelope); the
+Explicit poses (seeded starts and torsion steps) and continuous states:
+receptor and clash terms by the docking score's parity rules (strict 1e-4
+relative, else exact at the GPU's own coordinates -- ligate_pose_coords,
+ligate_state_coords -- with the coordinates inside the FP32 envelope); the
 filter counts equal the oracle's at the GPU's coordinates except for an atom
 on its threshold (a receptor sum within the bar of the cap, a coordinate on
 a box face).  The plan path gives the same values as the explicit path for
@@ -14,7 +15,8 @@ import pytest
 import oracle
 from paper_2304_09953_gb300 import docking as D
 from paper_2304_09953_gb300 import native as N
-from tests.parity import (REL, U32, Geometry, Stats, coord_envelope, features_check, rescore_check)
+from tests.parity import (REL, U32, Geometry, Stats, check_state_energies, coord_envelope, features_check,
+                          rescore_check)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -206,16 +208,18 @@ def test_rescore_states_matches_oracle_and_refined_plan_path(batched_small):
     same = 0
     org, h = np.asarray(w.pocket.origin), w.pocket.spacing
     rcp = w.pocket.receptor()
+    geo, stt = Geometry(w.pocket), Stats()
     for li in np.unique(lig):
         sel = np.nonzero(lig == li)[0]
         L = w.ligands.ligand(li)
         R_n = int(np.sum(L[3] != 0))
         x = oracle.state_coords(L, np.array([st64[k] for k in sel]))
         o = oracle.rescore_coords(L, w.pocket, w.sampling, rcp, x)
+        for key in ("e_inter", "e_clash"):
+            check_state_energies(geo, L, w.pocket, w.sampling, rec[sel], [st64[k] for k in sel], r[sel][key],
+                                 o[key], stt,
+                                 value=lambda x, key=key: oracle.rescore_coords(L, w.pocket, w.sampling, rcp, x)[key])
         for m, k in enumerate(sel):
-            tol = 1e-4 * max(o["scale"][m], 1.0)
-            assert abs(r[k]["e_inter"] - o["e_inter"][m]) <= tol
-            assert abs(r[k]["e_clash"] - o["e_clash"][m]) <= tol
             ok = r[k]["n_outside"] == o["n_outside"][m] and r[k]["n_capped"] == o["n_capped"][m]
             same += ok
             if not ok:
@@ -241,7 +245,7 @@ def test_rescore_states_matches_oracle_and_refined_plan_path(batched_small):
                 dcap = abs(int(r[k]["n_capped"]) - int(o["n_capped"][m]))
                 dout = abs(int(r[k]["n_outside"]) - int(o["n_outside"][m]))
                 assert dcap <= int(cross.sum()) and dout <= int(near.sum()), (k, dcap, dout)
-    print(f"states with filter counts equal to the oracle's: {same} of {n}")
+    print(f"{stt.line()}; states with filter counts equal to the oracle's: {same} of {n}")
     # refined plan records vs their states through the explicit path
     pl = D.Plan(ph, bh, w.sampling, mode="bf16")
     pl.run()
