@@ -78,7 +78,7 @@ def algorithmic_flops(work, S, n_starts, total_atoms):
 # valid only for the kernel revision it was captured on (sha1 prefix of
 # dock.cu + dock_device.cuh); any other revision reports null until it is
 # captured again.
-TRAFFIC_BYTES = {("7ed334d424a8", "batched", 10000): 103064832 + 68303104}
+TRAFFIC_BYTES = {("6a4ce4926843", "batched", 10000): 95450112 + 34710784}
 
 
 def kernel_source_sha():

@@ -245,6 +245,21 @@ __device__ void build_memo(const DockParams &p, const WarpSmem &w, float4 *pose,
   }
 }
 
+// Drops the L2 copies of the whole 128-byte lines inside [lo, hi) without
+// writing them back to DRAM: for scratch whose contents are dead (a
+// ligand's merged partial lists, a warp's clash tables at exit).  Lines that
+// reach outside the range may hold another owner's live data and are left
+// alone.  Warp-collective over `lane`; the caller has finished its reads.
+// A discard acts as a write of undefined data, so the fence and the warp
+// barrier order it before any lane's next write to the same lines.
+__device__ __forceinline__ void l2_discard(const void *lo, const void *hi, int lane) {
+  const uintptr_t a = ((uintptr_t)lo + 127u) & ~(uintptr_t)127u, b = (uintptr_t)hi & ~(uintptr_t)127u;
+  for (uintptr_t q = a + (uintptr_t)lane * 128u; q < b; q += 32u * 128u)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(q) : "memory");
+  __threadfence();
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // CTAs of at most 128 threads; MINB of them must fit on one SM: 4 caps the
 // registers at 128 (16 resident warps), 5 at 102 (20 warps), 6 at 85 (24
@@ -278,10 +293,17 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
     int it = 0;
     if (lane == 0) it = atomicAdd(p.queue, 1);
     it = __shfl_sync(FULL, it, 0);
-    if (it >= n_items) break;
+    if (it >= n_items) {
+      if (m1) {  // this warp's clash tables are dead: no write-back
+        __syncwarp();
+        l2_discard(m1, m1 + (size_t)p.m1max * S * S, lane);
+      }
+      break;
+    }
     const Item item = p.items[it];
     if (item.ligand != cur) {
       __syncwarp();
+      if (m1 && cur >= 0) l2_discard(m1, m1 + (size_t)p.m1max * S * S, lane);  // the last ligand's tables
       clash_ref = load_ligand(p, w, item.ligand, d, lane);
       cur = item.ligand;
       n_memo = min(d.n_rot, memo_bonds(S));
@@ -468,6 +490,8 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         if (cs != EMPTY_SID) top.insert(ce, cs, c0, c1, c2, c3, K, lane);
       }
     }
+    __syncwarp();  // the ligand's partial lists are merged and dead: no write-back
+    l2_discard(p.partial + (size_t)slot0 * K, p.partial + (size_t)(slot0 + nit) * K, lane);
     int rank = lane;
     if (p.rescore) {
       for (int j = 0; j < K; ++j) {
