@@ -68,6 +68,24 @@ def test_first_64_ligands(batched_small):
     print(st.line())
 
 
+def test_clash_tables_with_unaligned_scratch(batched_small):
+    """S = 12: a clash table is 12 x 12 floats (576 bytes), so the per-warp
+    table regions do not start on 128-byte lines; 64 ligands x 256 starts
+    keep many warps busy side by side, each dropping its own dead tables from
+    L2 when it takes the next ligand.  Every ligand that has single-separator
+    tables must still match the oracle."""
+    w = batched_small
+    samp = Sampling(w.sampling.quats[:32], 8, 12, 8)
+    with_tables = [i for i in range(w.ligands.n)
+                   if np.any(N.ligate_inspect_ligand(w.ligands, i)[1][2:, 6] > 0)]
+    assert len(with_tables) >= 20
+    res = D.dock(w.pocket, w.ligands, samp, mode="fp32")
+    st = Stats()
+    for i in with_tables[::2]:
+        compare_ligand(w.ligands.ligand(i), w.pocket, samp, res[i], K=8, stats=st)
+    print(st.line())
+
+
 def _dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
 
