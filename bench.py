@@ -39,7 +39,10 @@ WORKLOAD = ("batched: 10000 ligands (N~U{15..60}, R~U{0..12}), 8x64^3 maps @0.37
 WORKLOADS = {"batched": WORKLOAD,
              "combined": ("combined: 1000000 ligands (N log-uniform {10..80}, R~U{0..15}), "
                           "8x96^3 maps @0.375 A, 256 orient x 32 anchors x S=16, top-16")}
-# Roofline of the docking kernel, two FLOP counts (FMA = 2):
+# Roofline of the docking kernel, two FLOP counts (FMA = 2), both over the
+# poses the kernel evaluated (a start whose energy bound already exceeds the
+# K-th best stops its sweep; its remaining poses are decided, not computed,
+# and count in poses/s but not in FLOP/s):
 #  * algorithmic (the method's own count, per unique pose): every atom
 #    evaluation of a unique pose (N per start, moved atoms x (S - 1) per bond)
 #    costs 50 FLOP (rotation 9 FMA, rigid move 9 FMA, grid coordinate 3 FMA,
@@ -65,11 +68,13 @@ def executed_flops(work, S):
 
 
 def algorithmic_flops(work, S, n_starts, total_atoms):
-    """Unique-pose count: the plan's atom and pair counts include the k = 0
-    trial of every bond, which repeats the current pose."""
+    """Unique-pose count of the poses the run evaluated (device counters):
+    the atom and pair counts include the k = 0 trial of every bond, which
+    repeats the current pose.  Sweeps stopped by the lower bound are not
+    counted: their poses were decided without being computed."""
     rigid = float(n_starts) * float(total_atoms)
-    atoms = rigid + (work.atom_evals - rigid) * (S - 1) / S
-    pairs = work.pair_evals * (S - 1) / S
+    atoms = rigid + (work.done_atom_evals - rigid) * (S - 1) / S
+    pairs = work.done_pair_evals * (S - 1) / S
     return FLOP_ALG_ATOM * atoms + FLOP_ALG_PAIR * pairs, atoms, pairs
 
 
@@ -78,7 +83,7 @@ def algorithmic_flops(work, S, n_starts, total_atoms):
 # valid only for the kernel revision it was captured on (sha1 prefix of
 # dock.cu + dock_device.cuh); any other revision reports null until it is
 # captured again.
-TRAFFIC_BYTES = {("6a4ce4926843", "batched", 10000): 95450112 + 34710784}
+TRAFFIC_BYTES = {("364cd6c24966", "batched", 10000): 98448896 + 42856704}
 
 
 def kernel_source_sha():
@@ -747,6 +752,9 @@ def main():
                             "starts_per_item": list(t_.starts_per_item), "reg_cap": t_.reg_cap},
                    "autotune_s": round(tune_s, 2), "parallelism": f"replicas x{ws}"},
         "poses_per_s": poses_s,
+        "poses_note": "unique poses of the search space decided per second (O x A x (1 + R (S - 1)) per "
+                      "ligand): evaluated, or excluded by the sweep's lower bound on a start's final "
+                      "energy; roofline FLOP counts cover the evaluated ones only",
         "plain": {"value": n_job / (plain_ms / 1000), "unit": "ligands/s",
                   "poses_per_s": ws * work_plain.poses / (plain_ms / 1000), "ms_per_step": plain_ms,
                   "form": "fp32 plain maps, default tile, no rescore",
@@ -772,6 +780,9 @@ def main():
                                 "peak_note": "measured: ligate_probe_gather, random 16 B corner-cell "
                                              "gathers over the whole BF16 map, all SMs (L2-served)"},
                      "work_per_launch": {"atom_evals_unique": alg_atoms, "pair_trials_unique": alg_pairs,
+                                         "starts": work.starts, "starts_bounded_out": work.done_pruned_starts,
+                                         "atom_evals_search_space": work.atom_evals,
+                                         "pair_trials_search_space": work.pair_evals,
                                          "algorithmic_flop": alg, "executed_flop": flops,
                                          "atom_evals": work.done_atom_evals,
                                          "pair_tests": work.done_pair_tests,

@@ -287,6 +287,12 @@ typedef struct {
   double done_atom_evals;
   double done_pair_tests;
   double done_pair_survivors;
+  /* Candidate clash pairs x S of the bond sweeps the run evaluated (the
+   * counterpart of pair_evals after the bound), and the starts whose sweep
+   * stopped because a lower bound of their final energy exceeded the K-th
+   * best energy already found (they cannot enter the top-K). */
+  double done_pair_evals;
+  double done_pruned_starts;
 } ligate_work;
 ligate_status ligate_plan_work(const ligate_plan *plan, ligate_work *out);
 void ligate_plan_destroy(ligate_plan *plan);

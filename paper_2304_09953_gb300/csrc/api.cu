@@ -4,6 +4,8 @@
 // autotuner.  Paper Sec. 2 (docking of every library ligand into a prepared
 // pocket) and Sec. 3.3 (batches of ligand-pocket pairs, ligands grouped by
 // atom and rotatable-bond count, batch shape tuned per size).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -61,6 +63,21 @@ static int pow2ceil(int v) {
 
 using namespace ligate;
 
+// Least value an atom of each type can score in a sweep over the map of
+// layout `mode`: the least FP32 map value rounded as the packed map stores
+// it (round to nearest is monotonic, so this is the least stored value; a
+// trilinear interpolation of stored values lies above it up to FP32
+// rounding), or the out-of-box penalty if that is lower.
+void ligate::set_map_minima(DockParams &p, const PocketDev &d, int mode) {
+  for (int t = 0; t < LIGATE_MAX_TYPES; ++t) {
+    float v = t < d.n_types ? d.h_min[t] : 0.f;
+    if (mode == MODE_BF16_CORNER) v = __bfloat162float(__float2bfloat16_rn(v));
+    else if (mode == MODE_F16_CORNER) v = __half2float(__float2half_rn(v));
+    p.gmin[t] = std::min(v, p.g.penalty);
+  }
+}
+
+
 // ===========================================================================
 
 extern "C" const char *ligate_last_error(void) { return g_err; }
@@ -105,6 +122,12 @@ extern "C" ligate_status ligate_pocket_create(const float *maps, int n_types, in
   d.spacing = spacing;
   d.n_anchors = n_anchors;
   d.h_anchors.assign(anchors, anchors + 3 * n_anchors);
+  for (int t = 0; t < n_types; ++t) {  // each map's least value: the sweep's lower bounds
+    const float *m = maps + (size_t)t * nodes;
+    float lo = m[0];
+    for (size_t i = 1; i < nodes; ++i) lo = std::min(lo, m[i]);
+    d.h_min[t] = lo;
+  }
   auto fail = [&](cudaError_t e, const char *w) {
     ligate_status st = cuda_fail(e, w);
     ligate_pocket_destroy(p);
@@ -781,6 +804,7 @@ ligate_status base_params(const ligate_pocket *P, const ligate_batch *B, const l
   p.g.fx1 = (float)(d.nx - 1); p.g.fy1 = (float)(d.ny - 1); p.g.fz1 = (float)(d.nz - 1);
   p.g.penalty = s->penalty;
   p.g.cx = 8388608.f + (float)(d.nx - 2); p.g.cy = 8388608.f + (float)(d.ny - 2); p.g.cz = 8388608.f + (float)(d.nz - 2);
+  set_map_minima(p, d, mode);
   p.n_anchor = s->n_anchor;
   p.n_starts = s->n_orient * s->n_anchor;
   p.S = s->torsion_steps;
@@ -843,7 +867,7 @@ struct ligate_plan {
   const ligate_batch *batch = nullptr;
   double origin[3] = {0, 0, 0}, h = 1.0;
   size_t counter_bytes = 0;
-  unsigned long long *stats = nullptr;  // [3] executed-work counters of the last run
+  unsigned long long *stats = nullptr;  // [N_STATS] executed-work counters of the last run
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1059,14 +1083,14 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
   const size_t ni = items.size();
   cudaError_t e;
-  pl->counter_bytes = sizeof(int) * (size_t)(n + 1);
-  if ((e = dmalloc(&pl->stats, 3)) != cudaSuccess) {
+  pl->counter_bytes = sizeof(int) * (2 * (size_t)n + 1);  // queue, done[n], lig_thr[n]
+  if ((e = dmalloc(&pl->stats, N_STATS)) != cudaSuccess) {
     free_plan(pl);
     return cuda_fail(e, "plan allocation");
   }
   if ((e = dmalloc(&pl->items, ni)) != cudaSuccess || (e = dmalloc(&pl->lig_items, n)) != cudaSuccess ||
       (e = dmalloc(&pl->lig_slot0, n)) != cudaSuccess ||
-      (e = dmalloc(&pl->counters, (size_t)n + 1)) != cudaSuccess ||
+      (e = dmalloc(&pl->counters, 2 * (size_t)n + 1)) != cudaSuccess ||
       (e = dmalloc(&pl->partial, ni * p.K)) != cudaSuccess ||
       (e = dmalloc(&pl->out, (size_t)n * p.K)) != cudaSuccess) {
     free_plan(pl);
@@ -1096,6 +1120,7 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   p.lig_slot0 = pl->lig_slot0;
   p.queue = pl->counters;
   p.done = pl->counters + 1;
+  p.lig_thr = reinterpret_cast<unsigned *>(pl->counters + 1 + n);
   p.stats = pl->stats;
   p.partial = pl->partial;
   p.out = pl->out;
@@ -1131,7 +1156,7 @@ static ligate_status plan_capture(ligate_plan *pl) {
   CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking), "capture stream");
   CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t e = cudaMemsetAsync(pl->counters, 0, pl->counter_bytes, pl->cap_stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(pl->stats, 0, 3 * sizeof(unsigned long long), pl->cap_stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->stats, 0, N_STATS * sizeof(unsigned long long), pl->cap_stream);
   if (e == cudaSuccess && pl->p.n_items > 0)
     e = launch_dock(pl->mode, pl->tile.reg_cap, pl->p, pl->grid, pl->block, pl->smem, pl->cap_stream);
   cudaGraph_t g = nullptr;
@@ -1346,7 +1371,8 @@ extern "C" ligate_status ligate_plan_run_subset(ligate_plan *pl, const int32_t *
                                               p.K);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "plan_run_subset: selection");
     if ((e = cudaMemsetAsync(pl->counters, 0, sizeof(int) * ((size_t)n_sel + 1), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(pl->stats, 0, 3 * sizeof(unsigned long long), s)) != cudaSuccess)
+        (e = cudaMemsetAsync(pl->counters + 1 + n, 0, sizeof(int) * (size_t)n_sel, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(pl->stats, 0, N_STATS * sizeof(unsigned long long), s)) != cudaSuccess)
       return cuda_fail(e, "plan_run_subset");
     DockParams q = p;
     q.items = pl->sub_items;
@@ -1382,7 +1408,7 @@ extern "C" ligate_status ligate_plan_get_tile(const ligate_plan *pl, ligate_tile
 extern "C" ligate_status ligate_plan_work(const ligate_plan *pl, ligate_work *w) {
   if (!pl || !w) { set_error("plan_work: NULL argument"); return LIGATE_ERR_INVALID; }
   *w = pl->work;
-  unsigned long long c[3] = {0, 0, 0};
+  unsigned long long c[N_STATS] = {};
   if (pl->exec) {
     cudaError_t e = cudaMemcpy(c, pl->stats, sizeof(c), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "plan_work");
@@ -1390,6 +1416,8 @@ extern "C" ligate_status ligate_plan_work(const ligate_plan *pl, ligate_work *w)
   w->done_atom_evals = (double)c[0];
   w->done_pair_tests = (double)c[1];
   w->done_pair_survivors = (double)c[2];
+  w->done_pair_evals = (double)c[3] * pl->p.S;
+  w->done_pruned_starts = (double)c[4];
   return LIGATE_OK;
 }
 
@@ -1398,7 +1426,7 @@ extern "C" void ligate_plan_destroy(ligate_plan *pl) { free_plan(pl); }
 // One docking run of a plan, launched directly on `st` (no graph).
 static cudaError_t plan_launch(ligate_plan *pl, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(pl->counters, 0, pl->counter_bytes, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(pl->stats, 0, 3 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->stats, 0, N_STATS * sizeof(unsigned long long), st);
   if (e == cudaSuccess && pl->p.n_items > 0)
     e = launch_dock(pl->mode, pl->tile.reg_cap, pl->p, pl->grid, pl->block, pl->smem, st);
   pl->rows = pl->n_ligands;
@@ -1430,12 +1458,13 @@ extern "C" ligate_status ligate_dock_batch(const ligate_pocket *P, const ligate_
     ligate_batch_destroy(B);
     return st;
   }
-  // Two parts: the first eighth is packed, planned and launched, then the
-  // rest is packed, uploaded and planned on the host while the first part
-  // docks (an eighth of the work is several times the rest's host time),
-  // and its kernel fills the SMs as the first one's CTAs finish (two
+  // Two parts: the first 1/32 of the ligands is packed, planned and
+  // launched, then the rest is packed, uploaded and planned on the host
+  // while the first part docks (its kernel time about matches the rest's
+  // host time; a larger first part only lengthens the exposed start), and
+  // the second kernel fills the SMs as the first one's CTAs finish (two
   // library streams).  The same poses as one plan over all ligands.
-  const int first = n / 8;
+  const int first = n / 32;
   const int32_t a0 = L->atom_offset[first], b0 = L->bond_offset[first];
   std::vector<int32_t> aoB(n - first + 1), boB(n - first + 1);
   for (int i = 0; i <= n - first; ++i) {

@@ -43,11 +43,13 @@ int dock_memo1_tables(const LigDesc &d, const BondRec *bonds, int) {
 // whose minimum over the circle is D0 + 2P - 2 sqrt(P^2 + Q^2).  A
 // pair whose minimum is beyond d_c contributes exactly zero at every
 // step and is dropped; the others are evaluated in closed form.
-// Warp-collective: every lane calls it, each with its own group's data.
+// Warp-collective: every lane calls it, each with its own group's data; a
+// group that is not `alive` (its start was pruned) loads and tests nothing.
 __device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem &w, const float4 *pose,
                                              const LigDesc &d, const BondRec &br, float nx, float ny,
                                              float nz, const float4 &pv, float ck, float sk, int g,
-                                             int k, int L, int G, unsigned &n_test, unsigned &n_pair) {
+                                             int k, int L, int G, unsigned &n_test, unsigned &n_pair,
+                                             bool alive = true) {
   float ac = 0.f;
   const int cap = PAIR_WARP / G;  // = 6 L
   float4 *list = w.list + g * cap;
@@ -56,7 +58,7 @@ __device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem
   const unsigned below = (1u << k) - 1u;
   const float omc = 1.f - ck;
   int cnt = 0;
-  for (int j = k; j < d.n_atoms; j += L) {
+  for (int j = alive ? k : d.n_atoms; j < d.n_atoms; j += L) {
     const float4 xj = pose[j];
     const float fx = xj.x - pv.x, fy = xj.y - pv.y, fz = xj.z - pv.z;
     const float a = fmaf(fx, nx, fmaf(fy, ny, fz * nz));
@@ -109,7 +111,7 @@ __device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem
   // moved atom, the minimum distance over its circle is
   // sqrt(da^2 + (b_j - b_i)^2)
   const uint16_t *cand = p.cand + d.cand_base + br.cand_off;
-  n_test += br.n_cand;
+  if (alive) n_test += br.n_cand;
   // PASSES independent passes of L candidates per iteration: their
   // loads and tests overlap, then the survivors are appended in order
   constexpr int PASSES = 4;
@@ -119,13 +121,13 @@ __device__ __forceinline__ float clash_sweep(const DockParams &p, const WarpSmem
 #pragma unroll
     for (int u = 0; u < PASSES; ++u) {
       const int c = c0 + u * L + k;
-      pr[u] = c < br.n_cand ? __ldg(cand + c) : 0u;
+      pr[u] = alive && c < br.n_cand ? __ldg(cand + c) : 0u;
     }
 #pragma unroll
     for (int u = 0; u < PASSES; ++u) {
       const float2 hi = cab[pr[u] & 0xffu], hj = cab[pr[u] >> 8];
       const float da = hi.x - hj.x, db = hj.y - hi.y;
-      surv[u] = (c0 + u * L + k < br.n_cand) && fmaf(da, da, db * db) < p.dc2_grid_margin;
+      surv[u] = alive && (c0 + u * L + k < br.n_cand) && fmaf(da, da, db * db) < p.dc2_grid_margin;
     }
 #pragma unroll
     for (int u = 0; u < PASSES; ++u) {
@@ -260,6 +262,52 @@ __device__ __forceinline__ void l2_discard(const void *lo, const void *hi, int l
   __syncwarp();
 }
 
+// Lower bound of a start's final energy (branch and bound on the sweep).
+// A bond turns the DFS range (v, end); atom i is moved by no bond after the
+// last one whose range holds it.  Before bond b the atoms with lastb <= b are
+// fixed for good, the others can still reach any cell, and the clash term is
+// never negative, so the final energy is at least
+//   A_b + lbc[b],  A_b = grid energy of the fixed atoms at the current pose,
+//   lbc[b] = sum over the atoms a bond >= b moves of their type's map minimum.
+// lastb[i] = 1 + that last bond (0: no bond moves atom i).  Warp-collective.
+__device__ void bound_setup(const DockParams &p, const WarpSmem &w, const LigDesc &d, int lane) {
+  for (int i = lane; i < d.n_atoms; i += 32) {
+    int last = 0;
+    for (int b = 0; b < d.n_rot; ++b) {
+      const BondRec &br = w.bonds[b];
+      if (i > br.v && i < br.end) last = b + 1;
+    }
+    w.lastb[i] = (uint8_t)last;
+  }
+  for (int s = 0; s <= d.n_rot; ++s) {  // each lane reads the lastb entries it wrote
+    float a = 0.f;
+    for (int i = lane; i < d.n_atoms; i += 32)
+      if (w.lastb[i] > s) a += p.gmin[__float_as_int(w.ref[i].w)];
+    a = warp_sum(a);
+    if (lane == 0) w.lbc[s] = a;
+  }
+  __syncwarp();
+}
+
+// Order-preserving 32-bit key of a float (smaller value, smaller key) and
+// its inverse; the argmin of the sweep uses the same map.
+__device__ __forceinline__ unsigned value_key(float v) {
+  const unsigned b = __float_as_uint(v);
+  return b ^ ((unsigned)((int)b >> 31) | 0x80000000u);
+}
+__device__ __forceinline__ float key_value(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+}
+
+// True when a start whose final energy is at least `lb` cannot enter a top-K
+// whose K-th best energy is `thr`.  The margin covers the FP32 rounding of
+// the running energy and of the bound (sums of at most 128 terms of
+// magnitude at most the cap, over at most 16 bonds), so the test holds for
+// the kernel's own arithmetic; an empty top-K (thr = inf) prunes nothing.
+__device__ __forceinline__ bool beyond_bound(float lb, float thr) {
+  return lb > thr + 1.f + (fabsf(thr) + fabsf(lb)) * (1.f / 1024.f);
+}
+
 // ---------------------------------------------------------------------------
 // CTAs of at most 128 threads; MINB of them must fit on one SM: 4 caps the
 // registers at 128 (16 resident warps), 5 at 102 (20 warps), 6 at 85 (24
@@ -308,17 +356,28 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
       cur = item.ligand;
       n_memo = min(d.n_rot, memo_bonds(S));
       if (n_memo > 0) build_memo(p, w, pose, d, n_memo, ck, sk, g, k, L, G, S, m1);
+      bound_setup(p, w, d, lane);
     }
     top.clear();
-    unsigned n_atom = 0, n_test = 0, n_pair = 0;  // work counters of this lane's group
+    float thr = INF;  // K-th best energy of the item so far: a start bounded above it stops
+    float thr_pub = INF;  // the last value this warp shared with the row's other items
+    unsigned *const row_thr = p.lig_thr ? p.lig_thr + item.row : nullptr;
+    // work counters of this lane's group: atom interpolations, pair tests,
+    // pair survivors, candidate pairs of the evaluated sweeps, pruned starts
+    unsigned n_atom = 0, n_test = 0, n_pair = 0, n_cand = 0, n_prn = 0;
 
     for (int s0 = item.s0; s0 < item.s1; s0 += G) {
       const int sid = min(s0 + g, item.s1 - 1);  // a group past the end repeats the last start
       const unsigned n_atom0 = n_atom, n_test0 = n_test, n_pair0 = n_pair;
+      // the row's shared K-th best (any item's is at least the row's final
+      // one, so it bounds as safely as this item's own), loaded now and used
+      // after the rigid stage's gathers
+      unsigned shared_key = 0;
+      if (row_thr && lane == 0) shared_key = __ldcg(row_thr);
       // -- rigid start: pose = R_o (x - c) / h + (a - origin) / h
       float R[9], T[3];
       start_frame(p, sid, R, T);
-      float e = 0.f;
+      float e = 0.f, ef = 0.f;  // ef: the atoms no bond moves
       for (int i = k; i < d.n_atoms; i += L) {
         const float4 r = w.ref[i];
         float4 u;
@@ -328,16 +387,28 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         const int toff = __float_as_int(r.w) * ts;
         u.w = __int_as_float(toff);
         pose[i] = u;
-        e += grid_eval<MODE>(p.maps, toff, u.x, u.y, u.z, p.g);
+        const float gi = grid_eval<MODE>(p.maps, toff, u.x, u.y, u.z, p.g);
+        e += gi;
+        if (w.lastb[i] == 0) ef += gi;
       }
-      for (int o = L >> 1; o > 0; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
+      for (int o = L >> 1; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(FULL, e, o);
+        ef += __shfl_xor_sync(FULL, ef, o);
+      }
       float E = fmaf(p.clash_w, clash_ref, e);
+      float A = ef;  // grid energy of the atoms fixed for good (the bound's first part)
+      shared_key = __shfl_sync(FULL, shared_key, 0);
+      const float thr_use = fminf(thr, shared_key ? key_value(~shared_key) : INF);
+      // a group past the item's end, or a start bounded above the K-th best, sweeps nothing
+      bool alive = s0 + g < item.s1 && !beyond_bound(A + w.lbc[0], thr_use);
+      if (s0 + g < item.s1 && !alive) ++n_prn;
       n_atom += d.n_atoms;
       uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
       __syncwarp();
 
       // -- greedy torsion sweep
       for (int b = 0; b < d.n_rot; ++b) {
+        if (!__any_sync(FULL, alive)) break;  // every start of the warp is pruned
         const BondRec br = w.bonds[b];
         const float4 pv = pose[br.v];
         float nx, ny, nz;
@@ -346,17 +417,22 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         rot.make(ck, sk, nx, ny, nz, pv.x, pv.y, pv.z);
         // grid part: every moved atom at this lane's torsion step, two atoms
         // per iteration: two map gathers in flight per lane, and the rotation
-        // and interpolation arithmetic of the pair in packed FP32 (FFMA2)
-        float ag = 0.f, ag2 = 0.f;
+        // and interpolation arithmetic of the pair in packed FP32 (FFMA2);
+        // agf: the atoms this bond moves for the last time (fixed after it)
+        float ag = 0.f, ag2 = 0.f, agf = 0.f;
+        const int bb = b + 1, iend = alive ? br.end : 0;  // a pruned group evaluates nothing
         int i = br.v + 1;
-        for (; i + 1 < br.end; i += 2) {
+        for (; i + 1 < iend; i += 2) {
           const float4 q = pose[i], q2 = pose[i + 1];
           if (MODE == MODE_F32_PLAIN) {  // eight scalar gathers each: registers go to loads in flight
             float yx, yy, yz, zx, zy, zz;
             rot.apply(q.x, q.y, q.z, yx, yy, yz);
             rot.apply(q2.x, q2.y, q2.z, zx, zy, zz);
-            ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
-            ag2 += grid_eval<MODE>(p.maps, __float_as_int(q2.w), zx, zy, zz, p.g);
+            const float ga = grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
+            const float gb = grid_eval<MODE>(p.maps, __float_as_int(q2.w), zx, zy, zz, p.g);
+            ag += ga;
+            ag2 += gb;
+            agf += (w.lastb[i] == bb ? ga : 0.f) + (w.lastb[i + 1] == bb ? gb : 0.f);
             continue;
           }
           const float2 X = make_float2(q.x, q2.x), Y = make_float2(q.y, q2.y), Z = make_float2(q.z, q2.z);
@@ -370,15 +446,21 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
                                             ox.y, oy.y, oz.y, p.g);
           ag += v.x;
           ag2 += v.y;
+          agf += (w.lastb[i] == bb ? v.x : 0.f) + (w.lastb[i + 1] == bb ? v.y : 0.f);
         }
-        if (i < br.end) {
+        if (i < iend) {
           const float4 q = pose[i];
           float yx, yy, yz;
           rot.apply(q.x, q.y, q.z, yx, yy, yz);
-          ag += grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
+          const float ga = grid_eval<MODE>(p.maps, __float_as_int(q.w), yx, yy, yz, p.g);
+          ag += ga;
+          if (w.lastb[i] == bb) agf += ga;
         }
         ag += ag2;
-        n_atom += (unsigned)(br.end - br.v - 1) * (unsigned)S;
+        if (alive) {
+          n_atom += (unsigned)(br.end - br.v - 1) * (unsigned)S;
+          n_cand += (unsigned)br.n_cand;
+        }
         float ac;
         if (b < n_memo) {  // looked up: bond 0, or bond 1 after bond 0's step
           ac = k < S ? w.memo[b == 0 ? k : S + (int)(t0 & 0xffu) * S + k] : 0.f;
@@ -387,7 +469,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
           // step, loaded before the live sweep and added after it
           const bool has1 = m1 && b >= 2 && br.n_cand1 > 0;  // warp-uniform
           float c1 = 0.f;
-          if (has1 && k < S) {
+          if (alive && has1 && k < S) {
             const int e1 = br.e1 & 0xffff, q = e1 >> 2;
             const uint32_t tw = q == 0 ? t0 : q == 1 ? t1 : q == 2 ? t2 : t3;
             c1 = __ldcg(m1 + ((br.e1 >> 16) * S + ((tw >> (8 * (e1 & 3))) & 0xff)) * S + k);
@@ -396,7 +478,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
           const int skip = br.n_cand0 + (has1 ? br.n_cand1 : 0);
           live.cand_off += skip;
           live.n_cand -= skip;
-          ac = clash_sweep(p, w, pose, d, live, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair);
+          ac = clash_sweep(p, w, pose, d, live, nx, ny, nz, pv, ck, sk, g, k, L, G, n_test, n_pair, alive);
           if (br.n_cand0 > 0 && k < S) ac += w.memo[memo_row0(S) + (b - memo_bonds(S)) * S + k];
           ac += c1;
         }
@@ -407,12 +489,17 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         const unsigned key = vb ^ ((unsigned)((int)vb >> 31) | 0x80000000u);
         const unsigned gmask = L == 32 ? FULL : (((1u << L) - 1u) << glead);
         const unsigned kmin = __reduce_min_sync(gmask, key);
-        const int bk = __ffs(__ballot_sync(FULL, key == kmin) & gmask) - 1 - glead;
+        const int bk1 = __ffs(__ballot_sync(FULL, key == kmin) & gmask) - 1 - glead;
+        const int bk = alive ? bk1 : 0;  // a pruned group keeps its pose
         const float best = __uint_as_float((kmin & 0x80000000u) ? (kmin ^ 0x80000000u) : ~kmin);
         const float V0 = __shfl_sync(FULL, V, glead);
         const float cb = __shfl_sync(FULL, ck, glead + bk);
         const float sb = __shfl_sync(FULL, sk, glead + bk);
         E += best - V0;
+        // the atoms fixed from now on at the chosen step join the bound's
+        // first part; the rest may still reach their map minimum
+        A += __shfl_sync(FULL, agf, glead + bk);
+        if (alive && bb < d.n_rot && beyond_bound(A + w.lbc[bb], thr_use)) { alive = false; ++n_prn; }
         const uint32_t bits = (uint32_t)bk << (8 * (b & 3));
         switch (b >> 2) { case 0: t0 |= bits; break; case 1: t1 |= bits; break;
                           case 2: t2 |= bits; break; default: t3 |= bits; }
@@ -431,27 +518,39 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
 
       if (s0 + g >= item.s1) { n_atom = n_atom0; n_test = n_test0; n_pair = n_pair0; }
 
-      // -- candidates of this start group into the warp's top-K
+      // -- candidates of this start group into the warp's top-K (a pruned
+      // start's energy exceeds the K-th best: it could not enter)
       for (int gg = 0; gg < G; ++gg) {
         const int src = gg * L;
         const float ce = __shfl_sync(FULL, E, src);
         const uint32_t c0 = __shfl_sync(FULL, t0, src), c1 = __shfl_sync(FULL, t1, src),
                        c2 = __shfl_sync(FULL, t2, src), c3 = __shfl_sync(FULL, t3, src);
-        if (s0 + gg < item.s1) top.insert(ce, s0 + gg, c0, c1, c2, c3, K, lane);
+        const bool live = __shfl_sync(FULL, alive, src);
+        if (live) top.insert(ce, s0 + gg, c0, c1, c2, c3, K, lane);
+      }
+      thr = __shfl_sync(FULL, top.e, K - 1);
+      if (row_thr && thr < thr_pub) {  // share an improved K-th best with the row's other items
+        if (lane == 0) atomicMax(row_thr, ~value_key(thr));
+        thr_pub = thr;
       }
     }
 
     if (p.stats) {  // one count per start group (its lane 0)
-      unsigned long long a = k == 0 ? n_atom : 0, t = k == 0 ? n_test : 0, q = k == 0 ? n_pair : 0;
+      unsigned long long a = k == 0 ? n_atom : 0, t = k == 0 ? n_test : 0, q = k == 0 ? n_pair : 0,
+                         c = k == 0 ? n_cand : 0, r = k == 0 ? n_prn : 0;
       for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(FULL, a, o);
         t += __shfl_xor_sync(FULL, t, o);
         q += __shfl_xor_sync(FULL, q, o);
+        c += __shfl_xor_sync(FULL, c, o);
+        r += __shfl_xor_sync(FULL, r, o);
       }
       if (lane == 0) {
         atomicAdd(p.stats + 0, a);
         atomicAdd(p.stats + 1, t);
         atomicAdd(p.stats + 2, q);
+        atomicAdd(p.stats + 3, c);
+        atomicAdd(p.stats + 4, r);
       }
     }
 

@@ -222,8 +222,13 @@ struct WarpSmem {
   float4 *list;    // [PAIR_WARP] clash pairs that survive the circle bound of a bond
   float2 *cab;     // [G][nmax] (axial coordinate, radial distance) about the bond axis
   BondRec *bonds;  // [LIGATE_MAX_ROT]
+  float *lbc;      // [LBC_FLOATS] per sweep stage b: sum of the map minima of the atoms bonds >= b move
+  uint8_t *lastb;  // [nmax] 1 + the last bond that moves each atom (0: no bond moves it)
   float *memo;     // [memo_floats(S, rmax)] clash sums that every start shares
 };
+
+// floats of WarpSmem::lbc (LIGATE_MAX_ROT + 1 stages, padded to 16 bytes)
+constexpr int LBC_FLOATS = (LIGATE_MAX_ROT + 1 + 3) / 4 * 4;
 
 // Surviving clash pairs buffered per warp before they are evaluated for
 // every torsion step: 192 entries, 192 / G = 6 L per start group (the
@@ -251,7 +256,8 @@ __host__ __device__ inline int memo_floats(int S, int rmax) {
 // keep a histogram there, 0 for those that need neither).
 __host__ __device__ inline size_t smem_bytes_per_warp(int nmax, int S, int G, int rmax, int list = PAIR_WARP) {
   return (size_t)nmax * 16 + (size_t)G * (nmax + 1) * 16 + (size_t)list * 16 +
-         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)memo_floats(S, rmax) * 4;
+         (size_t)G * nmax * 8 + sizeof(BondRec) * LIGATE_MAX_ROT + (size_t)LBC_FLOATS * 4 +
+         (size_t)((nmax + 15) & ~15) + (size_t)memo_floats(S, rmax) * 4;
 }
 
 
@@ -262,7 +268,9 @@ __device__ __forceinline__ WarpSmem warp_smem(unsigned char *base, int nmax, int
   w.list = w.pose + (size_t)G * (nmax + 1);
   w.cab = reinterpret_cast<float2 *>(w.list + list);
   w.bonds = reinterpret_cast<BondRec *>(w.cab + (size_t)G * nmax);
-  w.memo = reinterpret_cast<float *>(w.bonds + LIGATE_MAX_ROT);
+  w.lbc = reinterpret_cast<float *>(w.bonds + LIGATE_MAX_ROT);
+  w.lastb = reinterpret_cast<uint8_t *>(w.lbc + LBC_FLOATS);
+  w.memo = reinterpret_cast<float *>(w.lastb + ((nmax + 15) & ~15));
   return w;
 }
 

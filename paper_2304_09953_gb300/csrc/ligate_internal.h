@@ -84,6 +84,7 @@ struct PocketDev {
   float *map_f32c = nullptr;       // corner [T][cells][8]
   uint16_t *map_bf16c = nullptr;   // corner [T][cells][8]
   uint16_t *map_f16c = nullptr;    // corner [T][cells][8]
+  float h_min[LIGATE_MAX_TYPES] = {};  // least value of each type's map (FP32)
   size_t n_nodes() const { return (size_t)nx * ny * nz; }
   size_t n_cells() const { return (size_t)(nx - 1) * (ny - 1) * (nz - 1); }
   // receptor for exact rescoring (ligate_pocket_set_receptor), grid units,
@@ -152,6 +153,12 @@ struct Item {
   int pad[3];
 };
 
+// Work counters of a docking run (DockParams::stats): atom interpolations,
+// clash candidates tested against the circle bound, surviving pairs,
+// candidate pairs of the evaluated sweeps (memoised ones included; times S
+// gives the pair trials), starts bounded out of the top-K.
+constexpr int N_STATS = 5;
+
 struct DockParams {
   // batch
   const LigDesc *lig;
@@ -177,7 +184,7 @@ struct DockParams {
   float inv_dc2_grid;      // h^2 / d_c^2
   float inv_dc2_ang;       // 1 / d_c^2
   float dc2_grid_margin;   // (d_c / h)^2 (1 + 1e-4): pairs beyond it never clash
-  unsigned long long *stats;  // optional [3]: atom interpolations, pair tests, pair evaluations
+  unsigned long long *stats;  // optional [N_STATS]: see N_STATS
   int rescore;
   // work queue
   const Item *items;
@@ -187,6 +194,8 @@ struct DockParams {
   const int *lig_slot0;    // [n_ligands] first partial slot of each ligand
   int *queue;              // [1] next item
   int *done;               // [n_ligands] finished items per ligand
+  unsigned *lig_thr;       // optional [n_ligands]: least K-th best energy any item of the row has
+                           // reached, as ~(order-preserving key); 0 (reset value) = none yet
   PoseOut *partial;        // [n_items][K]
   PoseOut *out;            // [n_ligands][K]
   // shared-memory shape
@@ -196,7 +205,13 @@ struct DockParams {
   float *memo1;            // [resident warps][m1max][S][S] clash sums of the pairs one earlier bond
                            // separates, by that bond's step (null: those pairs are swept live)
   int m1max;               // tables per warp (bonds with such pairs, largest ligand)
+  // smallest value an atom of each type can score: the least stored map
+  // value (in the sweep map's precision) or the out-of-box penalty
+  float gmin[LIGATE_MAX_TYPES];
 };
+
+// gmin of DockParams for the sweep map of layout `mode`.
+void set_map_minima(DockParams &p, const PocketDev &d, int mode);
 
 // cos/sin of the S torsion steps 2 pi k / S (k = 0 exactly (1, 0)), FP64
 // rounded to FP32, into tab[2k], tab[2k + 1].

@@ -197,6 +197,7 @@ extern "C" ligate_status ligate_dock_noalloc(const ligate_pocket *P, const ligat
   p.g.fx1 = (float)(pk.nx - 1); p.g.fy1 = (float)(pk.ny - 1); p.g.fz1 = (float)(pk.nz - 1);
   p.g.penalty = s->penalty;
   p.g.cx = 8388608.f + (float)(pk.nx - 2); p.g.cy = 8388608.f + (float)(pk.ny - 2); p.g.cz = 8388608.f + (float)(pk.nz - 2);
+  set_map_minima(p, pk, mode);
   p.rot = (const float *)(base + o_rot);
   p.anc = (const float *)(base + o_anc);
   p.n_anchor = s->n_anchor;

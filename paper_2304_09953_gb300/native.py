@@ -76,7 +76,8 @@ class ligate_work(ctypes.Structure):
     _fields_ = [("poses", ctypes.c_double), ("atom_evals", ctypes.c_double),
                 ("pair_evals", ctypes.c_double), ("starts", ctypes.c_double),
                 ("done_atom_evals", ctypes.c_double), ("done_pair_tests", ctypes.c_double),
-                ("done_pair_survivors", ctypes.c_double)]
+                ("done_pair_survivors", ctypes.c_double), ("done_pair_evals", ctypes.c_double),
+                ("done_pruned_starts", ctypes.c_double)]
 
 
 # name -> (restype, argtypes)

@@ -86,6 +86,42 @@ def test_clash_tables_with_unaligned_scratch(batched_small):
     print(st.line())
 
 
+def test_sweep_bound_counts_and_pruning(batched_small):
+    """Branch and bound on the sweep.  With K equal to the number of starts
+    the K-th best stays infinite until the last start, nothing is bounded
+    out, and the device counters equal the search space exactly.  With 256
+    starts and K = 16 starts are bounded out (fewer atom evaluations and pair
+    trials than the search space), and every checked ligand's top-K still
+    matches the oracle, which sweeps every start in full."""
+    w = batched_small
+    ph, bh = D.PocketHandle(w.pocket), D.BatchHandle(w.ligands)
+    try:
+        for mode in ("fp32", "bf16"):
+            pl = D.Plan(ph, bh, Sampling(w.sampling.quats[:2], 4, 16, 8), mode=mode)
+            pl.result()
+            wk = pl.work()
+            pl.close()
+            assert wk.done_pruned_starts == 0
+            assert wk.done_atom_evals == wk.atom_evals and wk.done_pair_evals == wk.pair_evals
+        samp = Sampling(w.sampling.quats[:32], 8, 16, 16)
+        pl = D.Plan(ph, bh, samp, mode="fp32")
+        res = pl.result()
+        wk = pl.work()
+        pl.close()
+    finally:
+        bh.close()
+        ph.close()
+    print(f"bounded out: {wk.done_pruned_starts:.0f} of {wk.starts:.0f} starts; atom evaluations "
+          f"{wk.done_atom_evals / wk.atom_evals:.3f}, pair trials {wk.done_pair_evals / wk.pair_evals:.3f} "
+          "of the search space")
+    assert 0 < wk.done_pruned_starts < wk.starts
+    assert wk.done_atom_evals < wk.atom_evals and wk.done_pair_evals < wk.pair_evals
+    st = Stats()
+    for i in range(0, w.ligands.n, 8):
+        compare_ligand(w.ligands.ligand(i), w.pocket, samp, res[i], stats=st)
+    print(st.line())
+
+
 def _dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
 
@@ -380,7 +416,11 @@ def test_host_array_call_in_two_halves_equals_plan_path(full):
     bad.bonds[j] = bad.bonds[j + 1]  # a repeated edge: no longer a tree
     with pytest.raises(N.LigateError) as err:
         N.ligate_dock_batch(ph.h, bad, s, np.zeros_like(want))
-    assert "375" in str(err.value)  # the second part starts at ligand 3000 / 8
+    # "ligand <i> ... (ligand numbers counted from ligand <first> of the input)":
+    # the second part's number plus its first input ligand is the bad one
+    import re
+    m = re.search(r"ligand (\d+): .*counted from ligand (\d+) of the input", str(err.value))
+    assert m and int(m.group(1)) + int(m.group(2)) == 2500, str(err.value)
 
 
 def test_plan_output_is_the_last_run(batched_small):
