@@ -246,7 +246,11 @@ ligate_status ligate_plan_create_subset(const ligate_pocket *pocket, const ligat
  * ligate_pose[n_ligands][top_k] in ligand order, stays in the plan's device
  * buffer (ligate_plan_output); if `out` is not NULL it is also copied there
  * (host or device pointer) and, for host memory, the stream is
- * synchronised. */
+ * synchronised.  The result is each ligand's top_k over all its starts;
+ * a start's greedy sweep stops early once a lower bound of its final
+ * energy (the grid energy of the atoms no later bond moves plus each
+ * movable atom's map minimum) exceeds the top_k-th best energy already
+ * found, which cannot change the result (ligate_work counts such starts). */
 ligate_status ligate_plan_run(ligate_plan *plan, ligate_pose *out, void *stream);
 /* Enqueue one docking run of a SELECTION of the plan's ligands (paper
  * Sec. 3.5: only the ligands a cheaper predictor ranks best are docked),
