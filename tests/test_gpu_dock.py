@@ -122,6 +122,30 @@ def test_sweep_bound_counts_and_pruning(batched_small):
     print(st.line())
 
 
+def test_target_library_sample(workload_factory):
+    """Ligands of the 1,000,000-ligand target library (up to 80 atoms and 15
+    rotatable bonds, so all four packed torsion words; 8 x 96^3 maps), 256
+    starts: the FP32 form against the oracle on the largest and most flexible
+    ligands of the first 64, and the BF16 form with FP32 rescoring within
+    0.02 of the oracle's best on the same ligands."""
+    w = workload_factory("combined", n_ligands=64)
+    samp = Sampling(w.sampling.quats[:32], 8, w.sampling.torsion_steps, 16)
+    n_at = np.diff(w.ligands.atom_offset)
+    pick = sorted(set(np.argsort(-w.ligands.n_rot, kind="stable")[:6].tolist()) |
+                  set(np.argsort(-n_at, kind="stable")[:6].tolist()))
+    assert w.ligands.n_rot[pick].max() >= 13 and n_at[pick].max() >= 60
+    res = D.dock(w.pocket, w.ligands, samp, mode="fp32")
+    low = D.dock(w.pocket, w.ligands, samp, mode="bf16")
+    st = Stats()
+    errs = []
+    for i in pick:
+        lig = w.ligands.ligand(int(i))
+        info = compare_ligand(lig, w.pocket, samp, res[i], stats=st)
+        errs.append(abs(float(low[i]["score"][0]) - info["oracle_best"]))
+    print(st.line(), f"bf16 best vs oracle best: max {max(errs):.2e}")
+    assert max(errs) <= 0.02
+
+
 def _dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
 
