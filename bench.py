@@ -83,7 +83,7 @@ def algorithmic_flops(work, S, n_starts, total_atoms):
 # valid only for the kernel revision it was captured on (sha1 prefix of
 # dock.cu + dock_device.cuh); any other revision reports null until it is
 # captured again.
-TRAFFIC_BYTES = {("364cd6c24966", "batched", 10000): 98448896 + 42856704}
+TRAFFIC_BYTES = {("f0c666ff79a6", "batched", 10000): 96995328 + 41508864}
 
 
 def kernel_source_sha():

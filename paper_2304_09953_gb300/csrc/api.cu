@@ -68,6 +68,31 @@ using namespace ligate;
 // it (round to nearest is monotonic, so this is the least stored value; a
 // trilinear interpolation of stored values lies above it up to FP32
 // rounding), or the out-of-box penalty if that is lower.
+std::vector<uint16_t> ligate::anchor_visit_order(const float *xyz, int n) {
+  std::vector<uint16_t> order;
+  order.reserve(n);
+  std::vector<char> used(n, 0);
+  for (int a = 0; a < n; ++a) {
+    if (used[a]) continue;
+    used[a] = 1;
+    order.push_back((uint16_t)a);
+    int best = -1;
+    double bd = 0;
+    for (int c = 0; c < n; ++c) {
+      if (used[c]) continue;
+      const double dx = xyz[3 * a] - xyz[3 * c], dy = xyz[3 * a + 1] - xyz[3 * c + 1],
+                   dz = xyz[3 * a + 2] - xyz[3 * c + 2];
+      const double d2 = dx * dx + dy * dy + dz * dz;
+      if (best < 0 || d2 < bd) { best = c; bd = d2; }
+    }
+    if (best >= 0) {
+      used[best] = 1;
+      order.push_back((uint16_t)best);
+    }
+  }
+  return order;
+}
+
 void ligate::set_map_minima(DockParams &p, const PocketDev &d, int mode) {
   for (int t = 0; t < LIGATE_MAX_TYPES; ++t) {
     float v = t < d.n_types ? d.h_min[t] : 0.f;
@@ -859,6 +884,7 @@ struct ligate_plan {
   size_t smem = 0;
   int n_ligands = 0;
   float *rot = nullptr, *anc = nullptr, *quat = nullptr;
+  uint16_t *visit = nullptr;  // anchor visiting order (DockParams::visit)
   Item *items = nullptr;
   int *lig_items = nullptr, *lig_slot0 = nullptr, *counters = nullptr;
   PoseOut *partial = nullptr, *out = nullptr;
@@ -899,7 +925,7 @@ static void free_plan(ligate_plan *pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
-  cudaFree(pl->rot); cudaFree(pl->anc); cudaFree(pl->quat);
+  cudaFree(pl->rot); cudaFree(pl->anc); cudaFree(pl->quat); cudaFree(pl->visit);
   cudaFree(pl->items); cudaFree(pl->lig_items); cudaFree(pl->lig_slot0);
   cudaFree(pl->counters); cudaFree(pl->partial); cudaFree(pl->out); cudaFree(pl->stats);
   cudaFree(pl->row_lig);
@@ -992,6 +1018,14 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
                    opt ? opt->anc : nullptr);
   if (st != LIGATE_OK) { free_plan(pl); return st; }
   DockParams &p = pl->p;
+  {  // consecutive starts of a work item at nearby anchors
+    const std::vector<uint16_t> order = anchor_visit_order(P->d.h_anchors.data(), s->n_anchor);
+    cudaError_t e = dmalloc(&pl->visit, order.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(pl->visit, order.data(), sizeof(uint16_t) * order.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_plan(pl); return cuda_fail(e, "plan allocation"); }
+    p.visit = pl->visit;
+  }
   const int sms = device_sms();
   memset(&pl->tile, 0, sizeof(pl->tile));
   if (tile) pl->tile = *tile;

@@ -367,7 +367,10 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
     unsigned n_atom = 0, n_test = 0, n_pair = 0, n_cand = 0, n_prn = 0;
 
     for (int s0 = item.s0; s0 < item.s1; s0 += G) {
-      const int sid = min(s0 + g, item.s1 - 1);  // a group past the end repeats the last start
+      // visit index (a group past the end repeats the last one) -> start id:
+      // each orientation's anchors in the plan's visiting order
+      const int vi = min(s0 + g, item.s1 - 1);
+      const int sid = p.visit ? vi - vi % p.n_anchor + p.visit[vi % p.n_anchor] : vi;
       const unsigned n_atom0 = n_atom, n_test0 = n_test, n_pair0 = n_pair;
       // the row's shared K-th best (any item's is at least the row's final
       // one, so it bounds as safely as this item's own), loaded now and used
@@ -526,7 +529,8 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         const uint32_t c0 = __shfl_sync(FULL, t0, src), c1 = __shfl_sync(FULL, t1, src),
                        c2 = __shfl_sync(FULL, t2, src), c3 = __shfl_sync(FULL, t3, src);
         const bool live = __shfl_sync(FULL, alive, src);
-        if (live) top.insert(ce, s0 + gg, c0, c1, c2, c3, K, lane);
+        const int cs = __shfl_sync(FULL, sid, src);
+        if (live) top.insert(ce, cs, c0, c1, c2, c3, K, lane);
       }
       thr = __shfl_sync(FULL, top.e, K - 1);
       if (row_thr && thr < thr_pub) {  // share an improved K-th best with the row's other items

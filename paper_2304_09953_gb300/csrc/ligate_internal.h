@@ -205,6 +205,10 @@ struct DockParams {
   float *memo1;            // [resident warps][m1max][S][S] clash sums of the pairs one earlier bond
                            // separates, by that bond's step (null: those pairs are swept live)
   int m1max;               // tables per warp (bonds with such pairs, largest ligand)
+  // optional [n_anchor]: the order a work item visits each orientation's
+  // anchors in (consecutive entries are spatially close anchors, so the
+  // start groups of a warp sweep similar poses); null: anchor order
+  const uint16_t *visit;
   // smallest value an atom of each type can score: the least stored map
   // value (in the sweep map's precision) or the out-of-box penalty
   float gmin[LIGATE_MAX_TYPES];
@@ -212,6 +216,12 @@ struct DockParams {
 
 // gmin of DockParams for the sweep map of layout `mode`.
 void set_map_minima(DockParams &p, const PocketDev &d, int mode);
+
+// Visiting order of the first n of the pocket's anchors (DockParams::visit):
+// anchors paired greedily with their nearest remaining neighbour (Euclidean
+// distance, ties to the smaller index), pairs in the order of their first
+// anchor; deterministic.
+std::vector<uint16_t> anchor_visit_order(const float *anchors_xyz, int n);
 
 // cos/sin of the S torsion steps 2 pi k / S (k = 0 exactly (1, 0)), FP64
 // rounded to FP32, into tab[2k], tab[2k + 1].

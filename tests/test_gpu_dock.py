@@ -423,10 +423,10 @@ def test_device_subset_run_equals_rows_of_full_run(batched_small):
 
 
 def test_host_array_call_in_two_halves_equals_plan_path(full):
-    """ligate_dock_batch on 3,000 ligands packs and docks the library in two
-    parts (the second packed while the first docks, on two streams): the
-    same poses as one plan over all of them; a malformed ligand in the
-    second part is reported with its number in the input."""
+    """ligate_dock_batch on 3,000 ligands packs and docks the library in
+    parts (each packed while the previous one docks, one stream per part):
+    the same poses as one plan over all of them; a malformed ligand in a
+    later part is reported with its number in the input."""
     sub = make_workload("batched", n_ligands=3000, pocket=full.pocket)
     ph = D.PocketHandle(sub.pocket)
     bh = D.BatchHandle(sub.ligands)
