@@ -14,6 +14,13 @@
 // a shared-memory broadcast.  Only the moved side of the current bond is
 // re-scored (the rest of the score is the same for every k); the k = 0 lane
 // re-evaluates the current pose, so E += V(k*) - V(0).
+//
+// Branch and bound: a start whose lower bound on its final energy exceeds
+// the K-th best energy already found stops sweeping (bound_setup,
+// beyond_bound); the top-K is unchanged.  The two groups of a warp run in
+// lockstep, so a work item visits each orientation's anchors in the plan's
+// nearest-neighbour pair order (DockParams::visit): partners sweep nearby
+// poses and tend to stop together, and then the warp leaves the bond loop.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
