@@ -1018,7 +1018,7 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
                    opt ? opt->anc : nullptr);
   if (st != LIGATE_OK) { free_plan(pl); return st; }
   DockParams &p = pl->p;
-  {  // consecutive starts of a work item at nearby anchors
+  if (s->n_anchor <= 1024) {  // consecutive starts of a work item at nearby anchors (O(n^2) pairing)
     const std::vector<uint16_t> order = anchor_visit_order(P->d.h_anchors.data(), s->n_anchor);
     cudaError_t e = dmalloc(&pl->visit, order.size());
     if (e == cudaSuccess)

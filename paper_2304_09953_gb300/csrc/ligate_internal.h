@@ -207,7 +207,8 @@ struct DockParams {
   int m1max;               // tables per warp (bonds with such pairs, largest ligand)
   // optional [n_anchor]: the order a work item visits each orientation's
   // anchors in (consecutive entries are spatially close anchors, so the
-  // start groups of a warp sweep similar poses); null: anchor order
+  // start groups of a warp sweep similar poses); null: anchor order (plans
+  // with more than 1,024 anchors, the allocation-free entry point)
   const uint16_t *visit;
   // smallest value an atom of each type can score: the least stored map
   // value (in the sweep map's precision) or the out-of-box penalty
