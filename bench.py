@@ -83,7 +83,7 @@ def algorithmic_flops(work, S, n_starts, total_atoms):
 # valid only for the kernel revision it was captured on (sha1 prefix of
 # dock.cu + dock_device.cuh); any other revision reports null until it is
 # captured again.
-TRAFFIC_BYTES = {("f0c666ff79a6", "batched", 10000): 96995328 + 41508864}
+TRAFFIC_BYTES = {("3784072d478c", "batched", 10000): 100289536 + 45178112}
 
 
 def kernel_source_sha():
@@ -590,6 +590,10 @@ def main():
     poses_s = sum_over_ranks(work.poses, device="cuda") * args.steps / t_chosen
     mean_ms = t_chosen * 1000 / args.steps
     S = w.sampling.torsion_steps
+    # unique poses the kernels evaluated (the rest of the search space was
+    # excluded by the sweep's bound): starts + evaluated bond sweeps x (S - 1)
+    poses_eval_s = sum_over_ranks(work.starts + work.done_bond_sweeps * (S - 1),
+                                  device="cuda") * args.steps / t_chosen
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     mhz = clock_info["sm_mhz"] or clock_info["sm_max_mhz"] or 2070.0
@@ -752,11 +756,15 @@ def main():
                             "starts_per_item": list(t_.starts_per_item), "reg_cap": t_.reg_cap},
                    "autotune_s": round(tune_s, 2), "parallelism": f"replicas x{ws}"},
         "poses_per_s": poses_s,
+        "poses_evaluated_per_s": poses_eval_s,
         "poses_note": "unique poses of the search space decided per second (O x A x (1 + R (S - 1)) per "
                       "ligand): evaluated, or excluded by the sweep's lower bound on a start's final "
-                      "energy; roofline FLOP counts cover the evaluated ones only",
+                      "energy (poses_evaluated_per_s: the evaluated ones); roofline FLOP counts cover the evaluated "
+                      "ones only",
         "plain": {"value": n_job / (plain_ms / 1000), "unit": "ligands/s",
-                  "poses_per_s": ws * work_plain.poses / (plain_ms / 1000), "ms_per_step": plain_ms,
+                  "poses_per_s": ws * work_plain.poses / (plain_ms / 1000),
+                  "poses_evaluated_per_s": ws * (work_plain.starts + work_plain.done_bond_sweeps * (S - 1))
+                  / (plain_ms / 1000), "ms_per_step": plain_ms,
                   "form": "fp32 plain maps, default tile, no rescore",
                   "roofline_frac": plain_alg / (plain_ms / 1000) / 1e12 / peak,
                   "roofline_frac_executed": plain_flops / (plain_ms / 1000) / 1e12 / peak,

@@ -297,6 +297,10 @@ typedef struct {
    * best energy already found (they cannot enter the top-K). */
   double done_pair_evals;
   double done_pruned_starts;
+  /* Bond sweeps the run evaluated (S trial poses each, one of them the pose
+   * already held): the evaluated unique poses are starts + done_bond_sweeps
+   * x (S - 1), against `poses` for the whole search space. */
+  double done_bond_sweeps;
 } ligate_work;
 ligate_status ligate_plan_work(const ligate_plan *plan, ligate_work *out);
 void ligate_plan_destroy(ligate_plan *plan);

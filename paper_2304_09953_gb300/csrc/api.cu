@@ -1452,6 +1452,7 @@ extern "C" ligate_status ligate_plan_work(const ligate_plan *pl, ligate_work *w)
   w->done_pair_survivors = (double)c[2];
   w->done_pair_evals = (double)c[3] * pl->p.S;
   w->done_pruned_starts = (double)c[4];
+  w->done_bond_sweeps = (double)c[5];
   return LIGATE_OK;
 }
 

@@ -370,8 +370,9 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
     float thr_pub = INF;  // the last value this warp shared with the row's other items
     unsigned *const row_thr = p.lig_thr ? p.lig_thr + item.row : nullptr;
     // work counters of this lane's group: atom interpolations, pair tests,
-    // pair survivors, candidate pairs of the evaluated sweeps, pruned starts
-    unsigned n_atom = 0, n_test = 0, n_pair = 0, n_cand = 0, n_prn = 0;
+    // pair survivors, candidate pairs of the evaluated sweeps, pruned starts,
+    // evaluated bond sweeps
+    unsigned n_atom = 0, n_test = 0, n_pair = 0, n_cand = 0, n_prn = 0, n_bsw = 0;
 
     for (int s0 = item.s0; s0 < item.s1; s0 += G) {
       // visit index (a group past the end repeats the last one) -> start id:
@@ -470,6 +471,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         if (alive) {
           n_atom += (unsigned)(br.end - br.v - 1) * (unsigned)S;
           n_cand += (unsigned)br.n_cand;
+          ++n_bsw;
         }
         float ac;
         if (b < n_memo) {  // looked up: bond 0, or bond 1 after bond 0's step
@@ -548,13 +550,14 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
 
     if (p.stats) {  // one count per start group (its lane 0)
       unsigned long long a = k == 0 ? n_atom : 0, t = k == 0 ? n_test : 0, q = k == 0 ? n_pair : 0,
-                         c = k == 0 ? n_cand : 0, r = k == 0 ? n_prn : 0;
+                         c = k == 0 ? n_cand : 0, r = k == 0 ? n_prn : 0, v = k == 0 ? n_bsw : 0;
       for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(FULL, a, o);
         t += __shfl_xor_sync(FULL, t, o);
         q += __shfl_xor_sync(FULL, q, o);
         c += __shfl_xor_sync(FULL, c, o);
         r += __shfl_xor_sync(FULL, r, o);
+        v += __shfl_xor_sync(FULL, v, o);
       }
       if (lane == 0) {
         atomicAdd(p.stats + 0, a);
@@ -562,6 +565,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
         atomicAdd(p.stats + 2, q);
         atomicAdd(p.stats + 3, c);
         atomicAdd(p.stats + 4, r);
+        atomicAdd(p.stats + 5, v);
       }
     }
 

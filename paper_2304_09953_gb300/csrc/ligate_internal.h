@@ -156,8 +156,9 @@ struct Item {
 // Work counters of a docking run (DockParams::stats): atom interpolations,
 // clash candidates tested against the circle bound, surviving pairs,
 // candidate pairs of the evaluated sweeps (memoised ones included; times S
-// gives the pair trials), starts bounded out of the top-K.
-constexpr int N_STATS = 5;
+// gives the pair trials), starts bounded out of the top-K, evaluated bond
+// sweeps (each S trial poses, one of them the current pose).
+constexpr int N_STATS = 6;
 
 struct DockParams {
   // batch

@@ -77,7 +77,7 @@ class ligate_work(ctypes.Structure):
                 ("pair_evals", ctypes.c_double), ("starts", ctypes.c_double),
                 ("done_atom_evals", ctypes.c_double), ("done_pair_tests", ctypes.c_double),
                 ("done_pair_survivors", ctypes.c_double), ("done_pair_evals", ctypes.c_double),
-                ("done_pruned_starts", ctypes.c_double)]
+                ("done_pruned_starts", ctypes.c_double), ("done_bond_sweeps", ctypes.c_double)]
 
 
 # name -> (restype, argtypes)

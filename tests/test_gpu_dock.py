@@ -103,6 +103,7 @@ def test_sweep_bound_counts_and_pruning(batched_small):
             pl.close()
             assert wk.done_pruned_starts == 0
             assert wk.done_atom_evals == wk.atom_evals and wk.done_pair_evals == wk.pair_evals
+            assert wk.starts + wk.done_bond_sweeps * 15 == wk.poses  # S = 16
         samp = Sampling(w.sampling.quats[:32], 8, 16, 16)
         pl = D.Plan(ph, bh, samp, mode="fp32")
         res = pl.result()
@@ -116,6 +117,7 @@ def test_sweep_bound_counts_and_pruning(batched_small):
           "of the search space")
     assert 0 < wk.done_pruned_starts < wk.starts
     assert wk.done_atom_evals < wk.atom_evals and wk.done_pair_evals < wk.pair_evals
+    assert wk.starts + wk.done_bond_sweeps * 15 < wk.poses
     st = Stats()
     for i in range(0, w.ligands.n, 8):
         compare_ligand(w.ligands.ligand(i), w.pocket, samp, res[i], stats=st)
