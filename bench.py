@@ -84,7 +84,7 @@ def algorithmic_flops(work, S, n_starts, total_atoms):
 # valid only for the kernel revision it was captured on (sha1 prefix of
 # dock.cu + dock_device.cuh); any other revision reports null until it is
 # captured again.
-TRAFFIC_BYTES = {("3784072d478c", "batched", 10000): 100289536 + 45178112}
+TRAFFIC_BYTES = {("7eb195cfe1d7", "batched", 10000): 104452608 + 24905984}
 
 
 def kernel_source_sha():

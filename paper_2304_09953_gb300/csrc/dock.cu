@@ -198,7 +198,12 @@ __device__ void build_memo(const DockParams &p, const WarpSmem &w, float4 *pose,
         const float4 qv = pose[bb.v];
         bond_axis(pose[bb.u], qv, mx, my, mz);
         const float a1 = clash_sweep(p, w, pose, d, bb, mx, my, mz, qv, ck, sk, g, k, L, G, n_test, n_pair);
-        if (r * G + g < S && k < S) m1[(slot * S + te) * S + k] = a1;
+        if (r * G + g < S && k < S) {  // kept in L2 ahead of streaming data (evict-last policy)
+          uint64_t pol;
+          asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+          asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(m1 + (slot * S + te) * S + k), "f"(a1),
+                       "l"(pol) : "memory");
+        }
         __syncwarp();
       }
     }
@@ -484,7 +489,10 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
           if (alive && has1 && k < S) {
             const int e1 = br.e1 & 0xffff, q = e1 >> 2;
             const uint32_t tw = q == 0 ? t0 : q == 1 ? t1 : q == 2 ? t2 : t3;
-            c1 = __ldcg(m1 + ((br.e1 >> 16) * S + ((tw >> (8 * (e1 & 3))) & 0xff)) * S + k);
+            uint64_t pol;  // the tables stay in L2 ahead of streaming data (evict-last policy)
+            asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+            asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(c1)
+                         : "l"(m1 + ((br.e1 >> 16) * S + ((tw >> (8 * (e1 & 3))) & 0xff)) * S + k), "l"(pol));
           }
           BondRec live = br;
           const int skip = br.n_cand0 + (has1 ? br.n_cand1 : 0);
