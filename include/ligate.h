@@ -274,6 +274,30 @@ ligate_status ligate_plan_output(const ligate_plan *plan, const ligate_pose **de
  * ligand descriptors, so the triage network sees them (enqueues). */
 ligate_status ligate_plan_best_scores(const ligate_plan *plan, float *out, int stride, int column,
                                       void *stream);
+/* Screening for a library's best ligands (paper Sec. 2: the campaign keeps
+ * the ligands with the best scores; Sec. 3.5: cheaper passes first).
+ *
+ * ligate_plan_best_quantile: the k-th smallest of the last run's best
+ * scores, k = ceil(frac * rows) (1 <= k <= rows), into DEVICE out[0]
+ * (enqueues; the first call for a plan of a new size allocates scratch).
+ * Run on a plan whose starts are a subset of another plan's (the same
+ * pocket, precision, torsion steps and ligands; the first orientations and
+ * anchors of the same lists), it gives a value at or above the k-th best
+ * score that the full plan will find: each ligand's best over fewer starts
+ * is at least its best over all of them.
+ *
+ * ligate_plan_set_cutoff: attach DEVICE cutoff[0] (NULL detaches it; the
+ * value is read at each run, so it may be written on the device between
+ * runs).  With a cutoff, a start also stops once the lower bound of its
+ * final energy exceeds *cutoff (ligate_plan_run).  Every ligand whose best
+ * energy in the run's map precision is at or below *cutoff gets its exact
+ * best pose and all its top_k poses at or below *cutoff; other ligands may
+ * report fewer poses or none (start_id -1, score +inf).  So the ligands with
+ * the smallest scores up to the cutoff are found exactly.  Changing the
+ * cutoff pointer synchronises the device and re-captures the plan's run.
+ * Errors: INVALID, CUDA. */
+ligate_status ligate_plan_best_quantile(ligate_plan *plan, double frac, float *out, void *stream);
+ligate_status ligate_plan_set_cutoff(ligate_plan *plan, const float *cutoff);
 /* Kernel launches one run enqueues, and the shape in use. */
 ligate_status ligate_plan_get_tile(const ligate_plan *plan, ligate_tile *tile_out,
                                    int *kernel_launches);

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "ligate_internal.h"
+#include "mlp.h"
 
 namespace ligate {
 
@@ -885,6 +886,12 @@ struct ligate_plan {
   int n_ligands = 0;
   float *rot = nullptr, *anc = nullptr, *quat = nullptr;
   uint16_t *visit = nullptr;  // anchor visiting order (DockParams::visit)
+  // scratch of ligate_plan_best_quantile (grown on demand): best scores,
+  // sort keys and sorted indices, q_cap entries each
+  float *q_scores = nullptr;
+  unsigned long long *q_keys = nullptr;
+  int32_t *q_idx = nullptr;
+  int q_cap = 0;
   Item *items = nullptr;
   int *lig_items = nullptr, *lig_slot0 = nullptr, *counters = nullptr;
   PoseOut *partial = nullptr, *out = nullptr;
@@ -926,6 +933,7 @@ static void free_plan(ligate_plan *pl) {
   if (pl->graph) cudaGraphDestroy(pl->graph);
   if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
   cudaFree(pl->rot); cudaFree(pl->anc); cudaFree(pl->quat); cudaFree(pl->visit);
+  cudaFree(pl->q_scores); cudaFree(pl->q_keys); cudaFree(pl->q_idx);
   cudaFree(pl->items); cudaFree(pl->lig_items); cudaFree(pl->lig_slot0);
   cudaFree(pl->counters); cudaFree(pl->partial); cudaFree(pl->out); cudaFree(pl->stats);
   cudaFree(pl->row_lig);
@@ -1661,6 +1669,55 @@ extern "C" ligate_status ligate_plan_best_scores(const ligate_plan *pl, float *o
   best_scores_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(pl->out, n, pl->p.K, out, stride, column);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "plan_best_scores");
+  return LIGATE_OK;
+}
+
+__global__ void pick_value_kernel(const float *__restrict__ v, const int32_t *__restrict__ idx, int k,
+                                  float *__restrict__ out) {
+  if (threadIdx.x == 0) *out = v[idx[k - 1]];
+}
+
+extern "C" ligate_status ligate_plan_best_quantile(ligate_plan *pl, double frac, float *out, void *stream) {
+  if (!pl || !out || !(frac > 0.0) || frac > 1.0) {
+    set_error("plan_best_quantile: need a plan, an output and 0 < frac <= 1");
+    return LIGATE_ERR_INVALID;
+  }
+  const int n = pl->rows;
+  if (n == 0) { set_error("plan_best_quantile: the plan has no rows"); return LIGATE_ERR_INVALID; }
+  const int k = std::min(n, std::max(1, (int)std::ceil(frac * n - 1e-9)));
+  int n2 = 2048;
+  while (n2 < n) n2 <<= 1;
+  cudaError_t e = cudaSuccess;
+  if (pl->q_cap < n2) {  // grown once per size (allocates: not inside a capture)
+    cudaFree(pl->q_scores); cudaFree(pl->q_keys); cudaFree(pl->q_idx);
+    pl->q_scores = nullptr; pl->q_keys = nullptr; pl->q_idx = nullptr; pl->q_cap = 0;
+    if ((e = dmalloc(&pl->q_scores, n2)) != cudaSuccess || (e = dmalloc(&pl->q_keys, n2)) != cudaSuccess ||
+        (e = dmalloc(&pl->q_idx, n2)) != cudaSuccess)
+      return cuda_fail(e, "plan_best_quantile");
+    pl->q_cap = n2;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  best_scores_kernel<<<(n + 255) / 256, 256, 0, st>>>(pl->out, n, pl->p.K, pl->q_scores, 1, 0);
+  if ((e = cudaGetLastError()) == cudaSuccess) e = mlp::sort_select(pl->q_scores, n, k, pl->q_keys, n2, pl->q_idx, st);
+  if (e == cudaSuccess) {
+    pick_value_kernel<<<1, 32, 0, st>>>(pl->q_scores, pl->q_idx, k, out);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "plan_best_quantile");
+  return LIGATE_OK;
+}
+
+extern "C" ligate_status ligate_plan_set_cutoff(ligate_plan *pl, const float *cutoff) {
+  if (!pl) { set_error("plan_set_cutoff: NULL plan"); return LIGATE_ERR_INVALID; }
+  if (pl->p.cut == cutoff) return LIGATE_OK;
+  // the captured run holds the parameters it was captured with: capture it
+  // again at the next run, once no launch of it is in flight
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "plan_set_cutoff");
+  if (pl->exec) { cudaGraphExecDestroy(pl->exec); pl->exec = nullptr; }
+  if (pl->graph) { cudaGraphDestroy(pl->graph); pl->graph = nullptr; }
+  if (pl->cap_stream) { cudaStreamDestroy(pl->cap_stream); pl->cap_stream = nullptr; }
+  pl->p.cut = cutoff;
   return LIGATE_OK;
 }
 

@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
     float thr = INF;  // K-th best energy of the item so far: a start bounded above it stops
     float thr_pub = INF;  // the last value this warp shared with the row's other items
     unsigned *const row_thr = p.lig_thr ? p.lig_thr + item.row : nullptr;
+    const float cut = p.cut ? __ldcg(p.cut) : INF;  // screening cutoff (the same for every ligand)
     // work counters of this lane's group: atom interpolations, pair tests,
     // pair survivors, candidate pairs of the evaluated sweeps, pruned starts,
     // evaluated bond sweeps
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(128, MINB) dock_kernel(const DockParams p) {
       float E = fmaf(p.clash_w, clash_ref, e);
       float A = ef;  // grid energy of the atoms fixed for good (the bound's first part)
       shared_key = __shfl_sync(FULL, shared_key, 0);
-      const float thr_use = fminf(thr, shared_key ? key_value(~shared_key) : INF);
+      const float thr_use = fminf(fminf(thr, cut), shared_key ? key_value(~shared_key) : INF);
       // a group past the item's end, or a start bounded above the K-th best, sweeps nothing
       bool alive = s0 + g < item.s1 && !beyond_bound(A + w.lbc[0], thr_use);
       if (s0 + g < item.s1 && !alive) ++n_prn;

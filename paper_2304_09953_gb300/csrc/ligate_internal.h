@@ -197,6 +197,8 @@ struct DockParams {
   int *done;               // [n_ligands] finished items per ligand
   unsigned *lig_thr;       // optional [n_ligands]: least K-th best energy any item of the row has
                            // reached, as ~(order-preserving key); 0 (reset value) = none yet
+  const float *cut;        // optional [1], device: screening cutoff; a start stops once its bound
+                           // exceeds it (null: none; see ligate_plan_set_cutoff)
   PoseOut *partial;        // [n_items][K]
   PoseOut *out;            // [n_ligands][K]
   // shared-memory shape

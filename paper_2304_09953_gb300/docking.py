@@ -138,6 +138,15 @@ class Plan:
     def work(self):
         return N.ligate_plan_work(self.h)
 
+    def best_quantile(self, frac, out, stream=None):
+        """k-th smallest best score of the last run into DEVICE out[0]."""
+        N.ligate_plan_best_quantile(self.h, frac, out, stream)
+
+    def set_cutoff(self, cutoff):
+        """Screening cutoff for later runs: DEVICE tensor of one float, or None."""
+        self._cutoff = cutoff  # kept alive while attached
+        N.ligate_plan_set_cutoff(self.h, cutoff)
+
     def close(self):
         if getattr(self, "h", None):
             N.ligate_plan_destroy(self.h)

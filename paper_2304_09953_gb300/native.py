@@ -98,6 +98,8 @@ _SIGS = {
     "ligate_plan_run_subset": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
     "ligate_plan_output": (ctypes.c_int, [P, P]),
     "ligate_plan_best_scores": (ctypes.c_int, [P, P, ctypes.c_int, ctypes.c_int, P]),
+    "ligate_plan_best_quantile": (ctypes.c_int, [P, ctypes.c_double, P, P]),
+    "ligate_plan_set_cutoff": (ctypes.c_int, [P, P]),
     "ligate_plan_get_tile": (ctypes.c_int, [P, P, P]),
     "ligate_plan_work": (ctypes.c_int, [P, P]),
     "ligate_plan_destroy": (None, [P]),
@@ -405,6 +407,16 @@ def ligate_plan_rescore_refined(plan, refined, out, stream=None):
 def ligate_plan_best_scores(plan, out, stride, column, stream=None):
     check(load().ligate_plan_best_scores(plan, _ptr(out), int(stride), int(column), stream),
           "ligate_plan_best_scores")
+
+
+def ligate_plan_best_quantile(plan, frac, out, stream=None):
+    """k-th smallest best score of the last run (k = ceil(frac rows)) into DEVICE out[0]."""
+    check(load().ligate_plan_best_quantile(plan, float(frac), _ptr(out), stream), "ligate_plan_best_quantile")
+
+
+def ligate_plan_set_cutoff(plan, cutoff):
+    """Attach a DEVICE cutoff (one float) to a plan's runs; None detaches it."""
+    check(load().ligate_plan_set_cutoff(plan, _ptr(cutoff)), "ligate_plan_set_cutoff")
 
 
 def ligate_autotune(pocket, batch, sampling_struct, budget_ms=20000.0):

@@ -124,6 +124,59 @@ def test_sweep_bound_counts_and_pruning(batched_small):
     print(st.line())
 
 
+def test_screening_cutoff_keeps_every_pose_below_it(batched_small):
+    """ligate_plan_set_cutoff / ligate_plan_best_quantile on 64 ligands (256
+    starts, K = 16, FP32 maps).  The quantile is the k-th smallest best score;
+    with it as cutoff every pose at or below it is the full run's, bit for
+    bit and in the same order, no ligand reports a pose below its full-run
+    best, and fewer atoms are evaluated; detached, the run is the full run
+    again.  A plan over the first starts only (the coarse pass) gives a
+    quantile at or above the full plan's."""
+    w = batched_small
+    samp = Sampling(w.sampling.quats[:32], 8, 16, 16)
+    ph, bh = D.PocketHandle(w.pocket), D.BatchHandle(w.ligands)
+    try:
+        pl = D.Plan(ph, bh, samp, mode="fp32")
+        full = pl.result()
+        w_full = pl.work()
+        cut = torch.empty(1, dtype=torch.float32, device="cuda")
+        pl.best_quantile(0.25, cut)
+        torch.cuda.synchronize()
+        c = float(cut.item())
+        best = full["score"][:, 0]
+        assert c == np.sort(best)[int(np.ceil(0.25 * w.ligands.n)) - 1]
+        pl.set_cutoff(cut)
+        scr = pl.result()
+        w_scr = pl.work()
+        pl.set_cutoff(None)
+        again = pl.result()
+        pl.close()
+        coarse = D.Plan(ph, bh, Sampling(w.sampling.quats[:8], 4, 16, 1), mode="fp32")
+        coarse.result()
+        cq = torch.empty(1, dtype=torch.float32, device="cuda")
+        coarse.best_quantile(0.25, cq)
+        torch.cuda.synchronize()
+        coarse.close()
+    finally:
+        bh.close()
+        ph.close()
+    assert np.array_equal(again, full)
+    kept = 0
+    for i in range(w.ligands.n):
+        f, s = full[i], scr[i]
+        m = int(np.sum(f["score"] <= c))
+        assert np.array_equal(s[:m], f[:m]), i
+        assert m == 16 or s[m]["start_id"] == -1 or s[m]["score"] > c
+        ok = s["start_id"] >= 0
+        assert np.all(s["score"][ok] >= best[i])
+        kept += m > 0
+    assert kept == int(np.sum(best <= c))
+    assert w_scr.done_atom_evals < w_full.done_atom_evals
+    assert float(cq.item()) >= c
+    print(f"screening at the 25% quantile {c:.3f}: atom evaluations "
+          f"{w_scr.done_atom_evals / w_full.done_atom_evals:.3f} of the full run's")
+
+
 def test_target_library_sample(workload_factory):
     """Ligands of the 1,000,000-ligand target library (up to 80 atoms and 15
     rotatable bonds, so all four packed torsion words; 8 x 96^3 maps), 256
