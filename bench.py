@@ -84,7 +84,7 @@ def algorithmic_flops(work, S, n_starts, total_atoms):
 # valid only for the kernel revision it was captured on (sha1 prefix of
 # dock.cu + dock_device.cuh); any other revision reports null until it is
 # captured again.
-TRAFFIC_BYTES = {("7eb195cfe1d7", "batched", 10000): 104452608 + 24905984}
+TRAFFIC_BYTES = {("cf4358d5f3d0", "batched", 10000): 104403456 + 24783104}
 
 
 def kernel_source_sha():
@@ -130,6 +130,8 @@ def parse():
     ap.add_argument("--refine-iters", type=int, default=32)
     ap.add_argument("--train-ligands", type=int, default=200000)
     ap.add_argument("--keep-frac", type=float, default=0.05)
+    ap.add_argument("--coarse", default="32x8",
+                    help="coarse docking pass of the triage: first ORIENTATIONSxANCHORS of the sampling")
     a = ap.parse_args()
     if a.n_ligands is None:
         a.n_ligands = 10000 if a.workload == "batched" else 1_000_000
@@ -195,10 +197,13 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     t_train = time.perf_counter() - t1
 
     # coarse-docking variant: the same network also sees the best score of a
-    # cheap docking pass (first 32 orientations x 8 anchors = 256 starts, 1/32
-    # of the sampling) in the free descriptor column 233
+    # cheap docking pass (--coarse; by default the first 32 orientations x 8
+    # anchors = 256 starts, 1/32 of the sampling) in the free descriptor
+    # column 233
     import dataclasses
-    coarse_s = dataclasses.replace(w.sampling, quats=w.sampling.quats[:32], n_anchor=8, top_k=1)
+    cq, ca = (int(x) for x in args.coarse.split("x"))
+    coarse_s = dataclasses.replace(w.sampling, quats=w.sampling.quats[:cq], n_anchor=ca, top_k=1)
+    c_starts = cq * ca
     cp_tr = D.Plan(ph, tb, coarse_s, mode="bf16", rescore=False)
     cp_tr.run(sh)
     N.ligate_plan_best_scores(cp_tr.h, desc_tr, 256, 233, sh)
@@ -301,14 +306,14 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
     pred_c = pred_all.cpu().numpy()
     coarse_only = cplan.result(sh)["score"][:, 0]
     coarse = {"value": n / tc5, "unit": "ligands/s", "ms_per_step": 1000 * tc5, "keep_frac": args.keep_frac,
-              "recall_top1pct": T.recall(truth_scores, selc5),
+              "recall_top1pct": T.recall(truth_scores, selc5), "coarse_starts": c_starts,
               "recall_curve": {str(f): round(r, 4) for f, r in
                                T.recall_curve(pred_c, truth_scores, [0.05, 0.1, 0.2, 0.3, 0.5]).items()},
               "keep_needed_on_library_for_0.99": round(T.keep_for_recall(pred_c, truth_scores, 0.99), 4),
               "coarse_score_alone_recall_curve": {str(f): round(r, 4) for f, r in
                                                   T.recall_curve(coarse_only, truth_scores,
                                                                  [0.05, 0.1, 0.2, 0.3, 0.5]).items()},
-              "form": "descriptors + coarse docking score (256 starts, bf16) in column 233 + MLP rank + "
+              "form": f"descriptors + coarse docking score ({c_starts} starts, bf16) in column 233 + MLP rank + "
                       "dock kept fraction (chosen form)"}
     if keep_cal_c < 1.0:
         kcc, selcc, tcc = timed_c(keep_cal_c)
@@ -319,7 +324,7 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
 
     # exact screening for the library's top 1%: the coarse pass's best scores
     # give a cutoff at or above the library's own 1% cut (each ligand's best
-    # over 256 starts is at least its best over all 8,192), computed on the
+    # over the coarse starts is at least its best over all 8,192), computed on the
     # device; the chosen plan then stops every start whose energy bound
     # exceeds min(K-th best, cutoff), so the top 1% is docked exactly and the
     # rest only as far as it takes to rule it out
@@ -343,7 +348,7 @@ def run_triage(args, w, ph, bh, chosen, plain, tile, stream, sh):
               "cutoff": float(cut.item()), "library_top1pct_cut": float(np.sort(truth_scores)[k1 - 1]),
               "ligands_with_poses": int(np.sum(scr["start_id"][:, 0] >= 0)),
               "recall_top1pct": T.recall(truth_scores, top_of(scr["score"][:, 0], np.arange(n))),
-              "form": "coarse docking pass (256 starts, bf16) -> its 1% best-score quantile as cutoff on the "
+              "form": f"coarse docking pass ({c_starts} starts, bf16) -> its 1% best-score quantile as cutoff on the "
                       "device -> chosen form on every ligand, a start stopped once its energy bound exceeds "
                       "min(K-th best, cutoff): the top 1% docked exactly"}
     if keep_cal_c < 1.0:  # the same cutoff inside the calibrated coarse-docking triage

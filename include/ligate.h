@@ -284,7 +284,9 @@ ligate_status ligate_plan_best_scores(const ligate_plan *plan, float *out, int s
  * pocket, precision, torsion steps and ligands; the first orientations and
  * anchors of the same lists), it gives a value at or above the k-th best
  * score that the full plan will find: each ligand's best over fewer starts
- * is at least its best over all of them.
+ * is at least its best over all of them.  The quantile is taken over the
+ * scores the run reports, so for a cutoff in the search energies of the
+ * plan it is attached to, take it from a plan that does not rescore.
  *
  * ligate_plan_set_cutoff: attach DEVICE cutoff[0] (NULL detaches it; the
  * value is read at each run, so it may be written on the device between
