@@ -13,9 +13,14 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <unistd.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <fstream>
 #include <sstream>
 #include <string>
@@ -58,6 +63,79 @@ static int pow2ceil(int v) {
   int p = 1;
   while (p < v) p <<= 1;
   return p;
+}
+
+// Host worker threads for the per-ligand packing loops, started on first use
+// and kept for the life of the process (never destroyed: no join at exit).
+// Starting and joining 15 threads costs about half a millisecond, and a
+// batch runs two such loops.  One caller uses the pool at a time; a
+// concurrent caller, or a forked child (which inherits no workers), runs
+// its loop on threads of its own.
+struct HostPool {
+  std::mutex busy;  // held by the caller whose loop the workers run
+  std::mutex m;     // guards the fields below
+  std::condition_variable cv_work, cv_done;
+  std::vector<std::thread> workers;
+  pid_t pid = getpid();
+  uint64_t gen = 0;  // loops handed out so far
+  int pending = 0;   // workers not yet done with the current loop
+  const std::function<void()> *job = nullptr;
+
+  void work() {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void()> *j;
+      {
+        std::unique_lock<std::mutex> g(m);
+        cv_work.wait(g, [&] { return gen != seen; });
+        seen = gen;
+        j = job;
+      }
+      (*j)();
+      std::lock_guard<std::mutex> g(m);
+      if (--pending == 0) cv_done.notify_one();
+    }
+  }
+};
+
+static HostPool &host_pool() {
+  static HostPool *pool = new HostPool();
+  return *pool;
+}
+
+// fn(i) for every i in [0, n), handed out in blocks of 64 to `threads`
+// threads (the caller's included).
+static void parallel_for(int n, int threads, const std::function<void(int)> &fn) {
+  std::atomic<int> next(0);
+  const std::function<void()> body = [&]() {
+    for (;;) {
+      const int i0 = next.fetch_add(64);
+      if (i0 >= n) break;
+      for (int i = i0; i < std::min(n, i0 + 64); ++i) fn(i);
+    }
+  };
+  if (threads <= 1) { body(); return; }
+  HostPool &P = host_pool();
+  std::unique_lock<std::mutex> busy(P.busy, std::try_to_lock);
+  if (!busy.owns_lock() || P.pid != getpid()) {
+    std::vector<std::thread> th;
+    for (int t = 1; t < threads; ++t) th.emplace_back(body);
+    body();
+    for (auto &t : th) t.join();
+    return;
+  }
+  {
+    std::lock_guard<std::mutex> g(P.m);
+    while ((int)P.workers.size() < threads - 1) P.workers.emplace_back([&P] { P.work(); });
+    P.job = &body;
+    P.pending = (int)P.workers.size();
+    ++P.gen;
+  }
+  P.cv_work.notify_all();
+  body();
+  std::unique_lock<std::mutex> g(P.m);
+  P.cv_done.wait(g, [&] { return P.pending == 0; });
+  P.job = nullptr;
 }
 
 }  // namespace ligate
@@ -384,7 +462,8 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   parent.assign(n, -1);
   size.assign(n, 1);
   stack.clear();
-  std::vector<int> order;
+  std::vector<int> &order = P.order;
+  order.clear();
   order.reserve(n);
   stack.push_back(0);
   parent[0] = -1;
@@ -410,7 +489,6 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   }
   for (int p = n - 1; p > 0; --p) size[parent[order[p]]] += size[order[p]];
   P.n = n;
-  P.order = order;
   P.words = (n + 31) / 32;
   P.atoms.resize(n);
   P.types.resize(n);
@@ -479,7 +557,8 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   // earlier bonds that separate j from the moved subtree (an earlier bond e
   // separates j when exactly one of j and v lies in e's subtree [v_e, end_e)):
   // none, then the most frequent single bond e1, then the rest
-  P.cand.clear();
+  thread_local std::vector<uint16_t> cand;  // this ligand's candidates, copied out once at the end
+  cand.clear();
   // bitsets over DFS positions (at most LIGATE_MAX_ATOMS bits): for bond bi,
   // the atoms no earlier bond separates from the moved subtree, those exactly
   // one separates (and which one), and the rest; a candidate's group is its
@@ -495,7 +574,7 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   sep.assign(br.size() * MW, 0u);
   for (size_t bi = 0; bi < br.size(); ++bi) {
     BondRec &r = br[bi];
-    r.cand_off = (int)P.cand.size();
+    r.cand_off = (int)cand.size();
     uint32_t once[MW] = {0}, twice[MW] = {0};
     for (size_t e = 0; e < bi; ++e) {
       uint32_t *se = &sep[e * MW];
@@ -519,12 +598,12 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
       for (int i = r.v + 1; i < r.end; ++i)
         for (int wd = 0; wd < P.words; ++wd)
           for (uint32_t m = partners(i, wd) & group[wd]; m; m &= m - 1)
-            P.cand.push_back((uint16_t)(i | ((32 * wd + __builtin_ctz(m)) << 8)));
+            cand.push_back((uint16_t)(i | ((32 * wd + __builtin_ctz(m)) << 8)));
     };
     uint32_t none[MW];
     for (int wd = 0; wd < P.words; ++wd) none[wd] = ~once[wd];
     emit(none);
-    r.n_cand0 = (int)P.cand.size() - r.cand_off;
+    r.n_cand0 = (int)cand.size() - r.cand_off;
     // e1: the earlier bond that alone separates the most candidates (ties:
     // the earlier bond)
     r.e1 = -1;
@@ -541,13 +620,14 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
       for (int wd = 0; wd < P.words; ++wd) g1[wd] = sep[r.e1 * MW + wd] & ~twice[wd];
     for (int wd = 0; wd < P.words; ++wd) rest_bits[wd] = once[wd] & ~g1[wd];
     emit(g1);
-    r.n_cand1 = (int)P.cand.size() - r.cand_off - r.n_cand0;
+    r.n_cand1 = (int)cand.size() - r.cand_off - r.n_cand0;
     emit(rest_bits);
-    r.n_cand = (int)P.cand.size() - r.cand_off;
+    r.n_cand = (int)cand.size() - r.cand_off;
   }
   for (size_t bi = 2, slot = 0; bi < br.size(); ++bi)  // table slots of bonds 2, 3, ...
     if (br[bi].n_cand1 > 0) br[bi].e1 |= (int)(slot++) << 16;
   P.bonds = br;
+  P.cand.assign(cand.begin(), cand.end());
   return LIGATE_OK;
 }
 
@@ -615,22 +695,7 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   std::vector<std::string> errs(n);
   const unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
   const int nthreads = n < 256 ? 1 : (int)nt;
-  // fn(i) for every ligand, blocks of 64 ligands handed out to the threads
-  auto parallel = [&](auto fn) {
-    std::atomic<int> next(0);
-    auto worker = [&]() {
-      for (;;) {
-        const int i0 = next.fetch_add(64);
-        if (i0 >= n) break;
-        for (int i = i0; i < std::min(n, i0 + 64); ++i) fn(i);
-      }
-    };
-    std::vector<std::thread> th;
-    for (int t = 1; t < nthreads; ++t) th.emplace_back(worker);
-    worker();
-    for (auto &t : th) t.join();
-  };
-  parallel([&](int i) {
+  parallel_for(n, nthreads, [&](int i) {
     char buf[256];
     buf[0] = 0;
     st[i] = pack_one(L, i, packs[i], buf, sizeof(buf));
@@ -678,7 +743,7 @@ extern "C" ligate_status ligate_batch_create(const ligate_ligands *L, ligate_bat
   d.h_types.resize(na);
   d.h_cand.resize(nc);
   d.h_order.resize(na);
-  parallel([&](int i) {  // each ligand into its place, then release its pieces
+  parallel_for(n, nthreads, [&](int i) {  // each ligand into its place, then release its pieces
     const LigDesc &ld = d.h_lig[i];
     LigPack &pk = packs[i];
     for (int q = 0; q < ld.n_atoms; ++q) d.h_order[ld.atom_base + q] = (uint8_t)pk.order[q];
@@ -1118,9 +1183,32 @@ static ligate_status plan_create_impl(const ligate_pocket *P, const ligate_batch
   pl->work.atom_evals = aev;
   pl->work.pair_evals = pev;
   pl->work.starts = (double)n * p.n_starts;
-  std::vector<int> order(items.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  // descending cost (in single precision), ties in list order: an LSD radix
+  // sort of the complemented bit patterns (non-negative floats order like
+  // their bit patterns), 8 bits per pass, passes whose byte is the same for
+  // every item skipped
+  std::vector<uint32_t> key(items.size()), key2(items.size());
+  std::vector<uint32_t> order(items.size()), order2(items.size());
+  for (size_t i = 0; i < items.size(); ++i) {
+    const float c = (float)cost[i];
+    uint32_t bits;
+    memcpy(&bits, &c, 4);
+    key[i] = ~bits;
+    order[i] = (uint32_t)i;
+  }
+  for (int sh = 0; sh < 32; sh += 8) {
+    size_t cnt[257] = {0};
+    for (size_t i = 0; i < key.size(); ++i) ++cnt[((key[i] >> sh) & 255u) + 1];
+    if (std::any_of(cnt + 1, cnt + 257, [&](size_t c) { return c == key.size(); })) continue;
+    for (int dg = 0; dg < 256; ++dg) cnt[dg + 1] += cnt[dg];
+    for (size_t i = 0; i < key.size(); ++i) {
+      const size_t q = cnt[(key[i] >> sh) & 255u]++;
+      key2[q] = key[i];
+      order2[q] = order[i];
+    }
+    key.swap(key2);
+    order.swap(order2);
+  }
   std::vector<Item> sorted(items.size());
   for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
   const size_t ni = items.size();
