@@ -643,6 +643,13 @@ def main():
     work = chosen.work()
     work_plain = plain.work()
     n_lig = w.ligands.n  # this rank's ligands
+    # the chosen form's top 1% (by its reported best scores) against the
+    # plain FP32 form's, both from the last timed runs (this rank's ligands)
+    from paper_2304_09953_gb300 import triage as T
+    k1 = max(1, int(np.ceil(0.01 * n_lig)))
+    best_chosen = chosen.output()["score"][:, 0]
+    top_chosen = np.lexsort((np.arange(n_lig), best_chosen))[:k1]
+    recall_vs_plain = T.recall(plain.output()["score"][:, 0], top_chosen)
     value = n_job * args.steps / t_chosen
     poses_s = sum_over_ranks(work.poses, device="cuda") * args.steps / t_chosen
     mean_ms = t_chosen * 1000 / args.steps
@@ -815,6 +822,7 @@ def main():
                    "tile": {"warps_per_cta": t_.warps_per_cta, "ctas_per_sm": t_.ctas_per_sm,
                             "starts_per_item": list(t_.starts_per_item), "reg_cap": t_.reg_cap},
                    "autotune_s": round(tune_s, 2), "parallelism": f"replicas x{ws}"},
+        "top1pct_recall_vs_plain": recall_vs_plain,
         "poses_per_s": poses_s,
         "poses_evaluated_per_s": poses_eval_s,
         "poses_note": "unique poses of the search space decided per second (O x A x (1 + R (S - 1)) per "

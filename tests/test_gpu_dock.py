@@ -177,6 +177,54 @@ def test_screening_cutoff_keeps_every_pose_below_it(batched_small):
           f"{w_scr.done_atom_evals / w_full.done_atom_evals:.3f} of the full run's")
 
 
+def test_screening_with_rescoring_matches_the_chosen_form(workload_factory):
+    """Screening as the benchmark runs it, on 2,000 ligands of the target
+    library: a coarse plan (the first 32 orientations x 8 anchors, BF16, no
+    rescoring) gives the 1% quantile of its best scores on the device; the
+    chosen form (BF16 search, FP32 top-16 rescoring) run with that cutoff
+    ranks the same ligands in its top 1% as without it, reports the same
+    rescored best for every ligand whose BF16 best is at or below the cutoff,
+    and its BF16 search keeps every such pose of the full run bit for bit."""
+    import dataclasses
+    w = workload_factory("combined", n_ligands=2000)
+    n = w.ligands.n
+    k1 = int(np.ceil(0.01 * n))
+    ph, bh = D.PocketHandle(w.pocket), D.BatchHandle(w.ligands)
+    try:
+        chosen = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=True)
+        full = chosen.result()
+        coarse = D.Plan(ph, bh, dataclasses.replace(w.sampling, quats=w.sampling.quats[:32], n_anchor=8, top_k=1),
+                        mode="bf16", rescore=False)
+        coarse.run()
+        cut = torch.empty(1, dtype=torch.float32, device="cuda")
+        coarse.best_quantile(0.01, cut)
+        chosen.set_cutoff(cut)
+        scr = chosen.result()
+        search = D.Plan(ph, bh, w.sampling, mode="bf16", rescore=False)
+        s_full = search.result()
+        search.set_cutoff(cut)
+        s_scr = search.result()
+        c = float(cut.item())
+        for pl in (chosen, coarse, search):
+            pl.close()
+    finally:
+        bh.close()
+        ph.close()
+
+    def top(best):
+        return set(np.lexsort((np.arange(n), best))[:k1].tolist())
+
+    best16 = s_full["score"][:, 0]
+    inside = np.where(best16 <= c)[0]
+    assert c >= np.sort(best16)[k1 - 1]  # the coarse quantile bounds the full one
+    assert top(scr["score"][:, 0]) == top(full["score"][:, 0])
+    assert np.array_equal(scr["score"][inside, 0], full["score"][inside, 0])
+    for i in inside:
+        m = s_full[i]["score"] <= c
+        assert np.array_equal(s_scr[i][:int(m.sum())], s_full[i][m]), i
+    print(f"cutoff {c:.3f}: {len(inside)} of {n} ligands at or below it")
+
+
 def test_target_library_sample(workload_factory):
     """Ligands of the 1,000,000-ligand target library (up to 80 atoms and 15
     rotatable bonds, so all four packed torsion words; 8 x 96^3 maps), 256
