@@ -80,6 +80,38 @@ def test_batch_limits_are_unsupported():
         assert _create(N.make_ligands_struct(many)) == N.LIGATE_ERR_UNSUPPORTED
 
 
+def test_batch_packing_on_host_threads_reports_errors_per_caller():
+    """Batches of 600 ligands are packed on the library's host thread pool
+    (a batch of 256 ligands or more); one bad ligand in each fails the call
+    before any device work, with its own index in the caller's error
+    message.  Four callers at once: one runs on the pool, the others on
+    threads of their own, and every call returns."""
+    import threading
+    n = 600
+    libs = []
+    for bad in (500, 17, 333, 599):
+        lig = make_ligands(11, np.full(n, 20, np.int32), np.full(n, 3, np.int32), 8)
+        lig.bonds[lig.bond_offset[bad] + 2, 1] = 99  # an atom index outside the ligand
+        libs.append((bad, N.make_ligands_struct(lig)))
+    out = {}
+
+    def call(bad, st):
+        out[bad] = (_create(st), N.load().ligate_last_error())
+
+    for _ in range(3):
+        out.clear()
+        th = [threading.Thread(target=call, args=a) for a in libs]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(timeout=120)
+        assert not any(t.is_alive() for t in th)
+        for bad, _ in libs:
+            code, msg = out[bad]
+            assert code == N.LIGATE_ERR_INVALID
+            assert f"ligand {bad}: bond 2 has bad atom index".encode() in msg, msg
+
+
 def test_pocket_validation_errors_on_host():
     lib = N.load()
     h = ctypes.c_void_p()
