@@ -141,3 +141,17 @@ def test_null_handles_are_accepted_by_destroy():
 def test_null_plan_is_invalid(fn):
     lib = N.load()
     assert getattr(lib, fn)(None, None, None) == N.LIGATE_ERR_INVALID
+
+
+def test_screening_calls_reject_bad_arguments_on_host():
+    """ligate_plan_best_quantile and ligate_plan_set_cutoff check their
+    arguments before any device work: a NULL plan or output, or a fraction
+    outside (0, 1], is INVALID with a message."""
+    lib = N.load()
+    out = ctypes.c_float()
+    for frac in (0.01, 0.0, -1.0, 1.5, float("nan")):
+        assert lib.ligate_plan_best_quantile(None, ctypes.c_double(frac), ctypes.byref(out), None) == \
+            N.LIGATE_ERR_INVALID
+        assert b"0 < frac <= 1" in lib.ligate_last_error()
+    assert lib.ligate_plan_set_cutoff(None, None) == N.LIGATE_ERR_INVALID
+    assert b"NULL plan" in lib.ligate_last_error()
