@@ -530,27 +530,25 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   std::sort(br.begin(), br.end(), [](const BondRec &a, const BondRec &b) { return a.v < b.v; });
   P.n_rot = (int)br.size();
   // clash-eligible pairs in DFS numbering: topological distance >= 4, i.e.
-  // every atom but those within 3 bonds (a depth-3 walk on the tree, which
-  // only has to skip the atom it came from)
-  P.elig.assign((size_t)n * P.words, 0u);
-  for (int s0 = 0; s0 < n; ++s0) {  // walk in input numbering, bits in DFS numbering
-    uint32_t *row = P.elig.data() + (size_t)pos[s0] * P.words;
-    for (int w = 0; w < P.words; ++w) row[w] = ~0u;
-    if (n & 31) row[P.words - 1] = (1u << (n & 31)) - 1u;
-    const int *pos_of = pos.data();
-    auto near = [row, pos_of](int a) { const int q = pos_of[a]; row[q >> 5] &= ~(1u << (q & 31)); };
-    near(s0);
-    for (int qa = off[s0]; qa < off[s0 + 1]; ++qa) {
-      const int a = nbr[qa];
-      near(a);
-      for (int qb = off[a]; qb < off[a + 1]; ++qb) {
-        const int b = nbr[qb];
-        if (b == s0) continue;
-        near(b);
-        for (int qc = off[b]; qc < off[b + 1]; ++qc)
-          if (nbr[qc] != a) near(nbr[qc]);
-      }
-    }
+  // every atom but those within 3 bonds.  Atoms within d bonds of atom a
+  // (input numbering) as bit sets over DFS positions: within 0 = a itself,
+  // within d = within d - 1 of a or of a neighbour of a
+  const int W = P.words;
+  thread_local std::vector<uint32_t> near0, near1;
+  near0.assign((size_t)n * W, 0u);
+  for (int a = 0; a < n; ++a) near0[(size_t)a * W + (pos[a] >> 5)] |= 1u << (pos[a] & 31);
+  for (int d = 0; d < 3; ++d) {
+    near1 = near0;
+    for (int a = 0; a < n; ++a)
+      for (int q = off[a]; q < off[a + 1]; ++q)
+        for (int wd = 0; wd < W; ++wd) near1[(size_t)a * W + wd] |= near0[(size_t)nbr[q] * W + wd];
+    near0.swap(near1);
+  }
+  P.elig.assign((size_t)n * W, 0u);
+  for (int a = 0; a < n; ++a) {
+    uint32_t *row = P.elig.data() + (size_t)pos[a] * W;
+    for (int wd = 0; wd < W; ++wd) row[wd] = ~near0[(size_t)a * W + wd];
+    if (n & 31) row[W - 1] &= (1u << (n & 31)) - 1u;
   }
   // clash candidates of each bond: moved atom i (v < i < end) x fixed atom j
   // (outside [v, end), j != u), at least 4 bonds apart; ordered by the
