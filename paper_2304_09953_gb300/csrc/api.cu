@@ -555,8 +555,16 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   // earlier bonds that separate j from the moved subtree (an earlier bond e
   // separates j when exactly one of j and v lies in e's subtree [v_e, end_e)):
   // none, then the most frequent single bond e1, then the rest
-  thread_local std::vector<uint16_t> cand;  // this ligand's candidates, copied out once at the end
-  cand.clear();
+  // this ligand's candidates, written through a cursor into per-thread
+  // scratch sized for every moved x other-atom pair, copied out at the end
+  thread_local std::vector<uint16_t> cand;
+  {
+    size_t bound = 0;
+    for (const BondRec &b : br) bound += (size_t)(b.end - b.v) * n;
+    if (cand.size() < bound) cand.resize(bound);
+  }
+  uint16_t *const cw = cand.data();
+  int nc = 0;
   // bitsets over DFS positions (at most LIGATE_MAX_ATOMS bits): for bond bi,
   // the atoms no earlier bond separates from the moved subtree, those exactly
   // one separates (and which one), and the rest; a candidate's group is its
@@ -572,7 +580,7 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
   sep.assign(br.size() * MW, 0u);
   for (size_t bi = 0; bi < br.size(); ++bi) {
     BondRec &r = br[bi];
-    r.cand_off = (int)cand.size();
+    r.cand_off = nc;
     uint32_t once[MW] = {0}, twice[MW] = {0};
     for (size_t e = 0; e < bi; ++e) {
       uint32_t *se = &sep[e * MW];
@@ -596,12 +604,12 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
       for (int i = r.v + 1; i < r.end; ++i)
         for (int wd = 0; wd < P.words; ++wd)
           for (uint32_t m = partners(i, wd) & group[wd]; m; m &= m - 1)
-            cand.push_back((uint16_t)(i | ((32 * wd + __builtin_ctz(m)) << 8)));
+            cw[nc++] = (uint16_t)(i | ((32 * wd + __builtin_ctz(m)) << 8));
     };
     uint32_t none[MW];
     for (int wd = 0; wd < P.words; ++wd) none[wd] = ~once[wd];
     emit(none);
-    r.n_cand0 = (int)cand.size() - r.cand_off;
+    r.n_cand0 = nc - r.cand_off;
     // e1: the earlier bond that alone separates the most candidates (ties:
     // the earlier bond)
     r.e1 = -1;
@@ -618,14 +626,14 @@ ligate_status pack_one(const ligate_ligands *L, int li, LigPack &P, char *err, s
       for (int wd = 0; wd < P.words; ++wd) g1[wd] = sep[r.e1 * MW + wd] & ~twice[wd];
     for (int wd = 0; wd < P.words; ++wd) rest_bits[wd] = once[wd] & ~g1[wd];
     emit(g1);
-    r.n_cand1 = (int)cand.size() - r.cand_off - r.n_cand0;
+    r.n_cand1 = nc - r.cand_off - r.n_cand0;
     emit(rest_bits);
-    r.n_cand = (int)cand.size() - r.cand_off;
+    r.n_cand = nc - r.cand_off;
   }
   for (size_t bi = 2, slot = 0; bi < br.size(); ++bi)  // table slots of bonds 2, 3, ...
     if (br[bi].n_cand1 > 0) br[bi].e1 |= (int)(slot++) << 16;
   P.bonds = br;
-  P.cand.assign(cand.begin(), cand.end());
+  P.cand.assign(cand.begin(), cand.begin() + nc);
   return LIGATE_OK;
 }
 
